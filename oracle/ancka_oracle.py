@@ -1,0 +1,477 @@
+"""FP64 CPU oracle for the ANCKA hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this module.  The CUDA
+path never calls it and shares no code with it.
+
+It restates, in plain numpy / scipy.sparse float64, what the paper defines:
+
+* Section 3.1, Eq. (AK): cosine KNN augmentation graph A_K.
+* Eq. (beta_i): per-node mixing weight beta_i.
+* Eqs. (rw-hg), (rw-ag), (rw-mg): the topology walk matrix P_N; Eq.
+  (p-mat-ancka): P = (I - B) P_N + B P_K.
+* Algorithm 4 (ANCKA): InitBCM (Alg. 3, Eq. pi_c_t / argmaxlabel), the
+  orthogonal iteration (Eq. ortho-iter / zt), Discretize (Def. 2, Eq. updateY,
+  Eq. svd-in-discr, Alg. 5), CalMHC (Alg. 2, Eq. mhc-comp-ancka) and the
+  keep-the-best rule.
+
+Library routines serve as single steps (a dense or sparse matmul, a stable
+sort, LAPACK QR / SVD); nothing is blocked, fused or reordered beyond what the
+paper states.  Where the paper is silent the following readings are used
+(each one is also listed in the design notes):
+
+R1  cos(x, y) = 0 when either row is all-zero.
+R2  K-nearest neighbours are ordered by (similarity desc, index asc); the node
+    itself is excluded by index.
+R3  a node whose KNN degree D_K[i] <= 0 gets a zero row in P_K and beta_i = 0.
+R4  Q^(0) has k+1 columns; Discretize receives columns 2..k+1 of Q (the
+    constant column is the known leading eigenvector).
+R5  Discretize: R starts at I, max_iter = 20, the loop stops when
+    |obj - obj_prev| <= 4 eps max(1, |obj|); Y~ divides each column of Y by its
+    count (Alg. 5); a zero row of Q stays zero in the row-normalised Q~.
+R6  argmax ties go to the lowest index (InitBCM, Discretize, labels).
+R7  V_c: degree desc then id asc, k nodes, re-sorted by id; degree = number of
+    neighbours (graph), incident hyperedges (hypergraph), summed over layers
+    (multiplex).
+R8  Phi(Y^(0)) is evaluated with CalMHC before the loop; a later Y replaces the
+    kept one only if its Phi is strictly lower.
+R9  fixed schedule: T iterations, Discretize + CalMHC when t mod tau == 0 and
+    also at t == T; the early-termination tests (Eq. tcond-1/2) are used only
+    when ``early_stop`` is set.
+R10 QR: Householder (LAPACK) with the signs fixed so that diag(R) > 0.
+R11 directed graph input is made symmetric and binary (A or A^T); repeated
+    entries in an adjacency or a hyperedge count once; a node with no
+    neighbours in a layer contributes a zero row for that layer.
+R12 h(Y) = (Y^T Y)^{-1/2} Y with an empty cluster giving a zero column.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+F64 = np.float64
+EPS = np.finfo(F64).eps
+
+DEFAULTS = dict(k=5, K=10, alpha=0.2, beta=0.5, T=10, gamma=3, T_i=25, tau=5,
+                disc_max_iter=20, eps_Q=0.005, early_stop=False)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.1: cosine similarity and the KNN augmentation graph
+# ----------------------------------------------------------------------------
+def unit_rows(X):
+    """Rows of X scaled to unit 2-norm; zero rows stay zero (reading R1)."""
+    X = np.asarray(X, dtype=F64)
+    nrm = np.sqrt(np.einsum("ij,ij->i", X, X))
+    inv = np.zeros_like(nrm)
+    nz = nrm > 0
+    inv[nz] = 1.0 / nrm[nz]
+    return X * inv[:, None]
+
+
+def cosine(X, i, j):
+    """f(v_i, v_j) = cos(X[i], X[j]) of Section 3.1 for one pair (reading R1)."""
+    X = np.asarray(X, dtype=F64)
+    a, b = X[i], X[j]
+    na, nb = np.sqrt(a @ a), np.sqrt(b @ b)
+    if na == 0 or nb == 0:
+        return 0.0
+    return float(a @ b) / (na * nb)
+
+
+def knn_cosine(X, K, rows=None, chunk=256, extra=1):
+    """N_K(v_i) of Section 3.1 for every (or every listed) row i.
+
+    Returns ``idx`` (len(rows) x K, int64) and ``sim`` (len(rows) x (K+extra)):
+    the similarities of the first K+extra entries of the (sim desc, index asc)
+    order over V \\ {v_i} (readings R1, R2), so callers can see the gap
+    between the K-th and (K+1)-th neighbour.
+    """
+    Xn = unit_rows(X)
+    n = Xn.shape[0]
+    if not 1 <= K <= n - 1:
+        raise ValueError("need 1 <= K <= n-1")
+    rows = np.arange(n) if rows is None else np.asarray(rows, np.int64)
+    kk = min(K + extra, n - 1)
+    idx = np.empty((rows.size, K), np.int64)
+    sim = np.full((rows.size, K + extra), -np.inf)
+    for s in range(0, rows.size, chunk):
+        r = rows[s:s + chunk]
+        S = Xn[r] @ Xn.T
+        S[np.arange(r.size), r] = -np.inf  # v_i itself is not a candidate
+        order = np.argsort(-S, axis=1, kind="stable")[:, :kk]
+        idx[s:s + r.size] = order[:, :K]
+        sim[s:s + r.size, :kk] = np.take_along_axis(S, order, axis=1)
+    return idx, sim
+
+
+def knn_adjacency(X, idx):
+    """A_K of Eq. (AK) from the KNN lists.
+
+    A_K[i,j] = 2 f(i,j) if i and j are in each other's list, f(i,j) if only one
+    of them is, 0 otherwise.  f is evaluated once per unordered pair.
+    """
+    Xn = unit_rows(X)
+    n, K = idx.shape
+    src = np.repeat(np.arange(n, dtype=np.int64), K)
+    dst = np.asarray(idx, np.int64).ravel()
+    # membership count of the unordered pair {i, j}: 1 = one-sided, 2 = mutual
+    lo, hi = np.minimum(src, dst), np.maximum(src, dst)
+    key, count = np.unique(lo * n + hi, return_counts=True)
+    a, b = key // n, key % n
+    f = np.einsum("ij,ij->i", Xn[a], Xn[b])
+    w = count * f
+    A = sp.coo_matrix((np.concatenate([w, w]), (np.concatenate([a, b]), np.concatenate([b, a]))),
+                      shape=(n, n)).tocsr()
+    A.sum_duplicates()
+    return A
+
+
+def knn_transition(A_K):
+    """P_K = D_K^{-1} A_K (Alg. 4 line 1); rows with D_K <= 0 become zero (R3)."""
+    D = np.asarray(A_K.sum(axis=1)).ravel()
+    inv = np.zeros_like(D)
+    pos = D > 0
+    inv[pos] = 1.0 / D[pos]
+    return sp.diags(inv) @ A_K, D
+
+
+# ----------------------------------------------------------------------------
+# Section 6.1: the topology walk P_N
+# ----------------------------------------------------------------------------
+def adjacency_from_csr(n, row_ptr, col, directed=False):
+    """Binary adjacency matrix A; a directed input is made symmetric (R11)."""
+    row_ptr = np.asarray(row_ptr, np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(row_ptr))
+    A = sp.coo_matrix((np.ones(rows.size), (rows, np.asarray(col, np.int64))), shape=(n, n)).tocsr()
+    if directed:
+        A = A + A.T
+    A.data[:] = 1.0  # repeated entries count once (binary A)
+    A.eliminate_zeros()
+    return A
+
+
+def incidence_from_csr(n, he_ptr, he_nodes):
+    """Binary incidence H (m x n) with H[e, v] = 1 iff v in e (Section 2)."""
+    he_ptr = np.asarray(he_ptr, np.int64)
+    m = he_ptr.size - 1
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(he_ptr))
+    H = sp.coo_matrix((np.ones(rows.size), (rows, np.asarray(he_nodes, np.int64))), shape=(m, n)).tocsr()
+    H.data[:] = 1.0
+    return H
+
+
+def _inv_or_zero(v):
+    out = np.zeros_like(v, dtype=F64)
+    nz = v > 0
+    out[nz] = 1.0 / v[nz]
+    return out
+
+
+class Topology:
+    """P_N of Eqs. (rw-hg), (rw-ag), (rw-mg) kept in factored form.
+
+    ``apply(Q)`` returns P_N Q and ``apply_T(Q)`` returns P_N^T Q, each as the
+    paper orders the products (the hypergraph form never builds P_V P_E).
+    ``degree`` is delta(v) (reading R7).
+    """
+
+    def __init__(self, topo: dict):
+        self.kind = topo["kind"]
+        n = self.n = int(topo["n"])
+        if self.kind == "hypergraph":
+            H = incidence_from_csr(n, topo["he_ptr"], topo["he_nodes"])
+            dV = np.asarray(H.sum(axis=0)).ravel()   # delta(v): incident hyperedges
+            dE = np.asarray(H.sum(axis=1)).ravel()   # |e|
+            self.P_V = sp.diags(_inv_or_zero(dV)) @ H.T.tocsr()   # D_V^{-1} H^T
+            self.P_E = sp.diags(_inv_or_zero(dE)) @ H              # D_E^{-1} H
+            self.degree = dV
+        elif self.kind in ("graph", "multiplex"):
+            layers = topo["layers"]
+            directed = bool(topo.get("directed", False))
+            mats, deg = [], np.zeros(n)
+            for row_ptr, col in layers:
+                A = adjacency_from_csr(n, row_ptr, col, directed)
+                d = np.asarray(A.sum(axis=1)).ravel()
+                deg += d
+                mats.append(sp.diags(_inv_or_zero(d)) @ A)        # D_l^{-1} A_l
+            L = len(mats)
+            PN = mats[0]
+            for M in mats[1:]:
+                PN = PN + M
+            self.P_N = (PN * (1.0 / L)).tocsr() if L > 1 else PN.tocsr()
+            self.degree = deg
+        else:
+            raise ValueError(self.kind)
+
+    def apply(self, Q):
+        if self.kind == "hypergraph":
+            return self.P_V @ (self.P_E @ Q)          # Eq. (zt): P_V (P_E Q)
+        return self.P_N @ Q
+
+    def apply_T(self, Q):
+        if self.kind == "hypergraph":
+            return self.P_E.T @ (self.P_V.T @ Q)      # (Pi P_V) P_E, transposed
+        return self.P_N.T @ Q
+
+    def dense(self):
+        if self.kind == "hypergraph":
+            return (self.P_V @ self.P_E).toarray()
+        return self.P_N.toarray()
+
+
+def beta_vector(X, degree, beta, D_K):
+    """beta_i of Eq. (beta_i) with reading R3 for a non-positive KNN degree."""
+    X = np.asarray(X, F64)
+    zero_row = ~np.any(X != 0, axis=1)
+    b = np.full(X.shape[0], float(beta))
+    b[degree == 0] = 1.0
+    b[zero_row] = 0.0
+    b[D_K <= 0] = 0.0
+    return b
+
+
+class WalkOperator:
+    """P = (I - B) P_N + B P_K of Eq. (p-mat-ancka), applied as Eq. (zt)."""
+
+    def __init__(self, topo: Topology, P_K, b):
+        self.topo, self.P_K, self.b = topo, P_K, b
+
+    def apply(self, Q):
+        return (1.0 - self.b)[:, None] * self.topo.apply(Q) + self.b[:, None] * (self.P_K @ Q)
+
+    def dense(self):
+        return (1.0 - self.b)[:, None] * self.topo.dense() + self.b[:, None] * self.P_K.toarray()
+
+
+# ----------------------------------------------------------------------------
+# Section 4: BCM matrices
+# ----------------------------------------------------------------------------
+def bcm(labels, k):
+    """Binary cluster membership Y of Eq. (y)."""
+    n = labels.size
+    Y = np.zeros((n, k))
+    Y[np.arange(n), labels] = 1.0
+    return Y
+
+
+def h_norm(labels, k):
+    """h(Y) = (Y^T Y)^{-1/2} Y of Eq. (norm-y); empty cluster -> zero column (R12)."""
+    c = np.bincount(labels, minlength=k).astype(F64)
+    Y = bcm(labels, k)
+    return Y * _inv_sqrt_or_zero(c)[None, :]
+
+
+def _inv_sqrt_or_zero(c):
+    out = np.zeros_like(c)
+    nz = c > 0
+    out[nz] = 1.0 / np.sqrt(c[nz])
+    return out
+
+
+def argmax_rows(M):
+    """Row argmax with ties to the lowest column (R6); np.argmax does that."""
+    return np.argmax(M, axis=1).astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 4, lines 3-11: InitBCM
+# ----------------------------------------------------------------------------
+def centre_nodes(degree, k):
+    """V_c: the k largest-degree nodes (degree desc, id asc), sorted by id (R7)."""
+    order = np.lexsort((np.arange(degree.size), -degree))
+    return np.sort(order[:k])
+
+
+def init_bcm(topo: Topology, k, alpha, T_i):
+    """Pi^(t) = (1 - alpha) Pi^(t-1) P_N + alpha Z_0; g(v) = argmax_l Pi[l, v].
+
+    Pi is k x n; it is carried transposed (n x k) so Pi P_N becomes P_N^T Pi^T.
+    Returns (labels, V_c, Pi^T).
+    """
+    n = topo.n
+    Vc = centre_nodes(topo.degree, k)
+    Z0T = np.zeros((n, k))
+    Z0T[Vc, np.arange(k)] = 1.0
+    Pi0 = alpha * Z0T
+    Pi = Pi0.copy()
+    for _ in range(T_i):
+        Pi = (1.0 - alpha) * topo.apply_T(Pi) + Pi0
+    return argmax_rows(Pi), Vc, Pi
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1 / 4: QR step and Discretize
+# ----------------------------------------------------------------------------
+def qr_pos(Z):
+    """Householder QR (LAPACK) with diag(R) > 0 (reading R10)."""
+    Q, R = np.linalg.qr(Z)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s[None, :], R * s[:, None]
+
+
+def discretize(Qk, max_iter=20, return_trace=False):
+    """Discretize of Definition 2 / Algorithm 5 (readings R5, R6).
+
+    Qk is n x k (the eigenvector block without the constant column).
+    Returns the last labels Y (as an int vector) and, optionally, the trace of
+    objective values and the final rotation.
+    """
+    Qk = np.asarray(Qk, F64)
+    n, k = Qk.shape
+    nrm = np.sqrt(np.einsum("ij,ij->i", Qk, Qk))
+    Qt = Qk * _inv_or_zero(nrm)[:, None]             # row-normalised Q~
+    R = np.eye(k)
+    obj_prev = None
+    objs = []
+    labels = None
+    for _ in range(max_iter):
+        labels = argmax_rows(Qt @ R)                 # Eq. (updateY)
+        c = np.bincount(labels, minlength=k).astype(F64)
+        Yt = bcm(labels, k) * _inv_or_zero(c)[None, :]   # column-normalised Y~
+        M = Yt.T @ Qt                                # Y~^T Q~  (k x k)
+        U, Om, Vt = np.linalg.svd(M)                 # Eq. (svd-in-discr)
+        R = Vt.T @ U.T                               # R = V U^T
+        obj = n - 2.0 * Om.sum()
+        objs.append(obj)
+        if obj_prev is not None and abs(obj - obj_prev) <= 4 * EPS * max(1.0, abs(obj)):
+            break
+        obj_prev = obj
+    if return_trace:
+        return labels, objs, R
+    return labels
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 2 / Eq. (mhc-comp-ancka): multi-hop conductance
+# ----------------------------------------------------------------------------
+def cal_mhc(P: WalkOperator, labels, k, alpha, gamma):
+    """phi = 1 - (1/k) tr(Yh^T F^(gamma)), F^(l) = (1-alpha) P F^(l-1) + F^(0)."""
+    Yh = h_norm(labels, k)
+    F0 = alpha * Yh
+    F = F0
+    for _ in range(gamma):
+        F = (1.0 - alpha) * P.apply(F) + F0
+    return 1.0 - np.einsum("ij,ij->", Yh, F) / k
+
+
+def mhc_from_definition(S_dense, labels, k):
+    """Phi of Eq. (mh-cond) evaluated from a dense S (small n only)."""
+    total = 0.0
+    for c in range(k):
+        members = np.nonzero(labels == c)[0]
+        if members.size == 0:
+            continue
+        outside = np.ones(labels.size, bool)
+        outside[members] = False
+        total += S_dense[np.ix_(members, outside)].sum() / members.size
+    return total / k
+
+
+def multi_hop_dense(P_dense, alpha, gamma):
+    """S = alpha sum_{l=0..gamma} (1 - alpha)^l P^l of Eq. (approx-multi-hop)."""
+    n = P_dense.shape[0]
+    S = np.zeros((n, n))
+    Pl = np.eye(n)
+    for l in range(gamma + 1):
+        S += alpha * (1.0 - alpha) ** l * Pl
+        Pl = Pl @ P_dense
+    return S
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 4 end to end
+# ----------------------------------------------------------------------------
+def build_walk(topo_dict, X, K, beta, knn=None):
+    """Alg. 4 lines 1-2: P_K from the KNN lists and P_N from the topology."""
+    topo = Topology(topo_dict)
+    if knn is None:
+        idx, _ = knn_cosine(X, K)
+    else:
+        idx = np.asarray(knn, np.int64)
+    A_K = knn_adjacency(X, idx)
+    P_K, D_K = knn_transition(A_K)
+    b = beta_vector(X, topo.degree, beta, D_K)
+    return WalkOperator(topo, P_K, b), idx
+
+
+def ancka(topo_dict, X, params=None, knn=None, init_labels=None):
+    """Algorithm 4 (ANCKA) in FP64 with the fixed schedule of reading R9.
+
+    Returns a dict with the labels, the final Q (n x (k+1)), the InitBCM
+    labels, the phi trace and the Discretize inner-iteration counts.
+    """
+    p = dict(DEFAULTS)
+    if params:
+        p.update(params)
+    k, alpha, T, tau, gamma = p["k"], p["alpha"], p["T"], p["tau"], p["gamma"]
+    P, idx = build_walk(topo_dict, X, p["K"], p["beta"], knn)
+    n = P.topo.n
+    if init_labels is None:
+        y0, Vc, _ = init_bcm(P.topo, k, alpha, p["T_i"])
+    else:
+        y0, Vc = np.asarray(init_labels, np.int64), None
+    Y_best = y0.copy()
+    phi_best = cal_mhc(P, y0, k, alpha, gamma)       # reading R8
+    Q = np.concatenate([np.full((n, 1), 1.0 / np.sqrt(n)), h_norm(y0, k)], axis=1)
+    phis = [phi_best]
+    disc_iters = []
+    taken = []
+    t_run = 0
+    for t in range(1, T + 1):
+        Q_prev = Q
+        Z = P.apply(Q)                                # Eq. (zt)
+        Q, _ = qr_pos(Z)
+        t_run = t
+        if t % tau == 0 or t == T:
+            y_t, objs, _ = discretize(Q[:, 1:], p["disc_max_iter"], return_trace=True)
+            disc_iters.append(len(objs))
+            phi_t = cal_mhc(P, y_t, k, alpha, gamma)
+            phis.append(phi_t)
+            take = phi_t < phi_best
+            taken.append(bool(take))
+            if take:
+                Y_best, phi_best = y_t, phi_t
+            if p["early_stop"]:
+                conv = np.linalg.norm(Q - Q_prev) < p["eps_Q"]          # Eq. (tcond-1)
+                rising = len(phis) >= 3 and phis[-3] < phis[-2] < phis[-1]  # Eq. (tcond-2)
+                if conv or rising:
+                    break
+    return dict(labels=Y_best.astype(np.int64), Q=Q, init_labels=y0, centres=Vc,
+                phi=np.array(phis), phi_best=phi_best, disc_iters=disc_iters,
+                taken=taken, iters=t_run, knn_idx=idx)
+
+
+# ----------------------------------------------------------------------------
+# evaluation helpers
+# ----------------------------------------------------------------------------
+def adjusted_rand_index(a, b):
+    """Hubert-Arabie adjusted Rand index of two labelings."""
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    _, ai = np.unique(a, return_inverse=True)
+    _, bi = np.unique(b, return_inverse=True)
+    C = sp.coo_matrix((np.ones(a.size), (ai, bi))).toarray()
+
+    def comb2(x):
+        return x * (x - 1) / 2.0
+
+    s_ij = comb2(C).sum()
+    s_a = comb2(C.sum(axis=1)).sum()
+    s_b = comb2(C.sum(axis=0)).sum()
+    total = comb2(float(a.size))
+    expected = s_a * s_b / total if total > 0 else 0.0
+    max_idx = 0.5 * (s_a + s_b)
+    if max_idx == expected:
+        return 1.0
+    return (s_ij - expected) / (max_idx - expected)
+
+
+def max_principal_angle(A, B):
+    """Largest principal angle between span(A) and span(B) (arcsin form)."""
+    Qa, _ = np.linalg.qr(np.asarray(A, F64))
+    Qb, _ = np.linalg.qr(np.asarray(B, F64))
+    resid = Qb - Qa @ (Qa.T @ Qb)
+    s = np.linalg.norm(resid, 2)
+    return float(np.arcsin(min(1.0, s)))
