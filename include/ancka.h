@@ -1,0 +1,202 @@
+/*
+ * ancka.h -- C ABI of the GB300 (sm_103a) ANCKA hot path.
+ *
+ * ANCKA (attributed network clustering, arXiv 2408.05459) clusters the nodes
+ * of an attributed graph, hypergraph or multiplex graph into k groups:
+ *   1. KNN augmentation (Section 3.1, Eq. AK): for every node the K most
+ *      cosine-similar other nodes by attributes, giving the KNN graph A_K and
+ *      its walk matrix P_K = D_K^-1 A_K;
+ *   2. the augmented walk P = (I - B) P_N + B P_K (Eq. p-mat-ancka) with P_N
+ *      from Eq. rw-hg (hypergraph), rw-ag (graph) or rw-mg (multiplex) and
+ *      B = diag(beta_i) (Eq. beta_i);
+ *   3. Algorithm 4: InitBCM, T orthogonal iterations Z = P Q, QR, and every
+ *      tau iterations Discretize (Def. 2, Alg. 5) + CalMHC (Alg. 2), keeping
+ *      the labels with the lowest multi-hop conductance.
+ *
+ * Conventions for every entry point
+ *   - Pointers are DEVICE pointers of the current CUDA device unless the
+ *     function name ends in _host.  The caller owns every input and output
+ *     buffer; the library allocates its own workspace with stream-ordered
+ *     cudaMallocAsync on `stream` and frees it before returning.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Matrices are row-major and dense unless stated; int32 node ids.
+ *   - Inputs are validated on the host before any launch; a bad argument
+ *     returns ANCKA_ERR_INVALID_ARG and launches nothing.
+ *   - When `info` is non-NULL the call synchronises `stream` before
+ *     returning and fills it; with info == NULL the call only enqueues work.
+ *   - No exceptions cross this interface; ancka_last_error() gives a
+ *     human-readable message for the last failing call of this thread.
+ *   - Requires a device of compute capability 10.3 (GB300); other devices
+ *     give ANCKA_ERR_UNSUPPORTED.  There is no CPU fallback.
+ */
+#ifndef ANCKA_H_
+#define ANCKA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ANCKA_OK = 0,
+  ANCKA_ERR_INVALID_ARG = 1,   /* argument out of range / inconsistent sizes */
+  ANCKA_ERR_OOM = 2,           /* device workspace allocation failed */
+  ANCKA_ERR_CUDA = 3,          /* a CUDA runtime call or kernel failed */
+  ANCKA_ERR_NUMERIC = 4,       /* Cholesky of a singular Gram matrix (rank-deficient Z) */
+  ANCKA_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
+  ANCKA_ERR_UNSUPPORTED = 6,   /* device is not sm_103 or option not available */
+  ANCKA_ERR_INTERNAL = 7
+} ancka_status;
+
+/* Arithmetic of the KNN similarity contraction (step 1).  Every choice
+ * returns the exact KNN lists of Section 3.1: candidates found in the low
+ * precision are re-ranked with a compensated FP32 dot product and rows whose
+ * candidate set cannot be certified are recomputed exhaustively. */
+typedef enum {
+  ANCKA_PREC_FP32 = 0,  /* CUDA-core FP32 contraction */
+  ANCKA_PREC_BF16 = 1,  /* tcgen05 BF16 x BF16 -> FP32 (TMEM) contraction */
+  ANCKA_PREC_FP8 = 2    /* reserved: FP8 e4m3 contraction */
+} ancka_prec;
+
+typedef enum { ANCKA_GRAPH = 0, ANCKA_HYPERGRAPH = 1, ANCKA_MULTIPLEX = 2 } ancka_topo_kind;
+
+/* Network topology N_O (Section 2).
+ *   graph / multiplex: L adjacency layers in CSR form.  Layer l's row pointer
+ *     is row_ptr + l*(n+1) (L*(n+1) int64 in total); its entries are
+ *     col_idx[row_ptr[l*(n+1)+i] .. row_ptr[l*(n+1)+i+1]) with offsets into
+ *     the single col_idx array (length nnz).  A graph has L = 1.  With
+ *     directed = 0 each layer is read as an undirected adjacency (both
+ *     directions present); with directed = 1 reversed edges are added
+ *     (Eq. rw-ag).  Repeated entries count once (A is binary).
+ *   hypergraph: m hyperedges, members of e at he_nodes[he_ptr[e] .. he_ptr[e+1])
+ *     (nnz = he_ptr[m]); repeated members count once.
+ * Node ids must lie in [0, n). */
+typedef struct {
+  int32_t kind;             /* ancka_topo_kind */
+  int32_t L;                /* number of layers (graph: 1) */
+  int64_t n;                /* number of nodes */
+  const int64_t* row_ptr;   /* graph/multiplex: L*(n+1) */
+  const int32_t* col_idx;   /* graph/multiplex: nnz */
+  int64_t nnz;              /* graph/multiplex: length of col_idx */
+  int32_t directed;         /* graph/multiplex: 1 = symmetrise */
+  int32_t pad_;
+  int64_t m;                /* hypergraph: number of hyperedges */
+  const int64_t* he_ptr;    /* hypergraph: m+1 */
+  const int32_t* he_nodes;  /* hypergraph: he_ptr[m] */
+} ancka_topology;
+
+/* Parameters of Algorithm 4 (defaults from the method's settings, Section 8.1). */
+typedef struct {
+  int32_t k;             /* clusters, 1 <= k <= 64 (default 5) */
+  int32_t K;             /* KNN neighbours, 1 <= K <= 64, K < n (default 10) */
+  float alpha;           /* walk stopping probability (0.2) */
+  float beta;            /* KNN mixing weight of Eq. beta_i (0.5) */
+  int32_t T;             /* orthogonal iterations T_a (10) */
+  int32_t gamma;         /* CalMHC hops (3) */
+  int32_t T_i;           /* InitBCM hops (25) */
+  int32_t tau;           /* Discretize / CalMHC interval (5) */
+  int32_t disc_max_iter; /* Discretize inner iterations (20) */
+  int32_t knn_prec;      /* ancka_prec (ANCKA_PREC_BF16) */
+  int32_t init;          /* 0 = InitBCM, 1 = labels in init_labels (device, n int32) */
+  int32_t pad_;
+  const int32_t* init_labels;
+} ancka_params;
+
+/* Optional device outputs (any field may be NULL). */
+typedef struct {
+  float* Q;              /* n x (k+1) row-major: the final orthonormal block Q^(T) */
+  int32_t* init_labels;  /* n: InitBCM labels Y^(0) */
+  int32_t* knn_idx;      /* n x K: KNN lists */
+  float* knn_sim;        /* n x K: their cosine similarities */
+} ancka_outputs;
+
+#define ANCKA_MAX_TRACE 64
+
+/* Diagnostics filled when a non-NULL pointer is passed (the call then syncs). */
+typedef struct {
+  int64_t knn_candidates;      /* (row, candidate) pairs re-ranked exactly */
+  int64_t knn_fallback_rows;   /* rows whose candidates could not be certified */
+  int32_t iters_run;           /* orthogonal iterations executed */
+  int32_t n_phi;               /* entries of phi[] used: phi(Y0), then one per Discretize */
+  double phi[ANCKA_MAX_TRACE];
+  int32_t disc_iters[ANCKA_MAX_TRACE]; /* Discretize inner iterations per call */
+  int32_t taken[ANCKA_MAX_TRACE];      /* 1 if that Discretize result became the kept Y */
+  double phi_best;
+  int32_t numeric_flags;       /* bit0: empty cluster seen in Discretize; bit1: SVD sweep limit hit */
+  int32_t pad_;
+  float ms_knn;                /* normalise + contraction + re-rank + fallback */
+  float ms_build;              /* A_K, P_K, beta, P_N structures */
+  float ms_init;               /* InitBCM + Q^(0) + phi(Y0) */
+  float ms_iter;               /* SpMM + CholeskyQR2 over all iterations */
+  float ms_disc;               /* all Discretize calls */
+  float ms_mhc;                /* all CalMHC calls and the keep-best step */
+  float ms_total;
+  float ms_contract;           /* the candidate similarity contraction kernel alone */
+} ancka_info;
+
+/* Fill *p with the defaults above. */
+void ancka_params_default(ancka_params* p);
+
+/* Static name of a status code. */
+const char* ancka_status_str(ancka_status s);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* ancka_last_error(void);
+
+/* ANCKA_OK if the current device is an sm_103 part this library was built for. */
+ancka_status ancka_device_check(void);
+
+/* Number of this library's own CUDA kernels launched by the calling process
+ * so far (a diagnostics counter; the kernels inside the one-off CUB sorts and
+ * scans of the graph build are not counted). */
+int64_t ancka_kernel_launches(void);
+
+/* KNN lists of Section 3.1 (Eq. AK inputs).
+ *   X        n x d FP32 attributes (device, row-major, any values; a zero row
+ *            has similarity 0 to everything)
+ *   out_idx  n x K int32: N_K(v_i) ordered by (cosine desc, index asc), i excluded
+ *   out_sim  n x K FP32: the cosines, correctly rounded from a compensated
+ *            (double-FP32) evaluation
+ *   prec     ancka_prec of the candidate contraction (FP32 or BF16)
+ * Requires 1 <= K <= 64, K < n, 1 <= d <= 4096, n < 2^31. */
+ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
+                       int32_t* out_idx, float* out_sim, ancka_info* info, void* stream);
+
+/* Algorithm 4 end to end: labels[i] in [0, k) for every node.
+ *   topo   topology with device pointers
+ *   X      n x d FP32 attributes (device)
+ *   labels n int32 output (device)
+ *   out    optional extra outputs (device buffers), may be NULL */
+ancka_status ancka_cluster(const ancka_topology* topo, const float* X, int32_t d,
+                           const ancka_params* p, int32_t* labels, const ancka_outputs* out,
+                           ancka_info* info, void* stream);
+
+/* As ancka_cluster but with the KNN lists supplied (n x K int32 indices and
+ * their FP32 cosines); X is still read for Eq. beta_i's zero-row test. */
+ancka_status ancka_cluster_with_knn(const ancka_topology* topo, const float* X, int32_t d,
+                                    const int32_t* knn_idx, const float* knn_sim,
+                                    const ancka_params* p, int32_t* labels,
+                                    const ancka_outputs* out, ancka_info* info, void* stream);
+
+/* ancka_cluster on HOST buffers: topo, X and labels are host pointers (pinned
+ * or pageable); the call copies inputs to the device, runs, copies labels
+ * back and synchronises. `out` must be NULL. */
+ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int32_t d,
+                                const ancka_params* p, int32_t* labels, ancka_info* info,
+                                void* stream);
+
+/* Discretize (Definition 2, Algorithm 5) of an n x k block.
+ *   Qk      n x k FP32 with leading dimension ldq >= k (device)
+ *   labels  n int32 output: the last Y of the alternation
+ *   iters   host int32 out (may be NULL): inner iterations executed
+ * R starts at I; stops when |obj - obj_prev| <= 4 eps max(1,|obj|) or after
+ * max_iter iterations.  The k x k SVD runs in FP64. 1 <= k <= 64. */
+ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq,
+                              int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANCKA_H_ */

@@ -1,0 +1,539 @@
+// C ABI of the ANCKA hot path: validation, workspace, phase sequencing.
+#include <atomic>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace ancka {
+
+namespace {
+thread_local char g_err[512] = "";
+std::atomic<int64_t> g_launches{0};
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+ancka_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  return e == cudaErrorMemoryAllocation ? ANCKA_ERR_OOM : ANCKA_ERR_CUDA;
+}
+
+namespace {
+
+#define ANCKA_REQUIRE(cond, ...)            \
+  do {                                      \
+    if (!(cond)) {                          \
+      ::ancka::set_error(__VA_ARGS__);      \
+      return ANCKA_ERR_INVALID_ARG;         \
+    }                                       \
+  } while (0)
+
+ancka_status device_check() {
+  int dev = 0;
+  ANCKA_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static int checked[64] = {0};  // 0 unknown, 1 ok, 2 bad
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && checked[dev] == 0) {
+    int major = 0, minor = 0;
+    ANCKA_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    ANCKA_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    checked[dev] = (major == 10 && minor == 3) ? 1 : 2;
+    if (checked[dev] == 1) {
+      // keep freed workspace in the stream-ordered pool between calls
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+    }
+  }
+  if (dev >= 64 || checked[dev] != 1) {
+    set_error("device %d is not a compute capability 10.3 (GB300) device", dev);
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  return ANCKA_OK;
+}
+
+struct Timer {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ph;
+};
+
+struct Phase {
+  Timer* t;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  int phase;
+  Phase(Timer* tt, cudaStream_t st, int p) : t(tt), s(st), phase(p) {
+    if (t) {
+      cudaEventCreate(&a);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Phase() {
+    if (t) {
+      cudaEvent_t b;
+      cudaEventCreate(&b);
+      cudaEventRecord(b, s);
+      t->ev.push_back(a);
+      t->ev.push_back(b);
+      t->ph.push_back(phase);
+    }
+  }
+};
+
+void fill_times(Timer& t, ancka_info* info) {
+  float acc[8] = {0};
+  for (size_t q = 0; q < t.ph.size(); ++q) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.ev[2 * q], t.ev[2 * q + 1]) == cudaSuccess && t.ph[q] < 8) acc[t.ph[q]] += ms;
+  }
+  for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+  t.ev.clear();
+  if (info) {
+    info->ms_knn = acc[0];
+    info->ms_build = acc[1];
+    info->ms_init = acc[2];
+    info->ms_iter = acc[3];
+    info->ms_disc = acc[4];
+    info->ms_mhc = acc[5];
+  }
+}
+
+__global__ void k_zero_rows(const float* __restrict__ X, int64_t n, int d, int32_t* __restrict__ z) {
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  bool any = false;
+  for (int c = lane; c < d; c += 32) any |= X[row * d + c] != 0.f;
+  any = __any_sync(0xffffffffu, any);
+  if (lane == 0) z[row] = any ? 0 : 1;
+}
+
+__global__ void k_check_knn(const int32_t* __restrict__ idx, int64_t n, int K, int32_t* __restrict__ bad) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * K) return;
+  const int32_t j = idx[q];
+  if (j < 0 || j >= n || j == (int32_t)(q / K)) atomicExch(bad, 1);
+}
+
+__global__ void k_check_labels(const int32_t* __restrict__ y, int64_t n, int k, int32_t* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (y[i] < 0 || y[i] >= k)) atomicExch(bad, 1);
+}
+
+ancka_status read_flag(const int32_t* dev, cudaStream_t s, int32_t* host) {
+  ANCKA_CUDA(cudaMemcpyAsync(host, dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  return ANCKA_OK;
+}
+
+ancka_status validate_knn_args(const float* X, int64_t n, int32_t d, int32_t K, int32_t prec) {
+  ANCKA_REQUIRE(X != nullptr, "X is NULL");
+  ANCKA_REQUIRE(n >= 2 && n < (int64_t(1) << 31) - 1, "n = %lld out of range [2, 2^31-1)", (long long)n);
+  ANCKA_REQUIRE(d >= 1 && d <= 4096, "d = %d out of range [1, 4096]", d);
+  ANCKA_REQUIRE(K >= 1 && K <= 64 && K < n, "K = %d must satisfy 1 <= K <= 64 and K < n", K);
+  ANCKA_REQUIRE(prec == ANCKA_PREC_FP32 || prec == ANCKA_PREC_BF16 || prec == ANCKA_PREC_FP8,
+                "unknown precision %d", prec);
+  if (prec == ANCKA_PREC_FP8) {
+    set_error("FP8 contraction is not available in this build");
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  if (prec == ANCKA_PREC_BF16 && !knn_tc_available()) {
+    set_error("BF16 tensor-core contraction is not available in this build");
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  return ANCKA_OK;
+}
+
+// the KNN lists with every step on the device
+ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
+                      int32_t* idx, float* sim, int32_t** zero_row, int64_t* ncand, int64_t* nfb,
+                      bool counts, cudaStream_t s, cudaEvent_t* contract_ev = nullptr) {
+  PrepOut pr;
+  ANCKA_TRY(prep_rows(ws, X, n, d, prec, &pr, s));
+  if (zero_row) *zero_row = pr.zero_row;
+  // the candidate list certifies K when a few slots of slack remain
+  if (K <= kCandC / 2) {
+    float* cv;
+    int32_t* ci;
+    ANCKA_TRY(ws.alloc(&cv, (size_t)n * kCandC));
+    ANCKA_TRY(ws.alloc(&ci, (size_t)n * kCandC));
+    float acc;
+    if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[0], s));
+    if (prec == ANCKA_PREC_BF16) {
+      ANCKA_TRY(knn_candidates_bf16(pr, n, cv, ci, s));
+      // tensor-core FP32 accumulation: a few units in the last place per
+      // 16-wide MMA step (bound validated against exact products in tests)
+      acc = (float)((pr.dp / 16 + 2) * 2.384185791015625e-07);  // 2^-22 per step
+    } else {
+      ANCKA_TRY(knn_candidates_fp32(pr, n, cv, ci, s));
+      // sequential FMA accumulation over dp terms: gamma_dp with u = 2^-24
+      const double g = pr.dp * 5.960464477539063e-08;
+      acc = (float)(1.01 * g / (1.0 - g));
+    }
+    if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, acc, cv, ci, idx, sim, ncand, nfb, counts, s));
+  } else {
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, 0.f, nullptr, nullptr, idx, sim, ncand, nfb, counts, s));
+  }
+  return ANCKA_OK;
+}
+
+ancka_status validate_topology(const ancka_topology* t) {
+  ANCKA_REQUIRE(t != nullptr, "topology is NULL");
+  ANCKA_REQUIRE(t->n >= 2 && t->n < (int64_t(1) << 31) - 1, "topology n out of range");
+  if (t->kind == ANCKA_HYPERGRAPH) {
+    ANCKA_REQUIRE(t->m >= 1 && t->m < (int64_t(1) << 31) - 1, "hypergraph needs 1 <= m < 2^31");
+    ANCKA_REQUIRE(t->he_ptr && t->he_nodes, "hypergraph pointers are NULL");
+  } else if (t->kind == ANCKA_GRAPH || t->kind == ANCKA_MULTIPLEX) {
+    ANCKA_REQUIRE(t->L >= 1 && t->L <= 64, "layers L = %d out of range [1, 64]", t->L);
+    ANCKA_REQUIRE(t->kind == ANCKA_MULTIPLEX || t->L == 1, "a graph has exactly one layer");
+    ANCKA_REQUIRE(t->row_ptr && (t->col_idx || t->nnz == 0), "graph pointers are NULL");
+  } else {
+    ANCKA_REQUIRE(false, "unknown topology kind %d", t->kind);
+  }
+  return ANCKA_OK;
+}
+
+ancka_status validate_params(const ancka_params* p, int64_t n) {
+  ANCKA_REQUIRE(p != nullptr, "params is NULL");
+  ANCKA_REQUIRE(p->k >= 1 && p->k <= 64 && p->k <= n, "k = %d must satisfy 1 <= k <= min(64, n)", p->k);
+  ANCKA_REQUIRE(p->alpha > 0.f && p->alpha <= 1.f, "alpha must lie in (0, 1]");
+  ANCKA_REQUIRE(p->beta >= 0.f && p->beta <= 1.f, "beta must lie in [0, 1]");
+  ANCKA_REQUIRE(p->T >= 1 && p->tau >= 1, "T and tau must be >= 1");
+  ANCKA_REQUIRE(p->gamma >= 0 && p->T_i >= 0, "gamma and T_i must be >= 0");
+  ANCKA_REQUIRE(p->disc_max_iter >= 1 && p->disc_max_iter <= 1000, "disc_max_iter out of range");
+  ANCKA_REQUIRE(p->T / p->tau + 2 <= ANCKA_MAX_TRACE, "T / tau too large for the trace");
+  ANCKA_REQUIRE(p->init == 0 || (p->init == 1 && p->init_labels), "init must be 0 or 1 with init_labels");
+  return ANCKA_OK;
+}
+
+ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d, const int32_t* knn_idx_in,
+                          const float* knn_sim_in, const ancka_params* p, int32_t* labels,
+                          const ancka_outputs* out, ancka_info* info, cudaStream_t s) {
+  ANCKA_TRY(device_check());
+  ANCKA_TRY(validate_topology(topo));
+  const int64_t n = topo->n;
+  ANCKA_TRY(validate_params(p, n));
+  ANCKA_REQUIRE(labels != nullptr, "labels is NULL");
+  if (!knn_idx_in) {
+    ANCKA_TRY(validate_knn_args(X, n, d, p->K, p->knn_prec));
+  } else {
+    ANCKA_REQUIRE(X && knn_sim_in && d >= 1 && p->K >= 1 && p->K < n, "bad KNN inputs");
+  }
+  if (info) memset(info, 0, sizeof(*info));
+  Timer timer;
+  Timer* tp = info ? &timer : nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaEvent_t cev[2] = {nullptr, nullptr};
+  bool contract_timed = false;
+  if (info) {
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventCreate(&cev[0]);
+    cudaEventCreate(&cev[1]);
+    cudaEventRecord(t0, s);
+  }
+  ancka_status st = ANCKA_OK;
+  {
+    Workspace ws(s);
+    const int K = p->K;
+    int32_t* idx = (out && out->knn_idx) ? out->knn_idx : nullptr;
+    float* sim = (out && out->knn_sim) ? out->knn_sim : nullptr;
+    int32_t* zero_row = nullptr;
+    int64_t ncand = 0, nfb = 0;
+    int32_t* bad;
+    st = ws.zeros(&bad, 1);
+    if (st == ANCKA_OK && !knn_idx_in) {
+      Phase ph(tp, s, 0);
+      if (!idx) st = ws.alloc(&idx, (size_t)n * K);
+      if (st == ANCKA_OK && !sim) st = ws.alloc(&sim, (size_t)n * K);
+      if (st == ANCKA_OK)
+        st = knn_impl(ws, X, n, d, K, p->knn_prec, idx, sim, &zero_row, &ncand, &nfb, info != nullptr, s,
+                      info && K <= kCandC / 2 ? cev : nullptr);
+      contract_timed = info && K <= kCandC / 2;
+    } else if (st == ANCKA_OK) {
+      Phase ph(tp, s, 0);
+      k_check_knn<<<(unsigned)ceil_div(n * K, 256), 256, 0, s>>>(knn_idx_in, n, K, bad);
+      int32_t hb = 0;
+      st = read_flag(bad, s, &hb);
+      if (st == ANCKA_OK && hb) {
+        set_error("KNN list entry out of range or equal to its own row");
+        st = ANCKA_ERR_INVALID_ARG;
+      }
+      if (st == ANCKA_OK) st = ws.alloc(&zero_row, (size_t)n);
+      if (st == ANCKA_OK) {
+        k_zero_rows<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(X, n, d, zero_row);
+        if (cudaGetLastError() != cudaSuccess) st = ANCKA_ERR_CUDA;
+      }
+      if (st == ANCKA_OK && out && out->knn_idx)
+        cudaMemcpyAsync(out->knn_idx, knn_idx_in, sizeof(int32_t) * n * K, cudaMemcpyDeviceToDevice, s);
+      if (st == ANCKA_OK && out && out->knn_sim)
+        cudaMemcpyAsync(out->knn_sim, knn_sim_in, sizeof(float) * n * K, cudaMemcpyDeviceToDevice, s);
+      idx = const_cast<int32_t*>(knn_idx_in);
+      sim = const_cast<float*>(knn_sim_in);
+    }
+    if (st == ANCKA_OK && p->init == 1) {
+      k_check_labels<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(p->init_labels, n, p->k, bad);
+      int32_t hb = 0;
+      st = read_flag(bad, s, &hb);
+      if (st == ANCKA_OK && hb) {
+        set_error("init_labels entry outside [0, k)");
+        st = ANCKA_ERR_INVALID_ARG;
+      }
+    }
+    Walk w;
+    if (st == ANCKA_OK) {
+      Phase ph(tp, s, 1);
+      st = build_topology(ws, *topo, &w, s);
+      if (st == ANCKA_OK) st = build_knn_part(ws, n, K, idx, sim, zero_row, p->beta, &w, s);
+    }
+    IterTrace tr{};
+    if (st == ANCKA_OK) {
+      st = ws.zeros(&tr.phi_dev, ANCKA_MAX_TRACE);
+      if (st == ANCKA_OK) st = ws.zeros(&tr.disc_iters_dev, ANCKA_MAX_TRACE);
+      if (st == ANCKA_OK) st = ws.zeros(&tr.taken_dev, ANCKA_MAX_TRACE);
+      if (st == ANCKA_OK) st = ws.zeros(&tr.flags_dev, 1);
+      if (st == ANCKA_OK) st = ws.zeros(&tr.phi_best_dev, 1);
+    }
+    if (st == ANCKA_OK) {
+      tr.events = tp ? &timer.ev : nullptr;
+      tr.phases = tp ? &timer.ph : nullptr;
+      IterCfg cfg{p->k, p->T, p->gamma, p->T_i, p->tau, p->disc_max_iter, p->alpha};
+      st = run_ancka(ws, w, cfg, p->init == 1 ? p->init_labels : nullptr, labels, out ? out->Q : nullptr,
+                     out ? out->init_labels : nullptr, &tr, s);
+    }
+    if (info && (st == ANCKA_OK || st == ANCKA_ERR_NUMERIC)) {
+      cudaEventRecord(t1, s);
+      cudaMemcpyAsync(info->phi, tr.phi_dev, sizeof(double) * ANCKA_MAX_TRACE, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(info->disc_iters, tr.disc_iters_dev, sizeof(int32_t) * ANCKA_MAX_TRACE,
+                      cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(info->taken, tr.taken_dev, sizeof(int32_t) * ANCKA_MAX_TRACE, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(&info->numeric_flags, tr.flags_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(&info->phi_best, tr.phi_best_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess && st == ANCKA_OK) st = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+      info->n_phi = tr.n_phi;
+      info->iters_run = p->T;
+      info->knn_candidates = ncand;
+      info->knn_fallback_rows = nfb;
+    }
+  }  // workspace released (stream-ordered)
+  if (info) {
+    cudaStreamSynchronize(s);
+    fill_times(timer, info);
+    float tot = 0.f;
+    if (cudaEventElapsedTime(&tot, t0, t1) == cudaSuccess) info->ms_total = tot;
+    float mc = 0.f;
+    if (contract_timed && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaEventDestroy(cev[0]);
+    cudaEventDestroy(cev[1]);
+  }
+  if (st == ANCKA_OK) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "kernel launch", __FILE__, __LINE__);
+  }
+  return st;
+}
+
+}  // namespace
+}  // namespace ancka
+
+using namespace ancka;
+
+extern "C" {
+
+void ancka_params_default(ancka_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->k = 5;
+  p->K = 10;
+  p->alpha = 0.2f;
+  p->beta = 0.5f;
+  p->T = 10;
+  p->gamma = 3;
+  p->T_i = 25;
+  p->tau = 5;
+  p->disc_max_iter = 20;
+  p->knn_prec = ANCKA_PREC_BF16;
+  p->init = 0;
+  p->init_labels = nullptr;
+}
+
+const char* ancka_status_str(ancka_status s) {
+  switch (s) {
+    case ANCKA_OK: return "ANCKA_OK";
+    case ANCKA_ERR_INVALID_ARG: return "ANCKA_ERR_INVALID_ARG";
+    case ANCKA_ERR_OOM: return "ANCKA_ERR_OOM";
+    case ANCKA_ERR_CUDA: return "ANCKA_ERR_CUDA";
+    case ANCKA_ERR_NUMERIC: return "ANCKA_ERR_NUMERIC";
+    case ANCKA_ERR_TIMEOUT: return "ANCKA_ERR_TIMEOUT";
+    case ANCKA_ERR_UNSUPPORTED: return "ANCKA_ERR_UNSUPPORTED";
+    case ANCKA_ERR_INTERNAL: return "ANCKA_ERR_INTERNAL";
+  }
+  return "ANCKA_ERR_UNKNOWN";
+}
+
+const char* ancka_last_error(void) { return g_err; }
+
+ancka_status ancka_device_check(void) { return device_check(); }
+
+int64_t ancka_kernel_launches(void) { return g_launches.load(); }
+
+ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t prec, int32_t* out_idx,
+                       float* out_sim, ancka_info* info, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_TRY(validate_knn_args(X, n, d, K, prec));
+  ANCKA_REQUIRE(out_idx && out_sim, "output pointers are NULL");
+  if (info) memset(info, 0, sizeof(*info));
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (info) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  ancka_status st;
+  int64_t nc = 0, nf = 0;
+  cudaEvent_t cev[2] = {nullptr, nullptr};
+  const bool timed = info && K <= kCandC / 2;
+  if (timed) {
+    cudaEventCreate(&cev[0]);
+    cudaEventCreate(&cev[1]);
+  }
+  {
+    Workspace ws(s);
+    st = knn_impl(ws, X, n, d, K, prec, out_idx, out_sim, nullptr, &nc, &nf, info != nullptr, s,
+                  timed ? cev : nullptr);
+  }
+  if (info) {
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && st == ANCKA_OK) st = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    info->ms_knn = ms;
+    info->ms_total = ms;
+    info->knn_candidates = nc;
+    info->knn_fallback_rows = nf;
+    if (timed) {
+      float mc = 0.f;
+      if (cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;
+      cudaEventDestroy(cev[0]);
+      cudaEventDestroy(cev[1]);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  return st;
+}
+
+ancka_status ancka_cluster(const ancka_topology* topo, const float* X, int32_t d, const ancka_params* p,
+                           int32_t* labels, const ancka_outputs* out, ancka_info* info, void* stream) {
+  return cluster_impl(topo, X, d, nullptr, nullptr, p, labels, out, info, static_cast<cudaStream_t>(stream));
+}
+
+ancka_status ancka_cluster_with_knn(const ancka_topology* topo, const float* X, int32_t d,
+                                    const int32_t* knn_idx, const float* knn_sim, const ancka_params* p,
+                                    int32_t* labels, const ancka_outputs* out, ancka_info* info, void* stream) {
+  if (!knn_idx || !knn_sim) {
+    set_error("knn_idx / knn_sim are NULL");
+    return ANCKA_ERR_INVALID_ARG;
+  }
+  return cluster_impl(topo, X, d, knn_idx, knn_sim, p, labels, out, info, static_cast<cudaStream_t>(stream));
+}
+
+ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int32_t d, const ancka_params* p,
+                                int32_t* labels, ancka_info* info, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_TRY(validate_topology(topo));
+  ANCKA_REQUIRE(X && labels, "X or labels is NULL");
+  const int64_t n = topo->n;
+  ANCKA_TRY(validate_params(p, n));
+  ANCKA_REQUIRE(d >= 1 && d <= 4096, "d out of range");
+  ancka_topology dt = *topo;
+  ancka_status st = ANCKA_OK;
+  {
+    Workspace ws(s);
+    float* dX;
+    int32_t* dlab;
+    ANCKA_TRY(ws.alloc(&dX, (size_t)n * d));
+    ANCKA_TRY(ws.alloc(&dlab, (size_t)n));
+    ANCKA_CUDA(cudaMemcpyAsync(dX, X, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
+    if (topo->kind == ANCKA_HYPERGRAPH) {
+      const int64_t m = topo->m;
+      const int64_t nnz = topo->he_ptr[m];
+      int64_t* hp;
+      int32_t* hn;
+      ANCKA_TRY(ws.alloc(&hp, (size_t)m + 1));
+      ANCKA_TRY(ws.alloc(&hn, (size_t)(nnz > 0 ? nnz : 1)));
+      ANCKA_CUDA(cudaMemcpyAsync(hp, topo->he_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, s));
+      if (nnz > 0) ANCKA_CUDA(cudaMemcpyAsync(hn, topo->he_nodes, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s));
+      dt.he_ptr = hp;
+      dt.he_nodes = hn;
+    } else {
+      const int64_t np = (int64_t)topo->L * (n + 1);
+      int64_t* rp;
+      int32_t* ci;
+      ANCKA_TRY(ws.alloc(&rp, (size_t)np));
+      ANCKA_TRY(ws.alloc(&ci, (size_t)(topo->nnz > 0 ? topo->nnz : 1)));
+      ANCKA_CUDA(cudaMemcpyAsync(rp, topo->row_ptr, sizeof(int64_t) * np, cudaMemcpyHostToDevice, s));
+      if (topo->nnz > 0)
+        ANCKA_CUDA(cudaMemcpyAsync(ci, topo->col_idx, sizeof(int32_t) * topo->nnz, cudaMemcpyHostToDevice, s));
+      dt.row_ptr = rp;
+      dt.col_idx = ci;
+    }
+    ancka_params dp = *p;
+    int32_t* dinit = nullptr;
+    if (p->init == 1) {
+      ANCKA_TRY(ws.alloc(&dinit, (size_t)n));
+      ANCKA_CUDA(cudaMemcpyAsync(dinit, p->init_labels, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+      dp.init_labels = dinit;
+    }
+    st = cluster_impl(&dt, dX, d, nullptr, nullptr, &dp, dlab, nullptr, info, s);
+    if (st == ANCKA_OK) ANCKA_CUDA(cudaMemcpyAsync(labels, dlab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  }
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq, int32_t max_iter,
+                              int32_t* labels, int32_t* iters, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_REQUIRE(Qk && labels, "Qk or labels is NULL");
+  ANCKA_REQUIRE(n >= 1 && n < (int64_t(1) << 31) - 1, "n out of range");
+  ANCKA_REQUIRE(k >= 1 && k <= 64, "k = %d out of range [1, 64]", k);
+  ANCKA_REQUIRE(ldq >= k, "ldq < k");
+  ANCKA_REQUIRE(max_iter >= 1 && max_iter <= 1000, "max_iter out of range");
+  ancka_status st;
+  int32_t hit = 0;
+  {
+    Workspace ws(s);
+    int32_t* it;
+    ANCKA_TRY(ws.zeros(&it, 1));
+    st = discretize(ws, Qk, n, k, ldq, max_iter, labels, it, nullptr, s);
+    if (st == ANCKA_OK && iters) {
+      ANCKA_CUDA(cudaMemcpyAsync(&hit, it, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaStreamSynchronize(s));
+      *iters = hit;
+    }
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Shared device helpers and internal host interfaces of the ANCKA library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/ancka.h"
+
+namespace ancka {
+
+// ---------------------------------------------------------------------------
+// error plumbing (host)
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+ancka_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define ANCKA_CUDA(x)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (x);                                                    \
+    if (e_ != cudaSuccess) return ::ancka::cuda_fail(e_, #x, __FILE__, __LINE__); \
+  } while (0)
+
+void count_launch();
+#define ANCKA_LAUNCHED()            \
+  do {                              \
+    ::ancka::count_launch();        \
+    ANCKA_CUDA(cudaGetLastError()); \
+  } while (0)
+
+#define ANCKA_TRY(x)                               \
+  do {                                             \
+    ancka_status s_ = (x);                         \
+    if (s_ != ANCKA_OK) return s_;                 \
+  } while (0)
+
+// Stream-ordered workspace: every buffer is allocated with cudaMallocAsync on
+// the call's stream and released (stream-ordered) when the object dies.
+class Workspace {
+ public:
+  explicit Workspace(cudaStream_t s) : s_(s) {}
+  ~Workspace() { release(); }
+  template <class T>
+  ancka_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&q, bytes, s_);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+      return ANCKA_ERR_OOM;
+    }
+    ptrs_.push_back(q);
+    *p = static_cast<T*>(q);
+    return ANCKA_OK;
+  }
+  template <class T>
+  ancka_status zeros(T** p, size_t count) {
+    ANCKA_TRY(alloc(p, count));
+    ANCKA_CUDA(cudaMemsetAsync(*p, 0, (count ? count : 1) * sizeof(T), s_));
+    return ANCKA_OK;
+  }
+  void release() {
+    for (void* q : ptrs_) cudaFreeAsync(q, s_);
+    ptrs_.clear();
+  }
+  cudaStream_t stream() const { return s_; }
+
+ private:
+  cudaStream_t s_;
+  std::vector<void*> ptrs_;
+};
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// ---------------------------------------------------------------------------
+// error-free transformations (Ogita, Rump, Oishi 2005, "Accurate sum and dot
+// product"): the _rn intrinsics are never contracted into FMAs, which keeps
+// TwoSum / TwoProd exact.
+// ---------------------------------------------------------------------------
+struct DW {  // unevaluated sum hi + lo
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// Dot2 accumulation step: (s, c) += x * y
+__device__ __forceinline__ void dot2_step(float& s, float& c, float x, float y) {
+  float p = __fmul_rn(x, y);
+  float ep = __fmaf_rn(x, y, -p);
+  float t, es;
+  two_sum(s, p, t, es);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(es, ep));
+}
+
+// combine two Dot2 partials (s1,c1) + (s2,c2)
+__device__ __forceinline__ void dot2_merge(float& s, float& c, float s2, float c2) {
+  float t, e;
+  two_sum(s, s2, t, e);
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), e);
+}
+
+// fixed-order butterfly reduction of a Dot2 partial across a full warp
+__device__ __forceinline__ void dot2_warp_reduce(float& s, float& c) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    float s2 = __shfl_xor_sync(0xffffffffu, s, off);
+    float c2 = __shfl_xor_sync(0xffffffffu, c, off);
+    // order the operands by lane so both partners compute the same value
+    int lane = threadIdx.x & 31;
+    if (lane & off) {
+      float ts = s, tc = c;
+      s = s2; c = c2; s2 = ts; c2 = tc;
+    }
+    dot2_merge(s, c, s2, c2);
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// internal host interfaces (one translation unit each)
+// ---------------------------------------------------------------------------
+
+// prep.cu: unit rows, low-precision copy, per-row quantisation error
+struct PrepOut {
+  int32_t dp;          // padded feature dimension of the copy
+  int64_t n_pad;       // padded row count of the copy
+  float* xu32;         // FP32 unit rows (n_pad x dp) or null
+  __nv_bfloat16* xb;   // BF16 unit rows (n_pad x dp) or null
+  float* err;          // n: upper bound of || copy_i - x_i/||x_i|| ||_2
+  double* nrm2;        // n: ||x_i||^2 (compensated)
+  int32_t* zero_row;   // n: 1 if x_i == 0
+  float* err_max;      // 1: max_i err_i
+};
+ancka_status prep_rows(Workspace& ws, const float* X, int64_t n, int32_t d, int prec, PrepOut* out,
+                       cudaStream_t s);
+
+// knn_simt.cu / knn_tc.cu: candidate top-C lists from the low-precision scores
+constexpr int kCandC = 32;  // candidates kept per row
+ancka_status knn_candidates_fp32(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
+                                 cudaStream_t s);
+ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
+                                 cudaStream_t s);
+bool knn_tc_available();
+
+// rerank.cu: certified exact re-rank + exhaustive fallback
+ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
+                        const PrepOut& pr, float acc_coef, const float* cand_val,
+                        const int32_t* cand_idx, int32_t* out_idx, float* out_sim,
+                        int64_t* n_candidates, int64_t* n_fallback, bool want_counts,
+                        cudaStream_t s);
+
+// graph.cu: walk structures
+struct Csr {
+  int64_t nrows = 0, nnz = 0;
+  int64_t* ptr = nullptr;
+  int32_t* col = nullptr;
+  float* val = nullptr;    // P_N (or KNN) values, may be null
+  float* valT = nullptr;   // P_N^T values on the same pattern (graph/multiplex)
+};
+struct Walk {
+  int kind = 0;
+  int64_t n = 0, m = 0;
+  Csr topo;         // graph/multiplex: merged layers; hypergraph: node -> hyperedges (H^T)
+  Csr edges;        // hypergraph: hyperedge -> nodes (H)
+  Csr knn;          // KNN part with values beta_i A_K[i,j] / D_K[i]
+  float* rs_topo = nullptr;     // n: (1 - beta_i) [/ delta_i for hypergraphs]
+  float* inv_deg = nullptr;     // hypergraph: n, 1/delta_v (0 if delta = 0)
+  float* inv_size = nullptr;    // hypergraph: m, 1/|e|
+  int32_t* degree = nullptr;    // n: delta(v) used for V_c
+  float* beta = nullptr;        // n: beta_i
+};
+ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cudaStream_t s);
+ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* idx, const float* sim,
+                            const int32_t* zero_row, float beta, Walk* w, cudaStream_t s);
+
+// iter.cu: the orthogonal iteration and its helpers
+struct IterCfg {
+  int32_t k, T, gamma, T_i, tau, disc_max_iter;
+  float alpha;
+};
+struct IterTrace {
+  double* phi_dev;         // device [ANCKA_MAX_TRACE]
+  int32_t* disc_iters_dev; // device [ANCKA_MAX_TRACE]
+  int32_t* taken_dev;      // device [ANCKA_MAX_TRACE]
+  int32_t* flags_dev;      // device [1]
+  double* phi_best_dev;    // device [1]
+  int n_phi;
+  std::vector<cudaEvent_t>* events;  // (phase, start, stop) triples
+  std::vector<int>* phases;
+};
+ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& c, const int32_t* init_labels,
+                       int32_t* labels_out, float* Q_out, int32_t* init_out, IterTrace* tr,
+                       cudaStream_t s);
+ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, int32_t ldq,
+                        int32_t max_iter, int32_t* labels, int32_t* iters_dev, int32_t* flags_dev,
+                        cudaStream_t s);
+
+}  // namespace ancka

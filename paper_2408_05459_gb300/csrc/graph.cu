@@ -1,0 +1,417 @@
+// Walk-matrix structures of Section 6.1 and the KNN graph of Eq. AK.
+//
+// Topology (built once per call, deterministic):
+//   graph / multiplex  each layer's (row, col) pairs (plus reversed pairs for
+//     directed input) are sorted and de-duplicated, giving the binary A_l of
+//     Eq. rw-ag / rw-mg; the layers are then concatenated row by row into one
+//     CSR whose values are P_N[i,j] = 1/(L deg_l(i)) and, on the same
+//     pattern, P_N^T[i,j] = 1/(L deg_l(j)) (A_l is symmetric).
+//   hypergraph  (e, v) pairs are sorted and de-duplicated into H (hyperedge
+//     -> members) and H^T (node -> incident hyperedges) of Eq. rw-hg; the
+//     diagonal scalings 1/|e| and 1/delta(v) are kept as vectors.
+// KNN part: row i holds its K out-neighbours with A_K = 2f (mutual) or f,
+// then the nodes that list i but are not listed by i (weight f), in source
+// order; values are pre-scaled to beta_i A_K[i,j] / D_K[i] (Eq. p-mat-ancka).
+#include <cub/cub.cuh>
+
+#include "common.cuh"
+
+namespace ancka {
+
+namespace {
+
+constexpr uint64_t kLowMask = 0xffffffffull;
+
+int bits_for(int64_t n) {
+  int b = 1;
+  while ((int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+// --- CUB wrappers (one-off preprocessing sorts / scans) ---------------------
+ancka_status sort_keys(Workspace& ws, uint64_t* keys_in, uint64_t* keys_out, int64_t count,
+                       int end_bit, cudaStream_t s) {
+  if (count == 0) return ANCKA_OK;
+  size_t tmp = 0;
+  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, keys_in, keys_out, count, 0, end_bit, s));
+  void* t = nullptr;
+  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp));
+  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, keys_in, keys_out, count, 0, end_bit, s));
+  return ANCKA_OK;
+}
+
+ancka_status unique_keys(Workspace& ws, const uint64_t* in, uint64_t* out, int64_t* count_dev,
+                         int64_t count, cudaStream_t s) {
+  size_t tmp = 0;
+  ANCKA_CUDA(cub::DeviceSelect::Unique(nullptr, tmp, in, out, count_dev, count, s));
+  void* t = nullptr;
+  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp));
+  ANCKA_CUDA(cub::DeviceSelect::Unique(t, tmp, in, out, count_dev, count, s));
+  return ANCKA_OK;
+}
+
+template <class T>
+ancka_status exclusive_scan(Workspace& ws, const T* in, T* out, int64_t count, cudaStream_t s) {
+  size_t tmp = 0;
+  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, count, s));
+  void* t = nullptr;
+  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp));
+  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, in, out, count, s));
+  return ANCKA_OK;
+}
+
+ancka_status read_count(const int64_t* dev, int64_t* host, cudaStream_t s) {
+  ANCKA_CUDA(cudaMemcpyAsync(host, dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  return ANCKA_OK;
+}
+
+// --- kernels -----------------------------------------------------------------
+__global__ void k_csr_to_keys(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                              int64_t n, int directed, uint64_t* __restrict__ keys,
+                              int32_t* __restrict__ bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t b = ptr[i], e = ptr[i + 1], base = ptr[0];
+  for (int64_t p = b; p < e; ++p) {
+    int32_t j = col[p];
+    if (j < 0 || j >= n) {
+      atomicExch(bad, 1);
+      j = 0;
+    }
+    int64_t q = p - base;
+    keys[directed ? 2 * q : q] = ((uint64_t)i << 32) | (uint32_t)j;
+    if (directed) keys[2 * q + 1] = ((uint64_t)j << 32) | (uint32_t)i;
+  }
+}
+
+__global__ void k_hyper_to_keys(const int64_t* __restrict__ he_ptr, const int32_t* __restrict__ nodes,
+                                int64_t m, int64_t n, uint64_t* __restrict__ keys,
+                                int32_t* __restrict__ bad) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  for (int64_t p = he_ptr[e]; p < he_ptr[e + 1]; ++p) {
+    int32_t v = nodes[p];
+    if (v < 0 || v >= n) {
+      atomicExch(bad, 1);
+      v = 0;
+    }
+    keys[p - he_ptr[0]] = ((uint64_t)e << 32) | (uint32_t)v;
+  }
+}
+
+// counts per high half of the keys; col = low half
+__global__ void k_keys_to_rows(const uint64_t* __restrict__ keys, const int64_t* __restrict__ cnt_dev,
+                               int32_t* __restrict__ rowcnt, int32_t* __restrict__ col) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *cnt_dev) return;
+  uint64_t k = keys[q];
+  atomicAdd(&rowcnt[k >> 32], 1);
+  if (col) col[q] = (int32_t)(k & kLowMask);
+}
+
+__global__ void k_swap_halves(const uint64_t* __restrict__ in, const int64_t* __restrict__ cnt_dev,
+                              uint64_t* __restrict__ out) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *cnt_dev) return;
+  uint64_t k = in[q];
+  out[q] = (k << 32) | (k >> 32);
+}
+
+__global__ void k_int_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+__global__ void k_inv_count(const int32_t* __restrict__ c, float* __restrict__ inv, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) inv[i] = c[i] > 0 ? 1.f / (float)c[i] : 0.f;
+}
+
+// merged multiplex / graph CSR: row i = layer 0 row i, layer 1 row i, ...
+__global__ void k_merge_layers(int L, int64_t n, const int64_t* const* __restrict__ lptr,
+                               const int32_t* const* __restrict__ lcol,
+                               const int32_t* const* __restrict__ ldeg,
+                               const int64_t* __restrict__ mptr, int32_t* __restrict__ mcol,
+                               float* __restrict__ val, float* __restrict__ valT) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = mptr[i];
+  float invL = 1.f / (float)L;
+  for (int l = 0; l < L; ++l) {
+    const int32_t* deg = ldeg[l];
+    float wi = deg[i] > 0 ? invL / (float)deg[i] : 0.f;
+    for (int64_t p = lptr[l][i]; p < lptr[l][i + 1]; ++p, ++o) {
+      int32_t j = lcol[l][p];
+      mcol[o] = j;
+      val[o] = wi;
+      valT[o] = deg[j] > 0 ? invL / (float)deg[j] : 0.f;  // deg[j] >= 1 for a symmetric A_l
+    }
+  }
+}
+
+__global__ void k_sum_deg(int L, int64_t n, const int32_t* const* __restrict__ ldeg,
+                          int32_t* __restrict__ deg, int64_t* __restrict__ mlen) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t s = 0;
+  for (int l = 0; l < L; ++l) s += ldeg[l][i];
+  deg[i] = s;
+  mlen[i] = s;
+}
+
+// --- KNN augmentation -------------------------------------------------------
+__global__ void k_knn_mutual(const int32_t* __restrict__ idx, int64_t n, int K,
+                             uint8_t* __restrict__ mutual, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ in_cnt) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * K) return;
+  int64_t i = q / K;
+  int32_t j = idx[q];
+  bool mu = false;
+  for (int p = 0; p < K; ++p) mu |= (idx[(int64_t)j * K + p] == (int32_t)i);
+  mutual[q] = mu ? 1 : 0;
+  if (mu) {
+    keys[q] = ~0ull;  // sorts after every real key
+  } else {
+    keys[q] = ((uint64_t)j << 32) | (uint32_t)i;
+    atomicAdd(&in_cnt[j], 1);
+  }
+}
+
+__global__ void k_knn_len(const int32_t* __restrict__ in_cnt, int64_t n, int K,
+                          int64_t* __restrict__ len, int64_t* __restrict__ in_len) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  len[i] = K + in_cnt[i];
+  in_len[i] = in_cnt[i];
+}
+
+// row i: K out-entries, then in-entries; A_K values, D_K, beta_i, P values.
+__global__ void k_knn_fill(const int32_t* __restrict__ idx, const float* __restrict__ sim,
+                           const uint8_t* __restrict__ mutual, const uint64_t* __restrict__ skeys,
+                           const int64_t* __restrict__ in_start, const int32_t* __restrict__ in_cnt,
+                           int64_t n, int K, const int64_t* __restrict__ ptr,
+                           int32_t* __restrict__ col, float* __restrict__ val,
+                           const int32_t* __restrict__ zero_row, const int32_t* __restrict__ degree,
+                           float beta, float* __restrict__ beta_out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = ptr[i];
+  double D = 0.0;
+  for (int p = 0; p < K; ++p) {
+    int64_t q = i * K + p;
+    float a = mutual[q] ? 2.f * sim[q] : sim[q];
+    col[o + p] = idx[q];
+    val[o + p] = a;
+    D += a;
+  }
+  int64_t b = in_start[i];
+  int32_t c = in_cnt[i];
+  for (int32_t t = 0; t < c; ++t) {
+    int32_t src = (int32_t)(skeys[b + t] & kLowMask);
+    float f = 0.f;
+    for (int p = 0; p < K; ++p)
+      if (idx[(int64_t)src * K + p] == (int32_t)i) f = sim[(int64_t)src * K + p];
+    col[o + K + t] = src;
+    val[o + K + t] = f;
+    D += f;
+  }
+  // Eq. beta_i, then reading R3 (a non-positive KNN degree disables the KNN walk)
+  float bi = zero_row[i] ? 0.f : (degree[i] == 0 ? 1.f : beta);
+  if (!(D > 0.0)) bi = 0.f;
+  beta_out[i] = bi;
+  float scale = D > 0.0 ? (float)((double)bi / D) : 0.f;
+  for (int64_t p = o; p < o + K + c; ++p) val[p] *= scale;
+}
+
+__global__ void k_topo_rowscale(const float* __restrict__ beta, const float* __restrict__ inv_deg,
+                                int64_t n, float* __restrict__ rs) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rs[i] = (1.f - beta[i]) * (inv_deg ? inv_deg[i] : 1.f);
+}
+
+inline unsigned grid_for(int64_t n, int b) { return (unsigned)ceil_div(n > 0 ? n : 1, b); }
+
+// sorted unique keys -> CSR over the high halves (rows 0..nrows-1)
+ancka_status keys_to_csr(Workspace& ws, const uint64_t* ukeys, const int64_t* ucnt_dev, int64_t ucnt,
+                         int64_t nrows, Csr* out, int32_t** rowcnt_out, cudaStream_t s) {
+  int32_t* rowcnt;
+  ANCKA_TRY(ws.zeros(&rowcnt, (size_t)nrows + 1));
+  ANCKA_TRY(ws.alloc(&out->col, (size_t)ucnt));
+  k_keys_to_rows<<<grid_for(ucnt, 256), 256, 0, s>>>(ukeys, ucnt_dev, rowcnt, out->col);
+  ANCKA_LAUNCHED();
+  int64_t* len;
+  ANCKA_TRY(ws.alloc(&len, (size_t)nrows + 1));
+  k_int_to_i64<<<grid_for(nrows + 1, 256), 256, 0, s>>>(rowcnt, len, nrows + 1);
+  ANCKA_LAUNCHED();
+  ANCKA_TRY(ws.alloc(&out->ptr, (size_t)nrows + 1));
+  ANCKA_TRY(exclusive_scan(ws, len, out->ptr, nrows + 1, s));
+  out->nrows = nrows;
+  out->nnz = ucnt;
+  *rowcnt_out = rowcnt;
+  return ANCKA_OK;
+}
+
+}  // namespace
+
+ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cudaStream_t s) {
+  const int64_t n = t.n;
+  w->kind = t.kind;
+  w->n = n;
+  int32_t* bad;
+  ANCKA_TRY(ws.zeros(&bad, 1));
+  const int nb = bits_for(n);
+  if (t.kind == ANCKA_HYPERGRAPH) {
+    const int64_t m = t.m;
+    w->m = m;
+    int64_t nnz = 0;
+    ANCKA_CUDA(cudaMemcpyAsync(&nnz, t.he_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int64_t base = 0;
+    ANCKA_CUDA(cudaMemcpyAsync(&base, t.he_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    nnz -= base;
+    uint64_t *k0, *k1, *k2;
+    ANCKA_TRY(ws.alloc(&k0, (size_t)nnz));
+    ANCKA_TRY(ws.alloc(&k1, (size_t)nnz));
+    ANCKA_TRY(ws.alloc(&k2, (size_t)nnz));
+    k_hyper_to_keys<<<grid_for(m, 256), 256, 0, s>>>(t.he_ptr, t.he_nodes, m, n, k0, bad);
+    ANCKA_LAUNCHED();
+    const int mb = bits_for(m);
+    ANCKA_TRY(sort_keys(ws, k0, k1, nnz, 32 + mb, s));
+    int64_t* ucnt_dev;
+    ANCKA_TRY(ws.alloc(&ucnt_dev, 1));
+    ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, nnz, s));
+    int64_t ucnt = 0;
+    ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
+    int32_t* esize;
+    ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, m, &w->edges, &esize, s));
+    // node -> hyperedge incidence
+    k_swap_halves<<<grid_for(ucnt, 256), 256, 0, s>>>(k2, ucnt_dev, k0);
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(sort_keys(ws, k0, k1, ucnt, 32 + nb, s));
+    int32_t* vdeg;
+    ANCKA_TRY(keys_to_csr(ws, k1, ucnt_dev, ucnt, n, &w->topo, &vdeg, s));
+    w->degree = vdeg;
+    ANCKA_TRY(ws.alloc(&w->inv_size, (size_t)m));
+    ANCKA_TRY(ws.alloc(&w->inv_deg, (size_t)n));
+    k_inv_count<<<grid_for(m, 256), 256, 0, s>>>(esize, w->inv_size, m);
+    ANCKA_LAUNCHED();
+    k_inv_count<<<grid_for(n, 256), 256, 0, s>>>(vdeg, w->inv_deg, n);
+    ANCKA_LAUNCHED();
+  } else {
+    const int L = t.L;
+    std::vector<const int64_t*> lptr(L);
+    std::vector<const int32_t*> lcol(L);
+    std::vector<const int32_t*> ldeg(L);
+    for (int l = 0; l < L; ++l) {
+      const int64_t* rp = t.row_ptr + (int64_t)l * (n + 1);
+      int64_t b = 0, e = 0;
+      ANCKA_CUDA(cudaMemcpyAsync(&b, rp, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaMemcpyAsync(&e, rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaStreamSynchronize(s));
+      int64_t cnt = (e - b) * (t.directed ? 2 : 1);
+      uint64_t *k0, *k1, *k2;
+      ANCKA_TRY(ws.alloc(&k0, (size_t)cnt));
+      ANCKA_TRY(ws.alloc(&k1, (size_t)cnt));
+      ANCKA_TRY(ws.alloc(&k2, (size_t)cnt));
+      k_csr_to_keys<<<grid_for(n, 256), 256, 0, s>>>(rp, t.col_idx, n, t.directed, k0, bad);
+      ANCKA_LAUNCHED();
+      ANCKA_TRY(sort_keys(ws, k0, k1, cnt, 32 + nb, s));
+      int64_t* ucnt_dev;
+      ANCKA_TRY(ws.alloc(&ucnt_dev, 1));
+      ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, cnt, s));
+      int64_t ucnt = 0;
+      ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
+      Csr lay;
+      int32_t* deg;
+      ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, n, &lay, &deg, s));
+      lptr[l] = lay.ptr;
+      lcol[l] = lay.col;
+      ldeg[l] = deg;
+    }
+    // merge layers
+    const int64_t** dlptr;
+    const int32_t** dlcol;
+    const int32_t** dldeg;
+    ANCKA_TRY(ws.alloc(&dlptr, (size_t)L));
+    ANCKA_TRY(ws.alloc(&dlcol, (size_t)L));
+    ANCKA_TRY(ws.alloc(&dldeg, (size_t)L));
+    ANCKA_CUDA(cudaMemcpyAsync(dlptr, lptr.data(), L * sizeof(void*), cudaMemcpyHostToDevice, s));
+    ANCKA_CUDA(cudaMemcpyAsync(dlcol, lcol.data(), L * sizeof(void*), cudaMemcpyHostToDevice, s));
+    ANCKA_CUDA(cudaMemcpyAsync(dldeg, ldeg.data(), L * sizeof(void*), cudaMemcpyHostToDevice, s));
+    int64_t* mlen;
+    ANCKA_TRY(ws.alloc(&mlen, (size_t)n + 1));
+    ANCKA_CUDA(cudaMemsetAsync(mlen + n, 0, sizeof(int64_t), s));
+    ANCKA_TRY(ws.alloc(&w->degree, (size_t)n));
+    k_sum_deg<<<grid_for(n, 256), 256, 0, s>>>(L, n, dldeg, w->degree, mlen);
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(ws.alloc(&w->topo.ptr, (size_t)n + 1));
+    ANCKA_TRY(exclusive_scan(ws, mlen, w->topo.ptr, n + 1, s));
+    int64_t tot = 0;
+    ANCKA_CUDA(cudaMemcpyAsync(&tot, w->topo.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    w->topo.nrows = n;
+    w->topo.nnz = tot;
+    ANCKA_TRY(ws.alloc(&w->topo.col, (size_t)tot));
+    ANCKA_TRY(ws.alloc(&w->topo.val, (size_t)tot));
+    ANCKA_TRY(ws.alloc(&w->topo.valT, (size_t)tot));
+    k_merge_layers<<<grid_for(n, 256), 256, 0, s>>>(L, n, dlptr, dlcol, dldeg, w->topo.ptr,
+                                                    w->topo.col, w->topo.val, w->topo.valT);
+    ANCKA_LAUNCHED();
+  }
+  int32_t hbad = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (hbad) {
+    set_error("topology: node id out of range [0, n)");
+    return ANCKA_ERR_INVALID_ARG;
+  }
+  return ANCKA_OK;
+}
+
+ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* idx, const float* sim,
+                            const int32_t* zero_row, float beta, Walk* w, cudaStream_t s) {
+  const int64_t nk = n * K;
+  uint8_t* mutual;
+  uint64_t *keys, *skeys;
+  int32_t* in_cnt;
+  ANCKA_TRY(ws.alloc(&mutual, (size_t)nk));
+  ANCKA_TRY(ws.alloc(&keys, (size_t)nk));
+  ANCKA_TRY(ws.alloc(&skeys, (size_t)nk));
+  ANCKA_TRY(ws.zeros(&in_cnt, (size_t)n));
+  k_knn_mutual<<<grid_for(nk, 256), 256, 0, s>>>(idx, n, K, mutual, keys, in_cnt);
+  ANCKA_LAUNCHED();
+  ANCKA_TRY(sort_keys(ws, keys, skeys, nk, 64, s));
+  int64_t *len, *in_len, *in_start;
+  ANCKA_TRY(ws.alloc(&len, (size_t)n + 1));
+  ANCKA_TRY(ws.alloc(&in_len, (size_t)n + 1));
+  ANCKA_TRY(ws.alloc(&in_start, (size_t)n + 1));
+  ANCKA_CUDA(cudaMemsetAsync(len + n, 0, sizeof(int64_t), s));
+  ANCKA_CUDA(cudaMemsetAsync(in_len + n, 0, sizeof(int64_t), s));
+  k_knn_len<<<grid_for(n, 256), 256, 0, s>>>(in_cnt, n, K, len, in_len);
+  ANCKA_LAUNCHED();
+  Csr& c = w->knn;
+  ANCKA_TRY(ws.alloc(&c.ptr, (size_t)n + 1));
+  ANCKA_TRY(exclusive_scan(ws, len, c.ptr, n + 1, s));
+  ANCKA_TRY(exclusive_scan(ws, in_len, in_start, n + 1, s));
+  int64_t tot = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&tot, c.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  c.nrows = n;
+  c.nnz = tot;
+  ANCKA_TRY(ws.alloc(&c.col, (size_t)tot));
+  ANCKA_TRY(ws.alloc(&c.val, (size_t)tot));
+  ANCKA_TRY(ws.alloc(&w->beta, (size_t)n));
+  k_knn_fill<<<grid_for(n, 128), 128, 0, s>>>(idx, sim, mutual, skeys, in_start, in_cnt, n, K, c.ptr,
+                                              c.col, c.val, zero_row, w->degree, beta, w->beta);
+  ANCKA_LAUNCHED();
+  ANCKA_TRY(ws.alloc(&w->rs_topo, (size_t)n));
+  k_topo_rowscale<<<grid_for(n, 256), 256, 0, s>>>(w->beta, w->kind == ANCKA_HYPERGRAPH ? w->inv_deg : nullptr,
+                                                   n, w->rs_topo);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+}  // namespace ancka

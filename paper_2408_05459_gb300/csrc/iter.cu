@@ -1,0 +1,1045 @@
+// Algorithm 4 after the walk matrices exist: InitBCM (Alg. 3 / Eq. pi_c_t),
+// the orthogonal iteration Z = P Q (Eq. zt) with CholeskyQR2, Discretize
+// (Def. 2, Alg. 5) and CalMHC (Alg. 2, Eq. mhc-comp-ancka), all enqueued on
+// one stream without host synchronisation.
+//
+// Dense blocks are n x ld FP32 row-major with ld = round_up(width, 4) and
+// zero padding columns.  Every reduction has a fixed order, so a run is
+// bitwise reproducible.  FP64 is used only for k x k work (Gram matrices,
+// Cholesky, the Discretize SVD) and for cross-CTA sums.
+#include <cub/cub.cuh>
+
+#include "common.cuh"
+
+namespace ancka {
+
+namespace {
+
+constexpr int kMaxW = 68;  // k <= 64 -> k+1 <= 65 columns, padded to 68
+
+inline unsigned grid_for(int64_t n, int b) { return (unsigned)ceil_div(n > 0 ? n : 1, b); }
+
+// ---------------------------------------------------------------------------
+// generic CSR SpMM with an optional second CSR part and a one-hot addend:
+//   out[i] = coef * ( rsA[i] * sum_p vA[p] csA[colA[p]] srcA[colA[p]]
+//                     + sum_p vB[p] srcB[colB[p]] )
+//            + oh_coef * oh_scale[oh_col[i]] * e_{oh_col[i]}
+// G lanes per row, one float4 column chunk per lane.
+// ---------------------------------------------------------------------------
+struct SpmmArgs {
+  const int64_t* ptrA = nullptr;
+  const int32_t* colA = nullptr;
+  const float* valA = nullptr;
+  const float* rsA = nullptr;
+  const float* csA = nullptr;
+  const float* srcA = nullptr;
+  int ldA = 0;
+  const int64_t* ptrB = nullptr;
+  const int32_t* colB = nullptr;
+  const float* valB = nullptr;
+  const float* srcB = nullptr;
+  int ldB = 0;
+  float coef = 1.f;
+  const int32_t* oh_col = nullptr;
+  const float* oh_scale = nullptr;
+  float oh_coef = 0.f;
+  float* out = nullptr;
+  int ldo = 0;
+  int64_t nrows = 0;
+  int nv4 = 0;  // float4 chunks per row
+};
+
+template <int G>
+__global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
+  if (i >= a.nrows || g >= a.nv4) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t p = a.ptrA[i], e = a.ptrA[i + 1]; p < e; ++p) {
+    const int32_t j = a.colA[p];
+    float w = a.valA ? a.valA[p] : 1.f;
+    if (a.csA) w *= a.csA[j];
+    const float4 x = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g);
+    acc.x = fmaf(w, x.x, acc.x);
+    acc.y = fmaf(w, x.y, acc.y);
+    acc.z = fmaf(w, x.z, acc.z);
+    acc.w = fmaf(w, x.w, acc.w);
+  }
+  if (a.rsA) {
+    const float r = a.rsA[i];
+    acc.x *= r;
+    acc.y *= r;
+    acc.z *= r;
+    acc.w *= r;
+  }
+  if (a.ptrB) {
+    for (int64_t p = a.ptrB[i], e = a.ptrB[i + 1]; p < e; ++p) {
+      const int32_t j = a.colB[p];
+      const float w = a.valB[p];
+      const float4 x = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j * a.ldB + 4 * g);
+      acc.x = fmaf(w, x.x, acc.x);
+      acc.y = fmaf(w, x.y, acc.y);
+      acc.z = fmaf(w, x.z, acc.z);
+      acc.w = fmaf(w, x.w, acc.w);
+    }
+  }
+  acc.x *= a.coef;
+  acc.y *= a.coef;
+  acc.z *= a.coef;
+  acc.w *= a.coef;
+  if (a.oh_col) {
+    const int c = a.oh_col[i];
+    if (c >= 4 * g && c < 4 * g + 4) {
+      const float add = a.oh_coef * (a.oh_scale ? a.oh_scale[c] : 1.f);
+      const int q = c - 4 * g;
+      if (q == 0) acc.x += add;
+      else if (q == 1) acc.y += add;
+      else if (q == 2) acc.z += add;
+      else acc.w += add;
+    }
+  }
+  *reinterpret_cast<float4*>(a.out + i * a.ldo + 4 * g) = acc;
+}
+
+ancka_status spmm(const SpmmArgs& a, cudaStream_t s) {
+  const int nv4 = a.nv4;
+  const int G = nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16;
+  const unsigned grid = grid_for(a.nrows * G, 256);
+  switch (G) {
+    case 1: k_spmm<1><<<grid, 256, 0, s>>>(a); break;
+    case 2: k_spmm<2><<<grid, 256, 0, s>>>(a); break;
+    case 4: k_spmm<4><<<grid, 256, 0, s>>>(a); break;
+    case 8: k_spmm<8><<<grid, 256, 0, s>>>(a); break;
+    default: k_spmm<16><<<grid, 256, 0, s>>>(a); break;
+  }
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gram partials: per CTA, sum over its row chunk of t_r t_r^T (upper triangle)
+// with t_r = Z[r] (or Z[r] Rinv when Rinv is given); 32-row tiles in FP32,
+// tiles accumulated in FP64.
+// ---------------------------------------------------------------------------
+constexpr int kGramThreads = 256, kGramTile = 32, kGramPairs = 9;  // 9*256 >= 65*66/2
+
+__global__ void __launch_bounds__(kGramThreads)
+k_gram_partial(const float* __restrict__ Z, int ldz, int64_t n, int w, double* __restrict__ partial) {
+  __shared__ float T[kGramTile][kMaxW + 1];
+  const int64_t per = ceil_div(n, (int64_t)gridDim.x);
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = (r0 + per < n) ? r0 + per : n;
+  const int np = w * (w + 1) / 2;
+  int pa[kGramPairs], pb[kGramPairs];
+  double accd[kGramPairs];
+#pragma unroll
+  for (int q = 0; q < kGramPairs; ++q) {
+    int p = threadIdx.x + q * kGramThreads;
+    int a = 0;
+    while (p >= w - a && a < w) {
+      p -= w - a;
+      ++a;
+    }
+    pa[q] = a;
+    pb[q] = a + p;
+    accd[q] = 0.0;
+  }
+  for (int64_t rb = r0; rb < r1; rb += kGramTile) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGramTile * w; e += kGramThreads) {
+      const int r = e / w, c = e % w;
+      const int64_t row = rb + r;
+      T[r][c] = row < r1 ? Z[row * ldz + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kGramPairs; ++q) {
+      if (threadIdx.x + q * kGramThreads < np) {
+        float acc = 0.f;
+        const int a = pa[q], b = pb[q];
+#pragma unroll 8
+        for (int r = 0; r < kGramTile; ++r) acc = fmaf(T[r][a], T[r][b], acc);
+        accd[q] += (double)acc;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kGramPairs; ++q) {
+    if (threadIdx.x + q * kGramThreads < np) {
+      double* P = partial + (int64_t)blockIdx.x * w * w;
+      P[pa[q] * w + pb[q]] = accd[q];
+      P[pb[q] * w + pa[q]] = accd[q];
+    }
+  }
+}
+
+// One CTA: G = sum of partials (fixed order), upper Cholesky G = R^T R in
+// FP64, Rinv = R^-1 (upper), written as FP32.  A non-positive pivot marks the
+// status and is replaced by a tiny one so the run finishes.
+__global__ void __launch_bounds__(256)
+k_chol_inv(const double* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
+           int32_t* __restrict__ status) {
+  extern __shared__ double csm[];  // G, R, X: w*w doubles each
+  const int ww = w * w;
+  double* G = csm;
+  double* R = csm + ww;
+  double* X = csm + 2 * ww;
+  for (int e = threadIdx.x; e < ww; e += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * ww + e];
+    G[e] = s;
+    R[e] = 0.0;
+    X[e] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    if (threadIdx.x == 0) {
+      double d = G[j * w + j];
+      for (int k = 0; k < j; ++k) d -= R[k * w + j] * R[k * w + j];
+      if (!(d > 1e-300)) {
+        atomicExch(status, 1);
+        d = 1e-300;
+      }
+      R[j * w + j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) {
+      double v = G[j * w + i];
+      for (int k = 0; k < j; ++k) v -= R[k * w + j] * R[k * w + i];
+      R[j * w + i] = v / R[j * w + j];
+    }
+    __syncthreads();
+  }
+  // columns of R^-1 by back substitution, one thread per column
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    X[c * w + c] = 1.0 / R[c * w + c];
+    for (int i = c - 1; i >= 0; --i) {
+      double v = 0.0;
+      for (int k = i + 1; k <= c; ++k) v += R[i * w + k] * X[k * w + c];
+      X[i * w + c] = -v / R[i * w + i];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ww; e += blockDim.x) Rinv_out[e] = (float)X[e];
+}
+
+// out[i, c] = sum_{a <= c} Z[i, a] Rinv[a, c]  (padding columns -> 0)
+template <int G>
+__global__ void __launch_bounds__(256)
+k_apply_rinv(const float* __restrict__ Z, int ld, int64_t n, int w, const float* __restrict__ Rinv,
+             float* __restrict__ out) {
+  __shared__ __align__(16) float Rs[kMaxW * kMaxW];
+  const int nv4 = ld / 4;
+  for (int e = threadIdx.x; e < w * ld; e += blockDim.x) {
+    const int a = e / ld, c = e % ld;
+    Rs[a * ld + c] = (c < w && a <= c) ? Rinv[a * w + c] : 0.f;
+  }
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
+  if (i >= n || g >= nv4) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* z = Z + i * ld;
+  const int amax = (4 * g + 3 < w - 1) ? 4 * g + 3 : w - 1;
+  for (int a = 0; a <= amax; ++a) {
+    const float za = z[a];
+    const float4 r = *reinterpret_cast<const float4*>(&Rs[a * ld + 4 * g]);
+    acc.x = fmaf(za, r.x, acc.x);
+    acc.y = fmaf(za, r.y, acc.y);
+    acc.z = fmaf(za, r.z, acc.z);
+    acc.w = fmaf(za, r.w, acc.w);
+  }
+  *reinterpret_cast<float4*>(out + i * ld + 4 * g) = acc;
+}
+
+int pick_g(int nv4) { return nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16; }
+
+ancka_status apply_rinv(const float* Z, int ld, int64_t n, int w, const float* Rinv, float* out,
+                        cudaStream_t s) {
+  const int G = pick_g(ld / 4);
+  const unsigned grid = grid_for(n * G, 256);
+  switch (G) {
+    case 1: k_apply_rinv<1><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
+    case 2: k_apply_rinv<2><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
+    case 4: k_apply_rinv<4><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
+    case 8: k_apply_rinv<8><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
+    default: k_apply_rinv<16><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
+  }
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Discretize
+// ---------------------------------------------------------------------------
+struct DiscState {
+  float* Rf;          // k x k FP32 copy of R for the argmax kernel
+  int32_t* counts;    // k
+  double* obj_prev;   // 1
+  int32_t* iter;      // 1
+  int32_t* done;      // 1
+  float* partial;     // nblk x k x k
+  int nblk;
+  int rows_per_blk;
+};
+
+__global__ void k_rownorm(const float* __restrict__ Q, int ldq, int off, int64_t n, int k,
+                          float* __restrict__ Qt, int ldt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* q = Q + i * ldq + off;
+  float s = 0.f;
+  for (int c = 0; c < k; ++c) s = fmaf(q[c], q[c], s);
+  const float inv = s > 0.f ? 1.f / sqrtf(s) : 0.f;  // a zero row stays zero
+  for (int c = 0; c < ldt; ++c) Qt[i * ldt + c] = c < k ? q[c] * inv : 0.f;
+}
+
+__global__ void k_disc_init(float* Rf, int32_t* counts, double* obj_prev, int32_t* iter, int32_t* done,
+                            int k) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rf[e] = (e / k == e % k) ? 1.f : 0.f;
+  for (int e = threadIdx.x; e < k; e += blockDim.x) counts[e] = 0;
+  if (threadIdx.x == 0) {
+    *obj_prev = 0.0;
+    *iter = 0;
+    *done = 0;
+  }
+}
+
+// labels[i] = argmax_c (Qt[i] R)[c], ties to the lowest c; per-CTA histogram
+template <int G>
+__global__ void __launch_bounds__(256)
+k_disc_argmax(const float* __restrict__ Qt, int ldt, int64_t n, int k, const float* __restrict__ Rf,
+              int32_t* __restrict__ labels, int32_t* __restrict__ counts, const int32_t* __restrict__ done) {
+  if (*done) return;
+  __shared__ __align__(16) float Rs[64 * 64];
+  __shared__ int32_t hist[64];
+  const int ldr = ldt;
+  for (int e = threadIdx.x; e < k * ldr; e += blockDim.x) {
+    const int a = e / ldr, c = e % ldr;
+    Rs[a * ldr + c] = c < k ? Rf[a * k + c] : 0.f;
+  }
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) hist[e] = 0;
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
+  const int nv4 = ldt / 4;
+  float best = -INFINITY;
+  int bc = 0x7fffffff;
+  if (i < n && g < nv4) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* q = Qt + i * ldt;
+    for (int a = 0; a < k; ++a) {
+      const float qa = q[a];
+      const float4 r = *reinterpret_cast<const float4*>(&Rs[a * ldr + 4 * g]);
+      acc.x = fmaf(qa, r.x, acc.x);
+      acc.y = fmaf(qa, r.y, acc.y);
+      acc.z = fmaf(qa, r.z, acc.z);
+      acc.w = fmaf(qa, r.w, acc.w);
+    }
+    const float v[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      const int c = 4 * g + q4;
+      if (c < k && v[q4] > best) {
+        best = v[q4];
+        bc = c;
+      }
+    }
+  }
+  // reduce within the G-lane group: max value, lowest column on ties
+#pragma unroll
+  for (int off = 1; off < G; off <<= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+    if (ob > best || (ob == best && oc < bc)) {
+      best = ob;
+      bc = oc;
+    }
+  }
+  if (i < n && g == 0) {
+    if (bc == 0x7fffffff) bc = 0;  // all-NaN row
+    labels[i] = bc;
+    atomicAdd(&hist[bc], 1);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k; e += blockDim.x)
+    if (hist[e]) atomicAdd(&counts[e], hist[e]);
+}
+
+// per-CTA k x k sums M'[l][c] = sum_{i in chunk, y_i = l} Qt[i][c]; thread
+// (slice, c) owns column c of its slice, rows in order (deterministic).
+__global__ void __launch_bounds__(256)
+k_disc_msum(const float* __restrict__ Qt, int ldt, int64_t n, int k, const int32_t* __restrict__ labels,
+            int rows_per_blk, float* __restrict__ partial, const int32_t* __restrict__ done) {
+  if (*done) return;
+  extern __shared__ float sM[];  // nsl x k x k
+  const int nsl = blockDim.x / k;
+  const int kk = k * k;
+  for (int e = threadIdx.x; e < nsl * kk; e += blockDim.x) sM[e] = 0.f;
+  __syncthreads();
+  const int sl = threadIdx.x / k, c = threadIdx.x % k;
+  const int64_t b0 = (int64_t)blockIdx.x * rows_per_blk;
+  const int64_t b1 = (b0 + rows_per_blk < n) ? b0 + rows_per_blk : n;
+  if (sl < nsl) {
+    const int64_t per = ceil_div(b1 - b0 > 0 ? b1 - b0 : 0, (int64_t)nsl);
+    const int64_t s0 = b0 + sl * per;
+    const int64_t s1 = (s0 + per < b1) ? s0 + per : b1;
+    float* my = sM + sl * kk;
+    for (int64_t i = s0; i < s1; ++i) my[labels[i] * k + c] += Qt[i * ldt + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    float s = 0.f;
+    for (int q = 0; q < nsl; ++q) s += sM[q * kk + e];
+    partial[(int64_t)blockIdx.x * kk + e] = s;
+  }
+}
+
+// One CTA of 1024 threads: M = Y~^T Q~ in FP64, one-sided Jacobi SVD
+// (Hestenes; round-robin pair schedule, one warp per pair), R = V U^T,
+// obj = n - 2 tr(Omega), and the stop test of Alg. 5.
+__global__ void __launch_bounds__(1024)
+k_disc_svd(const float* __restrict__ partial, int nblk, int k, int64_t n, int32_t* __restrict__ counts,
+           float* __restrict__ Rf, double* __restrict__ obj_prev, int32_t* __restrict__ iter,
+           int32_t* __restrict__ done, int32_t* __restrict__ iters_out, int32_t* __restrict__ flags,
+           int max_iter) {
+  if (*done) return;
+  extern __shared__ double dsm[];  // A: k x kp, V: kp x kp (kp = k rounded up to even)
+  __shared__ double sig[65];
+  __shared__ int rotated;
+  const int kp = (k + 1) & ~1;
+  double* A = dsm;
+  double* V = dsm + k * kp;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  // M[l][c] = (sum over blocks) / count_l
+  for (int e = threadIdx.x; e < k * kp; e += blockDim.x) {
+    const int l = e / kp, c = e % kp;
+    double s = 0.0;
+    if (c < k) {
+      for (int b = 0; b < nblk; ++b) s += (double)partial[(int64_t)b * k * k + l * k + c];
+      const int cnt = counts[l];
+      s = cnt > 0 ? s / (double)cnt : 0.0;
+    }
+    A[l * kp + c] = s;
+  }
+  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) V[e] = (e / kp == e % kp) ? 1.0 : 0.0;
+  __syncthreads();
+  bool empty = false;
+  for (int l = 0; l < k; ++l) empty |= counts[l] == 0;
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < kp - 1; ++r) {
+      if (wp < kp / 2) {
+        int p, q;
+        if (wp == 0) {
+          p = kp - 1;
+          q = r;
+        } else {
+          p = (r + wp) % (kp - 1);
+          q = (r - wp + kp - 1) % (kp - 1);
+        }
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int row = lane; row < k; row += 32) {
+          const double x = A[row * kp + p], y = A[row * kp + q];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum_d(al);
+        be = warp_sum_d(be);
+        ga = warp_sum_d(ga);
+        if (al > 0.0 && be > 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int row = lane; row < k; row += 32) {
+            const double x = A[row * kp + p], y = A[row * kp + q];
+            A[row * kp + p] = cs * x - sn * y;
+            A[row * kp + q] = sn * x + cs * y;
+          }
+          for (int row = lane; row < kp; row += 32) {
+            const double x = V[row * kp + p], y = V[row * kp + q];
+            V[row * kp + p] = cs * x - sn * y;
+            V[row * kp + q] = sn * x + cs * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // singular values and U (stored back into A's columns)
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double s = 0.0;
+    for (int row = 0; row < k; ++row) s += A[row * kp + c] * A[row * kp + c];
+    sig[c] = sqrt(s);
+  }
+  __syncthreads();
+  double smax = 0.0;
+  for (int c = 0; c < k; ++c) smax = fmax(smax, sig[c]);
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int row = e / k, c = e % k;
+    const double sc = sig[c];
+    A[row * kp + c] = (sc > 1e-13 * smax && sc > 0.0) ? A[row * kp + c] / sc : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // rank-deficient M (empty clusters): complete U to an orthonormal basis
+    for (int c = 0; c < k; ++c) {
+      if (sig[c] > 1e-13 * smax && sig[c] > 0.0) continue;
+      for (int cand = 0; cand < k; ++cand) {
+        double u[64];
+        for (int row = 0; row < k; ++row) u[row] = (row == cand) ? 1.0 : 0.0;
+        for (int rep = 0; rep < 2; ++rep)
+          for (int o = 0; o < k; ++o) {
+            if (o == c) continue;
+            double dot = 0.0;
+            for (int row = 0; row < k; ++row) dot += A[row * kp + o] * u[row];
+            for (int row = 0; row < k; ++row) u[row] -= dot * A[row * kp + o];
+          }
+        double nn = 0.0;
+        for (int row = 0; row < k; ++row) nn += u[row] * u[row];
+        if (nn > 0.25) {
+          nn = 1.0 / sqrt(nn);
+          for (int row = 0; row < k; ++row) A[row * kp + c] = u[row] * nn;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // R = V U^T  (R[a][b] = sum_j V[a][j] U[b][j])
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int a = e / k, b = e % k;
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += V[a * kp + j] * A[b * kp + j];
+    Rf[e] = (float)s;
+  }
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int c = 0; c < k; ++c) tr += sig[c];
+    const double obj = (double)n - 2.0 * tr;
+    const int it = *iter;
+    if (it > 0 && fabs(obj - *obj_prev) <= 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(obj))) *done = 1;
+    *obj_prev = obj;
+    *iter = it + 1;
+    if (it + 1 >= max_iter) *done = 1;
+    if (iters_out) *iters_out = it + 1;
+    if (flags) {
+      if (empty) atomicOr(flags, 1);
+      if (sweep >= 60) atomicOr(flags, 2);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k; e += blockDim.x) counts[e] = 0;
+}
+
+ancka_status disc_argmax(const float* Qt, int ldt, int64_t n, int k, const DiscState& st, int32_t* labels,
+                         cudaStream_t s) {
+  const int G = pick_g(ldt / 4);
+  const unsigned grid = grid_for(n * G, 256);
+  switch (G) {
+    case 1: k_disc_argmax<1><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
+    case 2: k_disc_argmax<2><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
+    case 4: k_disc_argmax<4><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
+    case 8: k_disc_argmax<8><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
+    default: k_disc_argmax<16><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
+  }
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// labels -> counts, 1/sqrt(count), one-hot fills, trace, keep-best
+// ---------------------------------------------------------------------------
+__global__ void k_count_labels(const int32_t* __restrict__ labels, int64_t n, int k, int32_t* __restrict__ cnt) {
+  __shared__ int32_t hist[64];
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) hist[e] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&hist[labels[i]], 1);
+  __syncthreads();
+  for (int e = threadIdx.x; e < k; e += blockDim.x)
+    if (hist[e]) atomicAdd(&cnt[e], hist[e]);
+}
+
+__global__ void k_inv_sqrt_counts(const int32_t* __restrict__ cnt, int k, float* __restrict__ inv) {
+  const int c = threadIdx.x;
+  if (c < k) inv[c] = cnt[c] > 0 ? (float)(1.0 / sqrt((double)cnt[c])) : 0.f;
+}
+
+// Q^(0) = [n^-1/2 1 | h(Y^(0))] (col_off = 1) or F^(0) = alpha h(Y) (col_off = 0)
+__global__ void k_fill_onehot(const int32_t* __restrict__ labels, const float* __restrict__ inv, int64_t n,
+                              int ld, int col_off, float first_col, float scale, float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int64_t i = t / ld;
+  const int c = (int)(t % ld);
+  float v = 0.f;
+  if (col_off == 1 && c == 0) v = first_col;
+  const int y = labels[i];
+  if (c == y + col_off) v = scale * inv[y];
+  out[t] = v;
+}
+
+// per-CTA partial of tr(Yh^T F) = sum_i inv[y_i] F[i, y_i]
+__global__ void k_trace_partial(const float* __restrict__ F, int ld, const int32_t* __restrict__ labels,
+                                const float* __restrict__ inv, int64_t n, double* __restrict__ partial) {
+  __shared__ double ws[8];
+  double s = 0.0;
+  const int64_t per = ceil_div(n, (int64_t)gridDim.x);
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = (r0 + per < n) ? r0 + per : n;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const int y = labels[i];
+    s += (double)inv[y] * (double)F[i * ld + y];
+  }
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// phi = 1 - tr / k; keep-best decision (strictly lower phi wins)
+__global__ void k_phi_decide(const double* __restrict__ partial, int nblk, int k, double* __restrict__ phi_slot,
+                             double* __restrict__ phi_best, int32_t* __restrict__ take,
+                             int32_t* __restrict__ taken_slot, int first) {
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int b = 0; b < nblk; ++b) t += partial[b];
+  const double phi = 1.0 - t / (double)k;
+  *phi_slot = phi;
+  int tk = first ? 1 : (phi < *phi_best ? 1 : 0);
+  if (tk) *phi_best = phi;
+  *take = tk;
+  if (taken_slot) *taken_slot = first ? 0 : tk;
+}
+
+__global__ void k_copy_if(const int32_t* __restrict__ take, const int32_t* __restrict__ src,
+                          int32_t* __restrict__ dst, int64_t n) {
+  if (!*take) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+// row argmax (InitBCM g(v) of Eq. argmaxlabel), ties to the lowest column
+__global__ void k_argmax_rows(const float* __restrict__ P, int ld, int64_t n, int k, int32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = P + i * ld;
+  float b = p[0];
+  int bc = 0;
+  for (int c = 1; c < k; ++c)
+    if (p[c] > b) {
+      b = p[c];
+      bc = c;
+    }
+  out[i] = bc;
+}
+
+// V_c: keys (UINT32_MAX - degree, id) sorted ascending; the first k ids,
+// re-sorted by id, become the centres (reading R7)
+__global__ void k_degree_keys(const int32_t* __restrict__ deg, int64_t n, uint64_t* __restrict__ keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) keys[i] = ((uint64_t)(0xffffffffu - (uint32_t)deg[i]) << 32) | (uint32_t)i;
+}
+
+__global__ void k_seed_setup(const uint64_t* __restrict__ sorted, int k, int32_t* __restrict__ seedcol) {
+  if (threadIdx.x != 0) return;
+  int32_t ids[64];
+  for (int r = 0; r < k; ++r) ids[r] = (int32_t)(sorted[r] & 0xffffffffull);
+  for (int a = 1; a < k; ++a) {
+    int32_t v = ids[a];
+    int b = a - 1;
+    while (b >= 0 && ids[b] > v) {
+      ids[b + 1] = ids[b];
+      --b;
+    }
+    ids[b + 1] = v;
+  }
+  for (int r = 0; r < k; ++r) seedcol[ids[r]] = r;
+}
+
+__global__ void k_fill_seed(const int32_t* __restrict__ seedcol, int64_t n, int ld, float alpha,
+                            float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int64_t i = t / ld;
+  const int c = (int)(t % ld);
+  out[t] = (seedcol[i] == c) ? alpha : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers
+// ---------------------------------------------------------------------------
+struct Ctx {
+  const Walk& w;
+  int64_t n;
+  int k, ld, ldk;
+  float alpha;
+  float* E;       // hypergraph edge buffer (m x max(ld, ldk))
+  cudaStream_t s;
+};
+
+// Z = P Q (Eq. zt); with oh_labels: Z = coef P Q + oh_coef h(Y)
+ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float coef,
+                        const int32_t* oh_labels, const float* oh_inv, float oh_coef) {
+  const Walk& w = c.w;
+  SpmmArgs a;
+  a.nv4 = ld / 4;
+  a.nrows = c.n;
+  a.ldo = ld;
+  a.out = Z;
+  a.coef = coef;
+  a.oh_col = oh_labels;
+  a.oh_scale = oh_inv;
+  a.oh_coef = oh_coef;
+  a.ptrB = w.knn.ptr;
+  a.colB = w.knn.col;
+  a.valB = w.knn.val;
+  a.srcB = Q;
+  a.ldB = ld;
+  if (w.kind == ANCKA_HYPERGRAPH) {
+    SpmmArgs e;
+    e.ptrA = w.edges.ptr;
+    e.colA = w.edges.col;
+    e.rsA = w.inv_size;
+    e.srcA = Q;
+    e.ldA = ld;
+    e.out = c.E;
+    e.ldo = ld;
+    e.nrows = w.m;
+    e.nv4 = ld / 4;
+    ANCKA_TRY(spmm(e, c.s));
+    a.ptrA = w.topo.ptr;
+    a.colA = w.topo.col;
+    a.rsA = w.rs_topo;
+    a.srcA = c.E;
+    a.ldA = ld;
+  } else {
+    a.ptrA = w.topo.ptr;
+    a.colA = w.topo.col;
+    a.valA = w.topo.val;
+    a.rsA = w.rs_topo;
+    a.srcA = Q;
+    a.ldA = ld;
+  }
+  return spmm(a, c.s);
+}
+
+// Pi^T <- (1 - alpha) P_N^T Pi^T + alpha Z_0^T  (one InitBCM hop)
+ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_t* seedcol) {
+  const Walk& w = c.w;
+  SpmmArgs a;
+  a.nv4 = c.ldk / 4;
+  a.nrows = c.n;
+  a.ldo = c.ldk;
+  a.out = out;
+  a.coef = 1.f - c.alpha;
+  a.oh_col = seedcol;
+  a.oh_coef = c.alpha;
+  if (w.kind == ANCKA_HYPERGRAPH) {
+    SpmmArgs e;  // y_e = sum_{v in e} Pi[v] / delta_v
+    e.ptrA = w.edges.ptr;
+    e.colA = w.edges.col;
+    e.csA = w.inv_deg;
+    e.srcA = Pi;
+    e.ldA = c.ldk;
+    e.out = c.E;
+    e.ldo = c.ldk;
+    e.nrows = w.m;
+    e.nv4 = c.ldk / 4;
+    ANCKA_TRY(spmm(e, c.s));
+    a.ptrA = w.topo.ptr;  // sum_{e ni i} y_e / |e|
+    a.colA = w.topo.col;
+    a.csA = w.inv_size;
+    a.srcA = c.E;
+    a.ldA = c.ldk;
+  } else {
+    a.ptrA = w.topo.ptr;
+    a.colA = w.topo.col;
+    a.valA = w.topo.valT;
+    a.srcA = Pi;
+    a.ldA = c.ldk;
+  }
+  return spmm(a, c.s);
+}
+
+struct Scratch {
+  int32_t* cnt;        // k
+  float* inv;          // k
+  float* Fa;
+  float* Fb;           // n x ldk
+  double* tpart;       // trace partials
+  int tblk;
+  int32_t* take;       // 1
+};
+
+// CalMHC(Y) (Alg. 2): phi into phi_slot, keep-best into best_labels
+ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma, double* phi_slot,
+                     double* phi_best, int32_t* taken_slot, int32_t* best_labels, bool first) {
+  cudaStream_t s = c.s;
+  ANCKA_CUDA(cudaMemsetAsync(sc.cnt, 0, sizeof(int32_t) * c.k, s));
+  k_count_labels<<<grid_for(c.n, 1024) < 304 ? grid_for(c.n, 1024) : 304, 256, 0, s>>>(labels, c.n, c.k, sc.cnt);
+  ANCKA_LAUNCHED();
+  k_inv_sqrt_counts<<<1, 64, 0, s>>>(sc.cnt, c.k, sc.inv);
+  ANCKA_LAUNCHED();
+  k_fill_onehot<<<grid_for(c.n * c.ldk, 256), 256, 0, s>>>(labels, sc.inv, c.n, c.ldk, 0, 0.f, c.alpha, sc.Fa);
+  ANCKA_LAUNCHED();
+  float* cur = sc.Fa;
+  float* nxt = sc.Fb;
+  for (int l = 0; l < gamma; ++l) {  // F <- (1 - alpha) P F + alpha h(Y)
+    ANCKA_TRY(apply_walk(c, cur, c.ldk, nxt, 1.f - c.alpha, labels, sc.inv, c.alpha));
+    float* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  k_trace_partial<<<sc.tblk, 256, 0, s>>>(cur, c.ldk, labels, sc.inv, c.n, sc.tpart);
+  ANCKA_LAUNCHED();
+  k_phi_decide<<<1, 32, 0, s>>>(sc.tpart, sc.tblk, c.k, phi_slot, phi_best, sc.take, taken_slot, first ? 1 : 0);
+  ANCKA_LAUNCHED();
+  k_copy_if<<<grid_for(c.n, 256), 256, 0, s>>>(sc.take, labels, best_labels, c.n);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+ancka_status make_disc_state(Workspace& ws, int64_t n, int k, DiscState* st) {
+  ANCKA_TRY(ws.alloc(&st->Rf, (size_t)k * k));
+  ANCKA_TRY(ws.alloc(&st->counts, (size_t)k));
+  ANCKA_TRY(ws.alloc(&st->obj_prev, 1));
+  ANCKA_TRY(ws.alloc(&st->iter, 1));
+  ANCKA_TRY(ws.alloc(&st->done, 1));
+  st->rows_per_blk = 2048;
+  st->nblk = (int)ceil_div(n, st->rows_per_blk);
+  ANCKA_TRY(ws.alloc(&st->partial, (size_t)st->nblk * k * k));
+  return ANCKA_OK;
+}
+
+ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64_t n, int k, int max_iter,
+                            int32_t* labels, int32_t* iters_out, int32_t* flags, cudaStream_t s) {
+  k_disc_init<<<1, 256, 0, s>>>(st.Rf, st.counts, st.obj_prev, st.iter, st.done, k);
+  ANCKA_LAUNCHED();
+  const int nsl = 256 / k;
+  const size_t smem = (size_t)nsl * k * k * sizeof(float);
+  const int kp = (k + 1) & ~1;
+  const size_t svd_smem = (size_t)(k * kp + kp * kp) * sizeof(double);
+  static bool configured = false;
+  if (!configured) {
+    ANCKA_CUDA(cudaFuncSetAttribute(k_disc_msum, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 4096));
+    ANCKA_CUDA(cudaFuncSetAttribute(k_disc_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
+    configured = true;
+  }
+  for (int it = 0; it < max_iter; ++it) {
+    ANCKA_TRY(disc_argmax(Qt, ldt, n, k, st, labels, s));
+    k_disc_msum<<<st.nblk, 256, smem, s>>>(Qt, ldt, n, k, labels, st.rows_per_blk, st.partial, st.done);
+    ANCKA_LAUNCHED();
+    k_disc_svd<<<1, 1024, svd_smem, s>>>(st.partial, st.nblk, k, n, st.counts, st.Rf, st.obj_prev, st.iter, st.done,
+                                  iters_out, flags, max_iter);
+    ANCKA_LAUNCHED();
+  }
+  return ANCKA_OK;
+}
+
+// CholeskyQR2: Q = Z R^-1 twice (diag(R) > 0), result in *out
+ancka_status cholqr2(Workspace& ws, const Ctx& c, float* Z, float* Q, int w, double* gpart, int gblk,
+                     float* Rinv, int32_t* status) {
+  cudaStream_t s = c.s;
+  const size_t csmem = (size_t)3 * w * w * sizeof(double);
+  static bool configured = false;
+  if (!configured) {
+    ANCKA_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 65 * 65 * 8));
+    configured = true;
+  }
+  k_gram_partial<<<gblk, kGramThreads, 0, s>>>(Z, c.ld, c.n, w, gpart);
+  ANCKA_LAUNCHED();
+  k_chol_inv<<<1, 256, csmem, s>>>(gpart, gblk, w, Rinv, status);
+  ANCKA_LAUNCHED();
+  ANCKA_TRY(apply_rinv(Z, c.ld, c.n, w, Rinv, Q, s));
+  k_gram_partial<<<gblk, kGramThreads, 0, s>>>(Q, c.ld, c.n, w, gpart);
+  ANCKA_LAUNCHED();
+  k_chol_inv<<<1, 256, csmem, s>>>(gpart, gblk, w, Rinv, status);
+  ANCKA_LAUNCHED();
+  ANCKA_TRY(apply_rinv(Q, c.ld, c.n, w, Rinv, Z, s));
+  (void)ws;
+  return ANCKA_OK;
+}
+
+struct PhaseTimer {
+  IterTrace* tr;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  int phase;
+  PhaseTimer(IterTrace* t, cudaStream_t st, int ph) : tr(t), s(st), phase(ph) {
+    if (tr && tr->events) {
+      cudaEventCreate(&a);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~PhaseTimer() {
+    if (tr && tr->events) {
+      cudaEvent_t b;
+      cudaEventCreate(&b);
+      cudaEventRecord(b, s);
+      tr->events->push_back(a);
+      tr->events->push_back(b);
+      tr->phases->push_back(phase);
+    }
+  }
+};
+
+}  // namespace
+
+// phases: 2 = init, 3 = iteration, 4 = discretize, 5 = mhc
+ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const int32_t* init_labels,
+                       int32_t* labels_out, float* Q_out, int32_t* init_out, IterTrace* tr,
+                       cudaStream_t s) {
+  const int64_t n = w.n;
+  const int k = cfg.k;
+  const int wq = k + 1;
+  const int ld = (int)round_up(wq, 4);
+  const int ldk = (int)round_up(k, 4);
+  float *Qa, *Qb, *Qt, *E = nullptr, *Rinv;
+  ANCKA_TRY(ws.alloc(&Qa, (size_t)n * ld));
+  ANCKA_TRY(ws.alloc(&Qb, (size_t)n * ld));
+  ANCKA_TRY(ws.alloc(&Qt, (size_t)n * ldk));
+  ANCKA_TRY(ws.alloc(&Rinv, (size_t)wq * wq));
+  if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(ws.alloc(&E, (size_t)(w.m > 0 ? w.m : 1) * (ld > ldk ? ld : ldk)));
+  Ctx c{w, n, k, ld, ldk, cfg.alpha, E, s};
+  Scratch sc;
+  ANCKA_TRY(ws.alloc(&sc.cnt, 64));
+  ANCKA_TRY(ws.alloc(&sc.inv, 64));
+  ANCKA_TRY(ws.alloc(&sc.Fa, (size_t)n * ldk));
+  ANCKA_TRY(ws.alloc(&sc.Fb, (size_t)n * ldk));
+  sc.tblk = (int)(ceil_div(n, 4096) < 304 ? ceil_div(n, 4096) : 304);
+  ANCKA_TRY(ws.alloc(&sc.tpart, (size_t)sc.tblk));
+  ANCKA_TRY(ws.alloc(&sc.take, 1));
+  const int gblk = (int)(ceil_div(n, 512) < 304 ? ceil_div(n, 512) : 304);
+  double* gpart;
+  ANCKA_TRY(ws.alloc(&gpart, (size_t)gblk * wq * wq));
+  int32_t *y0, *yt, *ybest, *chol_status;
+  ANCKA_TRY(ws.alloc(&y0, (size_t)n));
+  ANCKA_TRY(ws.alloc(&yt, (size_t)n));
+  ANCKA_TRY(ws.alloc(&ybest, (size_t)n));
+  ANCKA_TRY(ws.zeros(&chol_status, 1));
+  DiscState st;
+  ANCKA_TRY(make_disc_state(ws, n, k, &st));
+
+  // ---- InitBCM (Alg. 4 lines 3-11) ----
+  {
+    PhaseTimer pt(tr, s, 2);
+    if (init_labels) {
+      ANCKA_CUDA(cudaMemcpyAsync(y0, init_labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      uint64_t *keys, *skeys;
+      int32_t* seedcol;
+      ANCKA_TRY(ws.alloc(&keys, (size_t)n));
+      ANCKA_TRY(ws.alloc(&skeys, (size_t)n));
+      ANCKA_TRY(ws.alloc(&seedcol, (size_t)n));
+      ANCKA_CUDA(cudaMemsetAsync(seedcol, 0xff, sizeof(int32_t) * n, s));
+      k_degree_keys<<<grid_for(n, 256), 256, 0, s>>>(w.degree, n, keys);
+      ANCKA_LAUNCHED();
+      size_t tmp = 0;
+      ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, keys, skeys, n, 0, 64, s));
+      char* t;
+      ANCKA_TRY(ws.alloc(&t, tmp));
+      ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, keys, skeys, n, 0, 64, s));
+      k_seed_setup<<<1, 32, 0, s>>>(skeys, k, seedcol);
+      ANCKA_LAUNCHED();
+      k_fill_seed<<<grid_for(n * ldk, 256), 256, 0, s>>>(seedcol, n, ldk, cfg.alpha, sc.Fa);
+      ANCKA_LAUNCHED();
+      float* cur = sc.Fa;
+      float* nxt = sc.Fb;
+      for (int t2 = 0; t2 < cfg.T_i; ++t2) {
+        ANCKA_TRY(initbcm_hop(c, cur, nxt, seedcol));
+        float* tt = cur;
+        cur = nxt;
+        nxt = tt;
+      }
+      k_argmax_rows<<<grid_for(n, 256), 256, 0, s>>>(cur, ldk, n, k, y0);
+      ANCKA_LAUNCHED();
+    }
+    if (init_out) ANCKA_CUDA(cudaMemcpyAsync(init_out, y0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    // Q^(0) = [n^-1/2 1 | h(Y^(0))]
+    ANCKA_CUDA(cudaMemsetAsync(sc.cnt, 0, sizeof(int32_t) * k, s));
+    k_count_labels<<<grid_for(n, 1024) < 304 ? grid_for(n, 1024) : 304, 256, 0, s>>>(y0, n, k, sc.cnt);
+    ANCKA_LAUNCHED();
+    k_inv_sqrt_counts<<<1, 64, 0, s>>>(sc.cnt, k, sc.inv);
+    ANCKA_LAUNCHED();
+    k_fill_onehot<<<grid_for(n * ld, 256), 256, 0, s>>>(y0, sc.inv, n, ld, 1, (float)(1.0 / sqrt((double)n)), 1.f, Qa);
+    ANCKA_LAUNCHED();
+  }
+  {  // phi(Y^(0)) (reading R8)
+    PhaseTimer pt(tr, s, 5);
+    ANCKA_TRY(cal_mhc(c, sc, y0, cfg.gamma, tr->phi_dev + 0, tr->phi_best_dev, nullptr, ybest, true));
+  }
+  int slot = 1;
+  float* Q = Qa;
+  float* Z = Qb;
+  for (int t = 1; t <= cfg.T; ++t) {
+    {
+      PhaseTimer pt(tr, s, 3);
+      ANCKA_TRY(apply_walk(c, Q, ld, Z, 1.f, nullptr, nullptr, 0.f));   // Z = P Q
+      ANCKA_TRY(cholqr2(ws, c, Z, Q, wq, gpart, gblk, Rinv, chol_status));  // result in Z
+      float* tt = Q;
+      Q = Z;
+      Z = tt;
+    }
+    if (t % cfg.tau == 0 || t == cfg.T) {
+      if (slot >= ANCKA_MAX_TRACE) {
+        set_error("too many Discretize calls for the trace (T / tau >= %d)", ANCKA_MAX_TRACE);
+        return ANCKA_ERR_INVALID_ARG;
+      }
+      {
+        PhaseTimer pt(tr, s, 4);
+        k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Q, ld, 1, n, k, Qt, ldk);
+        ANCKA_LAUNCHED();
+        ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, cfg.disc_max_iter, yt, tr->disc_iters_dev + slot,
+                                 tr->flags_dev, s));
+      }
+      {
+        PhaseTimer pt(tr, s, 5);
+        ANCKA_TRY(cal_mhc(c, sc, yt, cfg.gamma, tr->phi_dev + slot, tr->phi_best_dev, tr->taken_dev + slot,
+                          ybest, false));
+      }
+      ++slot;
+    }
+  }
+  tr->n_phi = slot;
+  ANCKA_CUDA(cudaMemcpyAsync(labels_out, ybest, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  if (Q_out) ANCKA_CUDA(cudaMemcpy2DAsync(Q_out, sizeof(float) * wq, Q, sizeof(float) * ld, sizeof(float) * wq, n,
+                                         cudaMemcpyDeviceToDevice, s));
+  // a singular Gram matrix is reported (numeric failure of CholeskyQR)
+  int32_t cs = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&cs, chol_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (cs) {
+    set_error("CholeskyQR: Gram matrix of Z is not positive definite (rank-deficient block)");
+    return ANCKA_ERR_NUMERIC;
+  }
+  return ANCKA_OK;
+}
+
+ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, int32_t ldq, int32_t max_iter,
+                        int32_t* labels, int32_t* iters_dev, int32_t* flags_dev, cudaStream_t s) {
+  const int ldk = (int)round_up(k, 4);
+  float* Qt;
+  ANCKA_TRY(ws.alloc(&Qt, (size_t)n * ldk));
+  k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qk, ldq, 0, n, k, Qt, ldk);
+  ANCKA_LAUNCHED();
+  DiscState st;
+  ANCKA_TRY(make_disc_state(ws, n, k, &st));
+  return run_discretize(st, Qt, ldk, n, k, max_iter, labels, iters_dev, flags_dev, s);
+}
+
+}  // namespace ancka

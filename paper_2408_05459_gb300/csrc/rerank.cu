@@ -1,0 +1,233 @@
+// Exact KNN lists from low-precision candidates (Section 3.1, reading R2).
+//
+// Row i comes out of the contraction with its kCandC best approximate scores
+// s^_ij and the worst kept one, thr_i.  With the per-pair error bound
+//     |cos_ij - s^_ij| <= m_ij = e_i (1 + e_j) + e_j + acc (1 + e_i)(1 + e_j)
+// (e = quantisation bound of the row copies, acc = accumulation bound of the
+// contraction) the K-th largest lower bound lb_i = K-th max (s^ - m) is a
+// lower bound of the true K-th similarity.  Candidates with s^ + m < lb and
+// every non-candidate (s^ <= thr_i) when thr_i + m_max < lb cannot be in the
+// list.  The remaining candidates are re-scored with a compensated (Dot2)
+// dot product of the raw FP32 rows, evaluated in double, and sorted by
+// (cosine desc, index asc).  A row that fails the certificate is flagged and
+// recomputed exhaustively by k_knn_exhaustive.
+#include "common.cuh"
+
+namespace ancka {
+
+namespace {
+
+constexpr int kWarps = 8;
+
+struct Key {
+  double v;
+  int32_t j;
+};
+
+__device__ __forceinline__ bool before(double a, int32_t ia, double b, int32_t ib) {
+  return a > b || (a == b && ia < ib);
+}
+
+// bitonic sort of one (value, index) pair per lane: lane 0 ends with the
+// first element of the (value desc, index asc) order.
+__device__ __forceinline__ void warp_sort(double& v, int32_t& j) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int s = k >> 1; s > 0; s >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, v, s);
+      int32_t oj = __shfl_xor_sync(0xffffffffu, j, s);
+      bool lower = (lane & s) == 0;
+      bool dir = (lane & k) == 0;
+      bool self_first = before(v, j, ov, oj);
+      bool take = (lower == dir) ? !self_first : self_first;
+      if (take) {
+        v = ov;
+        j = oj;
+      }
+    }
+  }
+}
+
+// exact cosine of rows i and j with a warp: Dot2 partials, fixed-order merge
+__device__ __forceinline__ double exact_cos(const float* __restrict__ xi, const float* __restrict__ xj,
+                                            int d, double n2i, double n2j) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f, c = 0.f;
+  for (int t = lane; t < d; t += 32) dot2_step(s, c, xi[t], xj[t]);
+  dot2_warp_reduce(s, c);
+  if (n2i <= 0.0 || n2j <= 0.0) return 0.0;
+  double dot = (double)s + (double)c;
+  return dot / (sqrt(n2i) * sqrt(n2j));
+}
+
+__global__ void __launch_bounds__(kWarps * 32)
+k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __restrict__ err,
+         const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ nrm2,
+         const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx,
+         int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ fb_rows,
+         int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand) {
+  __shared__ unsigned int block_cand;
+  if (threadIdx.x == 0) block_cand = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (i < n) {
+    float v = cand_val[i * kCandC + lane];
+    int32_t j = cand_idx[i * kCandC + lane];
+    const bool valid = j >= 0;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const int nvalid = __popc(vmask);
+    const float ei = err[i], emax = *err_max_p;
+    const float ej = valid ? err[j] : 0.f;
+    const float m = ei * (1.f + ej) + ej + acc_coef * (1.f + ei) * (1.f + ej);
+    const float lower = valid ? v - m : -INFINITY;
+    const float upper = valid ? v + m : -INFINITY;
+    // K-th largest lower bound (ties by lane)
+    int rank = 0;
+    for (int t = 0; t < 32; ++t) {
+      float o = __shfl_sync(0xffffffffu, lower, t);
+      rank += (o > lower) || (o == lower && t < lane);
+    }
+    const unsigned kmask = __ballot_sync(0xffffffffu, rank == K - 1);
+    const float lb = __shfl_sync(0xffffffffu, lower, __ffs(kmask) - 1);
+    bool ok = nvalid >= K;
+    if (nvalid < n - 1) {  // there are nodes outside the candidate list
+      float thr = valid ? v : INFINITY;
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) thr = fminf(thr, __shfl_xor_sync(0xffffffffu, thr, off));
+      const float mmax = ei * (1.f + emax) + emax + acc_coef * (1.f + ei) * (1.f + emax);
+      // strict: every outside node's cosine is < lb <= the true K-th value
+      ok = ok && (thr + mmax < lb);
+    }
+    if (!ok) {
+      if (lane == 0) fb_rows[atomicAdd(fb_count, 1)] = (int32_t)i;
+    } else {
+      const bool inR = valid && upper >= lb;
+      unsigned rmask = __ballot_sync(0xffffffffu, inR);
+      if (lane == 0) atomicAdd(&block_cand, (unsigned)__popc(rmask));
+      const float* xi = X + i * (int64_t)d;
+      const double n2i = nrm2[i];
+      double myv = -INFINITY;
+      int32_t myj = INT32_MAX;
+      while (rmask) {
+        const int t = __ffs(rmask) - 1;
+        rmask &= rmask - 1;
+        const int32_t jt = __shfl_sync(0xffffffffu, j, t);
+        const double cs = exact_cos(xi, X + (int64_t)jt * d, d, n2i, nrm2[jt]);
+        if (lane == t) {
+          myv = cs;
+          myj = jt;
+        }
+      }
+      warp_sort(myv, myj);
+      if (lane < K) {
+        out_idx[i * K + lane] = myj;
+        out_sim[i * K + lane] = (float)myv;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && n_cand) atomicAdd(n_cand, (unsigned long long)block_cand);
+}
+
+// Exhaustive exact list for the flagged rows (or every row when K exceeds
+// what the candidate list can certify).  One CTA per row; each warp keeps a
+// sorted top-K of its own strided share of the keys in shared memory, and
+// thread 0 merges the warp lists.
+constexpr int kExWarps = 8;
+constexpr int kMaxK = 64;
+
+__global__ void __launch_bounds__(kExWarps * 32)
+k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const double* __restrict__ nrm2,
+                 const int32_t* __restrict__ rows, const int32_t* __restrict__ row_count,
+                 int64_t all_rows, int32_t* __restrict__ out_idx, float* __restrict__ out_sim) {
+  __shared__ double lv[kExWarps][kMaxK];
+  __shared__ int32_t li[kExWarps][kMaxK];
+  __shared__ int head[kExWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t count = rows ? (int64_t)*row_count : all_rows;
+  for (int64_t r = blockIdx.x; r < count; r += gridDim.x) {
+    const int64_t i = rows ? rows[r] : r;
+    for (int t = threadIdx.x; t < kExWarps * kMaxK; t += blockDim.x) {
+      lv[t / kMaxK][t % kMaxK] = -INFINITY;
+      li[t / kMaxK][t % kMaxK] = INT32_MAX;
+    }
+    __syncthreads();
+    const float* xi = X + i * (int64_t)d;
+    const double n2i = nrm2[i];
+    for (int64_t j = w; j < n; j += kExWarps) {
+      if (j == i) continue;
+      const double cs = exact_cos(xi, X + j * (int64_t)d, d, n2i, nrm2[j]);
+      if (lane == 0 && before(cs, (int32_t)j, lv[w][K - 1], li[w][K - 1])) {
+        int p = K - 1;
+        while (p > 0 && before(cs, (int32_t)j, lv[w][p - 1], li[w][p - 1])) {
+          lv[w][p] = lv[w][p - 1];
+          li[w][p] = li[w][p - 1];
+          --p;
+        }
+        lv[w][p] = cs;
+        li[w][p] = (int32_t)j;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < kExWarps; ++q) head[q] = 0;
+      for (int o = 0; o < K; ++o) {
+        int best = -1;
+        for (int q = 0; q < kExWarps; ++q) {
+          if (head[q] >= K) continue;
+          if (best < 0 || before(lv[q][head[q]], li[q][head[q]], lv[best][head[best]], li[best][head[best]]))
+            best = q;
+        }
+        out_idx[i * K + o] = li[best][head[best]];
+        out_sim[i * K + o] = (float)lv[best][head[best]];
+        ++head[best];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
+                        const PrepOut& pr, float acc_coef, const float* cand_val,
+                        const int32_t* cand_idx, int32_t* out_idx, float* out_sim,
+                        int64_t* n_candidates, int64_t* n_fallback, bool want_counts,
+                        cudaStream_t s) {
+  int32_t *fb_rows, *fb_count;
+  unsigned long long* ncand;
+  ANCKA_TRY(ws.alloc(&fb_rows, (size_t)n));
+  ANCKA_TRY(ws.zeros(&fb_count, 1));
+  ANCKA_TRY(ws.zeros(&ncand, 1));
+  const bool use_candidates = cand_val != nullptr;
+  if (use_candidates) {
+    k_rerank<<<(unsigned)ceil_div(n, kWarps), kWarps * 32, 0, s>>>(
+        X, n, d, K, pr.err, pr.err_max, acc_coef, pr.nrm2, cand_val, cand_idx, out_idx, out_sim,
+        fb_rows, fb_count, ncand);
+    ANCKA_LAUNCHED();
+    k_knn_exhaustive<<<304, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, fb_rows, fb_count, 0, out_idx,
+                                                   out_sim);
+    ANCKA_LAUNCHED();
+  } else {
+    const unsigned g = (unsigned)(n < 4096 ? n : 4096);
+    k_knn_exhaustive<<<g, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, nullptr, nullptr, n, out_idx,
+                                                 out_sim);
+    ANCKA_LAUNCHED();
+  }
+  if (want_counts) {
+    int32_t fb = 0;
+    unsigned long long nc = 0;
+    ANCKA_CUDA(cudaMemcpyAsync(&fb, fb_count, sizeof(fb), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&nc, ncand, sizeof(nc), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    *n_fallback = use_candidates ? fb : n;
+    *n_candidates = (int64_t)nc;
+  }
+  return ANCKA_OK;
+}
+
+}  // namespace ancka

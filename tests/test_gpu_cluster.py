@@ -1,0 +1,162 @@
+"""End-to-end parity of ancka_cluster / ancka_cluster_with_knn / ancka_discretize
+(through the C ABI) against the FP64 oracle's Algorithm 4."""
+import numpy as np
+import pytest
+
+from oracle import ancka_oracle as O
+from paper_2408_05459_gb300 import synth
+from tests.parity_util import ANGLE_MAX, ARI_MIN, compare_iteration, compare_knn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ak():
+    from paper_2408_05459_gb300 import ancka
+    ancka.load()
+    return ancka
+
+
+def _params(ak, **kw):
+    return ak.default_params(**kw)
+
+
+def _gpu_cluster(ak, g, prec="fp32", knn=None, init=None, **kw):
+    k = kw.pop("k", g["k"])
+    p = _params(ak, k=k, knn_prec=prec, **kw)
+    td = ak.topology_to_device(g)
+    X = torch.as_tensor(g["X"], device="cuda")
+    kl = None
+    if knn is not None:
+        kl = (torch.as_tensor(np.ascontiguousarray(knn[0], np.int32), device="cuda"),
+              torch.as_tensor(np.ascontiguousarray(knn[1], np.float32), device="cuda"))
+    il = torch.as_tensor(init.astype(np.int32), device="cuda") if init is not None else None
+    labels, ex, info = ak.cluster(td, X, p, knn_lists=kl, want_Q=True, want_init=True,
+                                  want_knn=knn is None, init_labels=il)
+    torch.cuda.synchronize()
+    out = {key: v.cpu().numpy() for key, v in ex.items()}
+    return labels.cpu().numpy(), out, info
+
+
+def _oracle_params(p):
+    return dict(k=p.k, K=p.K, alpha=p.alpha, beta=p.beta, T=p.T, gamma=p.gamma, T_i=p.T_i, tau=p.tau,
+                disc_max_iter=p.disc_max_iter)
+
+
+def _check(ak, g, prec="fp32", **kw):
+    labels, ex, info = _gpu_cluster(ak, g, prec, **kw)
+    p = _params(ak, k=kw.get("k", g["k"]), **{k: v for k, v in kw.items() if k != "k"})
+    o = O.ancka(g, g["X"], _oracle_params(p), knn=ex["knn_idx"])
+    # the KNN lists fed to the oracle iteration are themselves checked
+    n = g["n"]
+    rows = np.arange(n) if n <= 4000 else np.random.default_rng(0).choice(n, 256, replace=False)
+    compare_knn(g["X"], p.K, rows, ex["knn_idx"], ex["knn_sim"])
+    assert np.array_equal(ex["init_labels"], o["init_labels"])
+    ari, ang = compare_iteration(o, labels, ex["Q"])
+    assert ang <= ANGLE_MAX, ang
+    assert ari >= ARI_MIN, ari
+    assert info["n_phi"] == len(o["phi"])
+    assert np.allclose(info["phi"], o["phi"], atol=1e-4)
+    return labels, o, info
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_small_sbm_config(ak, prec):
+    g = synth.config_small_sbm(0)
+    labels, o, info = _check(ak, g, prec)
+    assert O.adjusted_rand_index(labels, g["labels"]) > 0.9
+
+
+def test_small_hypergraph(ak):
+    g = synth.hypergraph_tfidf(3000, 6, 5000, 64, 6, seed=3)
+    _check(ak, g, "fp32", k=6)
+
+
+def test_small_multiplex(ak):
+    g = synth.multiplex_sbm(2500, 4, 12.0, (6.0, 3.0), 32, 2.0, seed=4)
+    _check(ak, g, "fp32", k=4)
+
+
+def test_directed_graph(ak):
+    rng = np.random.default_rng(5)
+    n = 1500
+    src = rng.integers(0, n, 9000)
+    dst = (src + rng.integers(1, 40, 9000)) % n      # local, one direction only
+    rp, col = synth.csr_from_edges(n, src, dst, symmetric=False)
+    X = synth.gaussian_mixture(rng, rng.integers(0, 3, n), 3, 16, 1.0)
+    g = dict(kind="graph", n=n, k=3, X=X, layers=[(rp, col)], directed=1)
+    _check(ak, g, "fp32", k=3)
+
+
+def test_odd_k_and_ragged_sizes(ak):
+    g = synth.sbm_graph(1234, 7, 0.02, 0.002, 40, 1.0, seed=6)
+    _check(ak, g, "fp32", k=7, T=7, tau=3, gamma=2, T_i=9, K=5)
+
+
+def test_cliques_closed_form_on_gpu(ak):
+    k, c = 5, 24
+    g = synth.cliques_closed_form(k, c, seed=7)
+    init = np.random.default_rng(8).integers(0, k, k * c)
+    labels, ex, _ = _gpu_cluster(ak, g, "fp32", init=init, k=k, K=6, T=40, tau=5)
+    assert O.adjusted_rand_index(labels, g["labels"]) == 1.0
+    ind = O.bcm(g["labels"], k)
+    assert O.max_principal_angle(ex["Q"][:, :k].astype(np.float64), ind) < 1e-3
+
+
+def test_cluster_host_matches_device(ak):
+    g = synth.config_small_sbm(1)
+    p = _params(ak, k=5, knn_prec="fp32")
+    lab_h, info_h = ak.cluster_host(g, g["X"], p)
+    lab_d, _, _ = _gpu_cluster(ak, g, "fp32")
+    assert np.array_equal(lab_h, lab_d)
+    assert info_h["ms_total"] > 0
+
+
+def test_deterministic_runs(ak):
+    g = synth.config_small_sbm(2)
+    a = _gpu_cluster(ak, g, "fp32")
+    b = _gpu_cluster(ak, g, "fp32")
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1]["Q"], b[1]["Q"])
+
+
+def test_discretize_entry_point(ak):
+    rng = np.random.default_rng(9)
+    n, k = 5000, 8
+    truth = rng.integers(0, k, n)
+    Qk = O.bcm(truth, k) @ np.linalg.qr(rng.standard_normal((k, k)))[0] * 0.3 + 0.05 * rng.standard_normal((n, k))
+    lab, iters = ak.discretize(torch.as_tensor(Qk.astype(np.float32), device="cuda"))
+    o_lab, objs, _ = O.discretize(Qk.astype(np.float32).astype(np.float64), 20, return_trace=True)
+    assert O.adjusted_rand_index(lab.cpu().numpy(), o_lab) >= 0.999
+    assert iters == len(objs)
+
+
+def test_hypergraph_workload_with_verified_knn(ak):
+    """Full-size hypergraph (n = 1e5): GPU KNN checked on sampled rows, then the
+    oracle iteration on the same lists vs ancka_cluster_with_knn."""
+    g = synth.config_hypergraph(0)
+    labels, ex, info = _gpu_cluster(ak, g, "fp32", k=10)
+    rows = np.random.default_rng(1).choice(g["n"], 128, replace=False)
+    compare_knn(g["X"], 10, rows, ex["knn_idx"], ex["knn_sim"])
+    o = O.ancka(g, g["X"], dict(k=10), knn=ex["knn_idx"])
+    ari, ang = compare_iteration(o, labels, ex["Q"])
+    assert ang <= ANGLE_MAX and ari >= ARI_MIN, (ari, ang)
+    assert np.array_equal(ex["init_labels"], o["init_labels"])
+
+
+def test_invalid_arguments(ak):
+    g = synth.config_small_sbm(0)
+    with pytest.raises(ak.AnckaError) as e:
+        _gpu_cluster(ak, g, "fp32", k=65)
+    assert e.value.status == 1
+    with pytest.raises(ak.AnckaError) as e:
+        _gpu_cluster(ak, g, "fp32", alpha=0.0)
+    assert e.value.status == 1
+    bad = dict(g)
+    rp, col = g["layers"][0]
+    col = col.copy()
+    col[5] = g["n"] + 3
+    bad["layers"] = [(rp, col)]
+    with pytest.raises(ak.AnckaError) as e:
+        _gpu_cluster(ak, bad, "fp32")
+    assert e.value.status == 1

@@ -1,0 +1,96 @@
+"""KNN parity of the CUDA path (ancka_knn through the C ABI) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import ancka_oracle as O
+from paper_2408_05459_gb300 import synth
+from tests.parity_util import compare_knn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32", "bf16"]
+
+
+@pytest.fixture(scope="module")
+def ak():
+    from paper_2408_05459_gb300 import ancka
+    ancka.load()
+    return ancka
+
+
+def _run(ak, X, K, prec):
+    Xd = torch.as_tensor(np.ascontiguousarray(X, np.float32), device="cuda")
+    idx, sim, info = ak.knn(Xd, K, prec)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), sim.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,d,K", [(2000, 128, 10), (300, 5, 4), (129, 64, 16), (1000, 100, 10), (777, 130, 7)])
+def test_knn_random_shapes(ak, prec, n, d, K):
+    rng = np.random.default_rng(n + d + K)
+    labels = rng.integers(0, 5, n)
+    X = synth.gaussian_mixture(rng, labels, 5, d, 1.5)
+    idx, sim, info = _run(ak, X, K, prec)
+    c = compare_knn(X, K, np.arange(n), idx, sim)
+    assert c["exact_rows"] + c["near_tie_rows"] == n
+    assert info["knn_fallback_rows"] <= n // 20
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_knn_edge_cases(ak, prec):
+    rng = np.random.default_rng(7)
+    n, d, K = 260, 33, 6
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    X[3] = 0.0                     # zero row: all similarities 0, lowest indices win
+    X[10] = X[20] = X[30]          # exact duplicates: similarity-1 ties
+    X[40] = 3.0 * X[41]            # scaled copy
+    X[255:] = np.abs(X[255:])      # ragged tail rows
+    idx, sim, _ = _run(ak, X, K, prec)
+    compare_knn(X, K, np.arange(n), idx, sim)
+    assert idx[3].tolist() == [j for j in range(n) if j != 3][:K]
+    assert np.all(sim[3] == 0.0)
+    assert set(idx[30][:2].tolist()) == {10, 20}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_knn_tiny_and_large_K(ak, prec):
+    X = np.random.default_rng(1).standard_normal((3, 4)).astype(np.float32)
+    idx, sim, _ = _run(ak, X, 2, prec)
+    compare_knn(X, 2, np.arange(3), idx, sim)
+    # K beyond the candidate list: the exhaustive exact path
+    X = np.random.default_rng(2).standard_normal((400, 24)).astype(np.float32)
+    idx, sim, info = _run(ak, X, 40, prec)
+    compare_knn(X, 40, np.arange(400), idx, sim)
+    assert info["knn_fallback_rows"] == 400
+
+
+def test_knn_hypergraph_workload_sampled(ak):
+    """Full-size sparse TF-IDF attributes (n = 1e5, d = 500) on sampled rows."""
+    g = synth.config_hypergraph(0)
+    X = g["X"]
+    rows = np.random.default_rng(11).choice(X.shape[0], 192, replace=False)
+    for prec in PRECS:
+        idx, sim, info = _run(ak, X, 10, prec)
+        c = compare_knn(X, 10, rows, idx, sim)
+        assert c["exact_rows"] + c["near_tie_rows"] == rows.size
+        assert info["knn_fallback_rows"] < X.shape[0] // 100
+
+
+def test_knn_invalid_arguments(ak):
+    X = torch.zeros((5, 3), device="cuda")
+    with pytest.raises(ak.AnckaError) as e:
+        ak.knn(X, 5, "fp32")      # K >= n
+    assert e.value.status == 1
+    with pytest.raises(ak.AnckaError) as e:
+        ak.knn(X, 0, "fp32")
+    assert e.value.status == 1
+
+
+def test_knn_deterministic(ak):
+    X = np.random.default_rng(3).standard_normal((1500, 77)).astype(np.float32)
+    for prec in PRECS:
+        a = _run(ak, X, 9, prec)
+        b = _run(ak, X, 9, prec)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
