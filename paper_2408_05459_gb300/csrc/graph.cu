@@ -60,6 +60,17 @@ ancka_status exclusive_scan(Workspace& ws, const T* in, T* out, int64_t count, c
   return ANCKA_OK;
 }
 
+ancka_status check_bad(const int32_t* bad, cudaStream_t s, const char* fmt, int arg = 0) {
+  int32_t h = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    set_error(fmt, arg);
+    return ANCKA_ERR_INVALID_ARG;
+  }
+  return ANCKA_OK;
+}
+
 ancka_status read_count(const int64_t* dev, int64_t* host, cudaStream_t s) {
   ANCKA_CUDA(cudaMemcpyAsync(host, dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   ANCKA_CUDA(cudaStreamSynchronize(s));
@@ -67,6 +78,16 @@ ancka_status read_count(const int64_t* dev, int64_t* host, cudaStream_t s) {
 }
 
 // --- kernels -----------------------------------------------------------------
+// a row pointer must start at >= 0, never decrease, and end at <= limit
+__global__ void k_check_ptr(const int64_t* __restrict__ ptr, int64_t rows, int64_t limit,
+                            int32_t* __restrict__ bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > rows) return;
+  if (i == 0 && ptr[0] < 0) atomicExch(bad, 1);
+  if (i == rows && limit >= 0 && ptr[rows] > limit) atomicExch(bad, 1);
+  if (i < rows && ptr[i] > ptr[i + 1]) atomicExch(bad, 1);
+}
+
 __global__ void k_csr_to_keys(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                               int64_t n, int directed, uint64_t* __restrict__ keys,
                               int32_t* __restrict__ bad) {
@@ -266,6 +287,9 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
   if (t.kind == ANCKA_HYPERGRAPH) {
     const int64_t m = t.m;
     w->m = m;
+    k_check_ptr<<<grid_for(m + 1, 256), 256, 0, s>>>(t.he_ptr, m, -1, bad);
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(check_bad(bad, s, "hyperedge pointer must be non-negative and non-decreasing"));
     int64_t nnz = 0;
     ANCKA_CUDA(cudaMemcpyAsync(&nnz, t.he_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     int64_t base = 0;
@@ -278,11 +302,12 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     ANCKA_TRY(ws.alloc(&k2, (size_t)nnz));
     k_hyper_to_keys<<<grid_for(m, 256), 256, 0, s>>>(t.he_ptr, t.he_nodes, m, n, k0, bad);
     ANCKA_LAUNCHED();
+    ANCKA_TRY(check_bad(bad, s, "topology: node id out of range [0, n)"));
     const int mb = bits_for(m);
     ANCKA_TRY(sort_keys(ws, k0, k1, nnz, 32 + mb, s));
     int64_t* ucnt_dev;
-    ANCKA_TRY(ws.alloc(&ucnt_dev, 1));
-    ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, nnz, s));
+    ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
+    if (nnz > 0) ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, nnz, s));
     int64_t ucnt = 0;
     ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
     int32_t* esize;
@@ -307,6 +332,9 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     std::vector<const int32_t*> ldeg(L);
     for (int l = 0; l < L; ++l) {
       const int64_t* rp = t.row_ptr + (int64_t)l * (n + 1);
+      k_check_ptr<<<grid_for(n + 1, 256), 256, 0, s>>>(rp, n, t.nnz, bad);
+      ANCKA_LAUNCHED();
+      ANCKA_TRY(check_bad(bad, s, "row pointer of layer %d must be non-decreasing within [0, nnz]", l));
       int64_t b = 0, e = 0;
       ANCKA_CUDA(cudaMemcpyAsync(&b, rp, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       ANCKA_CUDA(cudaMemcpyAsync(&e, rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -318,10 +346,11 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
       ANCKA_TRY(ws.alloc(&k2, (size_t)cnt));
       k_csr_to_keys<<<grid_for(n, 256), 256, 0, s>>>(rp, t.col_idx, n, t.directed, k0, bad);
       ANCKA_LAUNCHED();
+      ANCKA_TRY(check_bad(bad, s, "topology: node id out of range [0, n)"));
       ANCKA_TRY(sort_keys(ws, k0, k1, cnt, 32 + nb, s));
       int64_t* ucnt_dev;
-      ANCKA_TRY(ws.alloc(&ucnt_dev, 1));
-      ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, cnt, s));
+      ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
+      if (cnt > 0) ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, cnt, s));
       int64_t ucnt = 0;
       ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
       Csr lay;
@@ -360,13 +389,6 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     k_merge_layers<<<grid_for(n, 256), 256, 0, s>>>(L, n, dlptr, dlcol, dldeg, w->topo.ptr,
                                                     w->topo.col, w->topo.val, w->topo.valT);
     ANCKA_LAUNCHED();
-  }
-  int32_t hbad = 0;
-  ANCKA_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ANCKA_CUDA(cudaStreamSynchronize(s));
-  if (hbad) {
-    set_error("topology: node id out of range [0, n)");
-    return ANCKA_ERR_INVALID_ARG;
   }
   return ANCKA_OK;
 }
