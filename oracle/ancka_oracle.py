@@ -43,6 +43,13 @@ R11 directed graph input is made symmetric and binary (A or A^T); repeated
     entries in an adjacency or a hyperedge count once; a node with no
     neighbours in a layer contributes a zero row for that layer.
 R12 h(Y) = (Y^T Y)^{-1/2} Y with an empty cluster giving a zero column.
+R13 Q^(0) = [n^{-1/2} 1 | h(Y^(0))] has rank k, not k+1: 1 = sum_c
+    sqrt(|C_c|) h(Y)_c lies in the span of h(Y), and an empty cluster adds a
+    zero column.  For the QR of Alg. 4 to be defined the dependent columns are
+    replaced, keeping span(h(Y^(0))): the column of the highest-index
+    non-empty cluster and the column of every empty cluster c become the sign
+    vector s_i / sqrt(n), s_i = +1 or -1 from the top bit of
+    splitmix64(64 i + c) (Steele, Lea, Flood 2014; Vigna's constants).
 """
 from __future__ import annotations
 
@@ -269,6 +276,27 @@ def _inv_sqrt_or_zero(c):
     return out
 
 
+def splitmix64(x):
+    """One output of the splitmix64 generator for state x (uint64 array)."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, np.uint64) + np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def initial_block(labels, k):
+    """Q^(0) = [n^{-1/2} 1 | h(Y^(0))] (Alg. 4 line 12) with reading R13."""
+    n = labels.size
+    Q = np.concatenate([np.full((n, 1), 1.0 / np.sqrt(n)), h_norm(labels, k)], axis=1)
+    counts = np.bincount(labels, minlength=k)
+    dependent = list(np.nonzero(counts == 0)[0]) + [int(np.nonzero(counts > 0)[0].max())]
+    for c in dependent:
+        bits = splitmix64(np.arange(n, dtype=np.uint64) * np.uint64(64) + np.uint64(c)) >> np.uint64(63)
+        Q[:, 1 + c] = np.where(bits == 1, -1.0, 1.0) / np.sqrt(n)
+    return Q
+
+
 def argmax_rows(M):
     """Row argmax with ties to the lowest column (R6); np.argmax does that."""
     return np.argmax(M, axis=1).astype(np.int64)
@@ -414,7 +442,7 @@ def ancka(topo_dict, X, params=None, knn=None, init_labels=None):
         y0, Vc = np.asarray(init_labels, np.int64), None
     Y_best = y0.copy()
     phi_best = cal_mhc(P, y0, k, alpha, gamma)       # reading R8
-    Q = np.concatenate([np.full((n, 1), 1.0 / np.sqrt(n)), h_norm(y0, k)], axis=1)
+    Q = initial_block(y0, k)
     phis = [phi_best]
     disc_iters = []
     taken = []

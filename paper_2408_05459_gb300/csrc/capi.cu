@@ -38,6 +38,9 @@ namespace {
   } while (0)
 
 ancka_status device_check() {
+  // discard a non-sticky error left by an unrelated earlier runtime call, so
+  // that the launch checks of this call only see this call's failures
+  cudaGetLastError();
   int dev = 0;
   ANCKA_CUDA(cudaGetDevice(&dev));
   static std::mutex mu;
@@ -100,6 +103,7 @@ void fill_times(Timer& t, ancka_info* info) {
   }
   for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
   t.ev.clear();
+  cudaGetLastError();
   if (info) {
     info->ms_knn = acc[0];
     info->ms_build = acc[1];
@@ -314,8 +318,8 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       st = run_ancka(ws, w, cfg, p->init == 1 ? p->init_labels : nullptr, labels, out ? out->Q : nullptr,
                      out ? out->init_labels : nullptr, &tr, s);
     }
+    if (info) cudaEventRecord(t1, s);
     if (info && (st == ANCKA_OK || st == ANCKA_ERR_NUMERIC)) {
-      cudaEventRecord(t1, s);
       cudaMemcpyAsync(info->phi, tr.phi_dev, sizeof(double) * ANCKA_MAX_TRACE, cudaMemcpyDeviceToHost, s);
       cudaMemcpyAsync(info->disc_iters, tr.disc_iters_dev, sizeof(int32_t) * ANCKA_MAX_TRACE,
                       cudaMemcpyDeviceToHost, s);
@@ -336,7 +340,9 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     float tot = 0.f;
     if (cudaEventElapsedTime(&tot, t0, t1) == cudaSuccess) info->ms_total = tot;
     float mc = 0.f;
-    if (contract_timed && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;
+    if (contract_timed && st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess)
+      info->ms_contract = mc;
+    cudaGetLastError();  // an event of a failed call may never have been recorded
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     cudaEventDestroy(cev[0]);
@@ -431,7 +437,8 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
     info->knn_fallback_rows = nf;
     if (timed) {
       float mc = 0.f;
-      if (cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;
+      if (st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;
+      cudaGetLastError();
       cudaEventDestroy(cev[0]);
       cudaEventDestroy(cev[1]);
     }

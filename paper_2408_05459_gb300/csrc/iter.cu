@@ -575,9 +575,23 @@ __global__ void k_inv_sqrt_counts(const int32_t* __restrict__ cnt, int k, float*
   if (c < k) inv[c] = cnt[c] > 0 ? (float)(1.0 / sqrt((double)cnt[c])) : 0.f;
 }
 
-// Q^(0) = [n^-1/2 1 | h(Y^(0))] (col_off = 1) or F^(0) = alpha h(Y) (col_off = 0)
-__global__ void k_fill_onehot(const int32_t* __restrict__ labels, const float* __restrict__ inv, int64_t n,
-                              int ld, int col_off, float first_col, float scale, float* __restrict__ out) {
+// splitmix64 (Steele, Lea, Flood 2014): one output for state x
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Q^(0) = [n^-1/2 1 | h(Y^(0))] (col_off = 1) or F^(0) = alpha h(Y) (col_off = 0).
+// [n^-1/2 1 | h(Y)] has rank k only (1 = sum_c sqrt|C_c| h(Y)_c, and an empty
+// cluster gives a zero column), so the QR would be undefined: the column of
+// the highest-index non-empty cluster and of every empty cluster c becomes
+// the sign vector +-n^-1/2 from the top bit of splitmix64(64 i + c), which
+// keeps span(h(Y)) and gives Q^(0) full rank.
+__global__ void k_fill_onehot(const int32_t* __restrict__ labels, const float* __restrict__ inv,
+                              const int32_t* __restrict__ cnt, int k, int64_t n, int ld, int col_off,
+                              float first_col, float scale, float* __restrict__ out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * ld) return;
   const int64_t i = t / ld;
@@ -586,6 +600,13 @@ __global__ void k_fill_onehot(const int32_t* __restrict__ labels, const float* _
   if (col_off == 1 && c == 0) v = first_col;
   const int y = labels[i];
   if (c == y + col_off) v = scale * inv[y];
+  if (col_off == 1 && c >= 1 && c <= k) {
+    int last = 0;
+    for (int q = 0; q < k; ++q)
+      if (cnt[q] > 0) last = q;
+    if (cnt[c - 1] == 0 || c - 1 == last)
+      v = (splitmix64((uint64_t)i * 64u + (uint64_t)(c - 1)) >> 63) ? -first_col : first_col;
+  }
   out[t] = v;
 }
 
@@ -795,7 +816,8 @@ ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma
   ANCKA_LAUNCHED();
   k_inv_sqrt_counts<<<1, 64, 0, s>>>(sc.cnt, c.k, sc.inv);
   ANCKA_LAUNCHED();
-  k_fill_onehot<<<grid_for(c.n * c.ldk, 256), 256, 0, s>>>(labels, sc.inv, c.n, c.ldk, 0, 0.f, c.alpha, sc.Fa);
+  k_fill_onehot<<<grid_for(c.n * c.ldk, 256), 256, 0, s>>>(labels, sc.inv, sc.cnt, c.k, c.n, c.ldk, 0, 0.f,
+                                                           c.alpha, sc.Fa);
   ANCKA_LAUNCHED();
   float* cur = sc.Fa;
   float* nxt = sc.Fb;
@@ -976,7 +998,8 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     ANCKA_LAUNCHED();
     k_inv_sqrt_counts<<<1, 64, 0, s>>>(sc.cnt, k, sc.inv);
     ANCKA_LAUNCHED();
-    k_fill_onehot<<<grid_for(n * ld, 256), 256, 0, s>>>(y0, sc.inv, n, ld, 1, (float)(1.0 / sqrt((double)n)), 1.f, Qa);
+    k_fill_onehot<<<grid_for(n * ld, 256), 256, 0, s>>>(y0, sc.inv, sc.cnt, k, n, ld, 1,
+                                                        (float)(1.0 / sqrt((double)n)), 1.f, Qa);
     ANCKA_LAUNCHED();
   }
   {  // phi(Y^(0)) (reading R8)

@@ -360,3 +360,36 @@ def test_cliques_closed_form():
     # the first k columns of Q span the cluster indicators
     assert O.max_principal_angle(res["Q"][:, :k], ind) <= max(1e-6, 10 * ev[k] ** T)
     assert O.adjusted_rand_index(res["labels"], g["labels"]) == 1.0
+
+
+# ----------------------------------------------------------------------------
+# reading R13: full-rank Q^(0) when InitBCM leaves a cluster empty
+# ----------------------------------------------------------------------------
+def test_splitmix64_reference_outputs():
+    # first three outputs of splitmix64 seeded with 0 (state advances by the
+    # golden-ratio increment; each output mixes the advanced state)
+    g = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        states = np.array([0, g, g * np.uint64(2)], dtype=np.uint64)
+    out = O.splitmix64(states)
+    assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_initial_block_full_rank_with_empty_cluster():
+    labels = np.array([0, 0, 2, 2, 2, 0, 2, 0, 0, 2] * 20)   # cluster 1 empty
+    # the paper's block [1/sqrt(n) | h(Y)] is rank deficient twice over here
+    raw = np.concatenate([np.full((200, 1), 1 / np.sqrt(200)), O.h_norm(labels, 3)], axis=1)
+    assert np.linalg.matrix_rank(raw) == 2
+    Q0 = O.initial_block(labels, 3)
+    assert np.linalg.matrix_rank(Q0) == 4
+    assert np.allclose(np.abs(Q0[:, [2, 3]]), 1 / np.sqrt(labels.size))
+    # span(h(Y)) is kept: h(Y)'s columns lie in span(Q0)
+    Yh = O.h_norm(labels, 3)
+    coef, *_ = np.linalg.lstsq(Q0, Yh, rcond=None)
+    assert np.allclose(Q0 @ coef, Yh)
+    assert np.allclose(Q0[:, 1], Yh[:, 0])
+    # a fully populated Y: only the last cluster's column is replaced
+    full = np.arange(200) % 3
+    Q1 = O.initial_block(full, 3)
+    assert np.linalg.matrix_rank(Q1) == 4
+    assert np.allclose(Q1[:, 1:3], O.h_norm(full, 3)[:, :2])
