@@ -55,7 +55,7 @@ class Info(ctypes.Structure):
     def to_dict(self) -> dict:
         n = self.n_phi
         return dict(knn_candidates=self.knn_candidates, knn_fallback_rows=self.knn_fallback_rows,
-                    iters_run=self.iters_run, phi=list(self.phi[:n]), disc_iters=list(self.disc_iters[:n]),
+                    iters_run=self.iters_run, n_phi=n, phi=list(self.phi[:n]), disc_iters=list(self.disc_iters[:n]),
                     taken=list(self.taken[:n]), phi_best=self.phi_best, numeric_flags=self.numeric_flags,
                     ms_knn=self.ms_knn, ms_build=self.ms_build, ms_init=self.ms_init, ms_iter=self.ms_iter,
                     ms_disc=self.ms_disc, ms_mhc=self.ms_mhc, ms_total=self.ms_total,

@@ -157,6 +157,10 @@ ancka_status validate_knn_args(const float* X, int64_t n, int32_t d, int32_t K, 
     set_error("BF16 tensor-core contraction is not available in this build");
     return ANCKA_ERR_UNSUPPORTED;
   }
+  if (prec == ANCKA_PREC_BF16 && K <= kCandC / 2 && round_up(d, 64) > knn_tc_max_dp()) {
+    set_error("BF16 contraction keeps the query block in shared memory: d must be <= %d", knn_tc_max_dp());
+    return ANCKA_ERR_UNSUPPORTED;
+  }
   return ANCKA_OK;
 }
 
@@ -176,7 +180,16 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
     float acc;
     if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[0], s));
     if (prec == ANCKA_PREC_BF16) {
-      ANCKA_TRY(knn_candidates_bf16(pr, n, cv, ci, s));
+      int32_t* terr;
+      ANCKA_TRY(ws.zeros(&terr, 1));
+      ANCKA_TRY(knn_candidates_bf16(pr, n, cv, ci, terr, s));
+      int32_t hterr = 0;
+      ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaStreamSynchronize(s));
+      if (hterr) {
+        set_error("tensor-core contraction: a pipeline wait expired (role %d)", hterr);
+        return ANCKA_ERR_TIMEOUT;
+      }
       // tensor-core FP32 accumulation: a few units in the last place per
       // 16-wide MMA step (bound validated against exact products in tests)
       acc = (float)((pr.dp / 16 + 2) * 2.384185791015625e-07);  // 2^-22 per step

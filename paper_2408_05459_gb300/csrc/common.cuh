@@ -137,6 +137,28 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Insert (s, j) into an unsorted register list of C scores whose minimum is
+// thr at slot mp (caller checked s > thr); recompute the minimum.  Fully
+// unrolled so the list stays in registers.
+template <int C>
+__device__ __forceinline__ void list_insert(float (&lv)[C], int32_t (&li)[C], float& thr, int& mp, float s,
+                                            int32_t j) {
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+    if (c == mp) {
+      lv[c] = s;
+      li[c] = j;
+    }
+  thr = lv[0];
+  mp = 0;
+#pragma unroll
+  for (int c = 1; c < C; ++c)
+    if (lv[c] < thr) {
+      thr = lv[c];
+      mp = c;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // internal host interfaces (one translation unit each)
 // ---------------------------------------------------------------------------
@@ -160,8 +182,9 @@ constexpr int kCandC = 32;  // candidates kept per row
 ancka_status knn_candidates_fp32(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
                                  cudaStream_t s);
 ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
-                                 cudaStream_t s);
+                                 int32_t* err, cudaStream_t s);
 bool knn_tc_available();
+int knn_tc_max_dp();
 
 // rerank.cu: certified exact re-rank + exhaustive fallback
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,

@@ -17,25 +17,6 @@ namespace {
 constexpr int kBM = 128, kBN = 128, kBK = 8, kThreads = 256;
 constexpr int kSPad = kBN + 1;  // conflict-free row reads of the score tile
 
-template <int C>
-__device__ __forceinline__ void list_insert(float (&lv)[C], int32_t (&li)[C], float& thr, int& mp,
-                                            float s, int32_t j) {
-#pragma unroll
-  for (int c = 0; c < C; ++c)
-    if (c == mp) {
-      lv[c] = s;
-      li[c] = j;
-    }
-  thr = lv[0];
-  mp = 0;
-#pragma unroll
-  for (int c = 1; c < C; ++c)
-    if (lv[c] < thr) {
-      thr = lv[c];
-      mp = c;
-    }
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
 k_knn_simt(const float* __restrict__ Xu, int64_t n, int64_t n_pad, int dp,
            float* __restrict__ cand_val, int32_t* __restrict__ cand_idx) {

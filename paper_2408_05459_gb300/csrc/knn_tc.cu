@@ -1,13 +1,388 @@
-// tcgen05 BF16 candidate search (filled in by the tensor-core kernel).
+// tcgen05 BF16 candidate search for the cosine KNN of Section 3.1.
+//
+// One CTA per 128 query rows sweeps every 256-row key tile:
+//   warp 0     TMA producer: the CTA's query block A (128 x dp BF16, 128-byte
+//              swizzle) once, then key tiles B (256 rows x 64 features per
+//              stage) through an nstages-deep ring (mbarrier full/empty);
+//   warp 1     MMA issuer: allocates 512 TMEM columns, issues
+//              tcgen05.mma.cta_group::1.kind::f16 (M=128, N=256, K=16) into
+//              two ping-pong FP32 accumulators, commits stage releases and
+//              accumulator-ready signals;
+//   warps 2-5  epilogue: tcgen05.ld (32x32b) of the accumulator row owned by
+//              the thread (TMEM lane = query row), threshold test and insert
+//              into a register-resident list of the kCandC best scores.
+// The MMA of tile t+1 overlaps the epilogue of tile t.  n x n scores never
+// leave the SM.  Every mbarrier wait is bounded: on expiry the kernel records
+// an error code, stops all roles, drains its own copies and MMAs (bounded),
+// frees TMEM and returns.
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace ancka {
 
-bool knn_tc_available() { return false; }
+namespace {
 
-ancka_status knn_candidates_bf16(const PrepOut&, int64_t, float*, int32_t*, cudaStream_t) {
-  set_error("BF16 tensor-core contraction is not available in this build");
-  return ANCKA_ERR_UNSUPPORTED;
+constexpr int kTM = 128;                 // query rows per CTA = TMEM lanes
+constexpr int kTN = 256;                 // key rows per tile = accumulator columns
+constexpr int kTK = 64;                  // features per stage: one 128-byte swizzle row
+constexpr int kThreads = 192;
+constexpr int kABytes = kTM * kTK * 2;   // 16 KB per 64-feature block of A
+constexpr int kBBytes = kTN * kTK * 2;   // 32 KB per stage of B
+constexpr int kMaxStages = 8;
+constexpr int kMaxSmem = 232448;         // 227 KB opt-in dynamic shared memory
+constexpr uint32_t kTmemCols = 512;      // two 256-column FP32 accumulators
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+struct __align__(8) Bars {
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
+  uint64_t a_full;
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on expiry (which raises the CTA-wide abort) or when
+// another role has already aborted
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* err, int code) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (abort && *abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      if (abort) *abort = 1;
+      if (err) atomicExch(err, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout (8-row x 128-byte atoms, 1024 bytes apart)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem_d),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
+         int64_t n_pad, int kb_count, int nstages, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
+         int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + kb_count * kABytes;
+  Bars* bars = reinterpret_cast<Bars*>(sB + nstages * kBBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ib = (int64_t)blockIdx.x * kTM;
+  const int ntiles = (int)ceil_div(n_pad, kTN);
+  volatile int* abort = &bars->abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(&bars->full[s], 1);
+      mbar_init(&bars->empty[s], 1);
+    }
+    mbar_init(&bars->a_full, 1);
+    mbar_init(&bars->tfull[0], 1);
+    mbar_init(&bars->tfull[1], 1);
+    mbar_init(&bars->tempty[0], 4);
+    mbar_init(&bars->tempty[1], 4);
+    mbar_init(&bars->drain, 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool pending[kMaxStages];
+      uint32_t pend_par[kMaxStages];
+      for (int s = 0; s < kMaxStages; ++s) pending[s] = false;
+      mbar_expect_tx(&bars->a_full, (uint32_t)(kb_count * kABytes));
+      for (int kb = 0; kb < kb_count; ++kb)
+        tma_load_2d(smem_u32(sA + kb * kABytes), &tmA, kb * kTK, (int)ib, &bars->a_full);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int t = 0; t < ntiles && ok; ++t) {
+        for (int kb = 0; kb < kb_count; ++kb) {
+          if (!mbar_wait(&bars->empty[stage], phase ^ 1, abort, err, 1)) {
+            ok = false;
+            break;
+          }
+          pending[stage] = false;
+          mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
+          tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, t * kTN, &bars->full[stage]);
+          pending[stage] = true;
+          pend_par[stage] = phase;
+          if (++stage == nstages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      if (!ok) {  // drain this warp's copies still in flight (bounded)
+        mbar_wait(&bars->a_full, 0, nullptr, nullptr, 0);
+        for (int s = 0; s < nstages; ++s)
+          if (pending[s]) mbar_wait(&bars->full[s], pend_par[s], nullptr, nullptr, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(&bars->a_full, 0, abort, err, 2);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool issued = false;
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int b = t & 1;
+        const uint32_t use = (uint32_t)(t >> 1);
+        if (!mbar_wait(&bars->tempty[b], (use & 1) ^ 1, abort, err, 3)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * kTN);
+        for (int kb = 0; kb < kb_count; ++kb) {
+          if (!mbar_wait(&bars->full[stage], phase, abort, err, 4)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + kb * kABytes);
+          const uint32_t b0 = smem_u32(sB + stage * kBBytes);
+#pragma unroll
+          for (int kk = 0; kk < kTK / 16; ++kk)
+            umma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+          issued = true;
+          umma_commit(&bars->empty[stage]);
+          if (++stage == nstages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&bars->tfull[b]);
+      }
+      if (!ok && issued) {  // wait for this thread's MMAs before TMEM is freed (bounded)
+        umma_commit(&bars->drain);
+        mbar_wait(&bars->drain, 0, nullptr, nullptr, 0);
+      }
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int r = q * 32 + lane;
+    const int64_t i = ib + r;
+    constexpr int C = kCandC;
+    float lv[C];
+    int32_t li[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      lv[c] = -INFINITY;
+      li[c] = -1;
+    }
+    float thr = -INFINITY;
+    int mp = 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    for (int t = 0; t < ntiles; ++t) {
+      const int b = t & 1;
+      const uint32_t use = (uint32_t)(t >> 1);
+      bool ok = mbar_wait(&bars->tfull[b], use & 1, abort, err, 5);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int64_t jb = (int64_t)t * kTN;
+#pragma unroll 1
+      for (int c = 0; c < kTN / 32; ++c) {
+        float v[32];
+        tmem_ld32(lane_base + (uint32_t)(b * kTN + c * 32), v);
+        // pass mask against the threshold at chunk start (it only rises, so
+        // the mask is a superset); padding keys and the row itself removed
+        uint32_t pm = 0;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) pm |= (v[e] > thr ? 1u : 0u) << e;
+        const int64_t j0 = jb + c * 32;
+        if (j0 + 32 > n) pm &= (j0 >= n) ? 0u : ((1u << (uint32_t)(n - j0)) - 1u);
+        if (i >= j0 && i < j0 + 32) pm &= ~(1u << (uint32_t)(i - j0));
+        // one insert per passing key; lanes without keys idle
+        while (__any_sync(0xffffffffu, pm != 0)) {
+          if (pm) {
+            const int e = __ffs(pm) - 1;
+            pm &= pm - 1;
+            float val = v[0];
+#pragma unroll
+            for (int q = 1; q < 32; ++q)
+              if (e == q) val = v[q];
+            if (val > thr) list_insert<C>(lv, li, thr, mp, val, (int32_t)(j0 + e));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->tempty[b]);
+    }
+    if (i < n) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        cand_val[i * kCandC + c] = lv[c];
+        cand_idx[i * kCandC + c] = li[c];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+ancka_status make_map(CUtensorMap* m, const void* base, int64_t dp, int64_t rows_total, uint32_t box_rows) {
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)dp, (cuuint64_t)rows_total};
+  cuuint64_t gstride[1] = {(cuuint64_t)dp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ANCKA_ERR_CUDA;
+  }
+  return ANCKA_OK;
+}
+
+}  // namespace
+
+bool knn_tc_available() { return true; }
+
+int knn_tc_max_dp() { return 512; }
+
+ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx, int32_t* err,
+                                 cudaStream_t s) {
+  const int kb_count = pr.dp / kTK;
+  if (pr.dp % kTK != 0 || kb_count < 1 || pr.dp > knn_tc_max_dp()) {
+    set_error("BF16 contraction supports up to %d features (got %d)", knn_tc_max_dp(), pr.dp);
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  const size_t fixed = 1024 + (size_t)kb_count * kABytes + sizeof(Bars);
+  int nstages = (int)((kMaxSmem - fixed) / kBBytes);
+  if (nstages > kMaxStages) nstages = kMaxStages;
+  if (nstages < 2) {
+    set_error("BF16 contraction: not enough shared memory for two stages");
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  // at least ~120 KB so that one CTA owns an SM and its 512 TMEM columns
+  size_t smem = fixed + (size_t)nstages * kBBytes;
+  if (smem < 120 * 1024) smem = 120 * 1024;
+  CUtensorMap ta, tb;
+  ANCKA_TRY(make_map(&ta, pr.xb, pr.dp, pr.n_pad, kTM));
+  ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN));
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_knn_tc<<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(ta, tb, n, pr.n_pad, kb_count, nstages, cand_val,
+                                                            cand_idx, err);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
 }
 
 }  // namespace ancka
