@@ -195,6 +195,20 @@ ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int3
 ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq,
                               int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
 
+/* Discretize exactly as ancka_discretize, but without allocating any device
+ * memory (the paper has no counterpart: this serves callers that must not
+ * allocate while they run -- code that reserves all memory at start-up,
+ * programs whose device memory is owned by another allocator, loops that
+ * avoid cudaMalloc/cudaFree because freeing synchronises the device).
+ * Scratch comes from a fixed 32 MiB device array inside the library, held by
+ * every GPU that loads it until exit; sizes needing more (about
+ * n * round_up(k, 4) * 4 bytes plus small state) return
+ * ANCKA_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * address and should come before any stream capture.  Calls share the array:
+ * calls that overlap on the GPU race.  Arguments as for ancka_discretize. */
+ancka_status ancka_discretize_noalloc(const float* Qk, int64_t n, int32_t k, int32_t ldq,
+                                      int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
     L.ancka_cluster_host.restype = ctypes.c_int
     L.ancka_discretize.argtypes = [vp, i64, i32, i32, i32, vp, ctypes.POINTER(i32), vp]
     L.ancka_discretize.restype = ctypes.c_int
+    L.ancka_discretize_noalloc.argtypes = [vp, i64, i32, i32, i32, vp, ctypes.POINTER(i32), vp]
+    L.ancka_discretize_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -292,3 +294,18 @@ def discretize(Qk, max_iter: int = 20):
     st = load().ancka_discretize(_ptr(Qk), n, k, Qk.stride(0), max_iter, _ptr(labels), ctypes.byref(it), _stream())
     _check("ancka_discretize", st)
     return labels, it.value
+
+
+def discretize_noalloc(Qk, labels, max_iter: int = 20):
+    """ancka_discretize_noalloc: Discretize into a caller-owned ``labels``
+    buffer using the library's fixed device scratch (no allocation inside the
+    call).  Returns the number of inner iterations."""
+    import torch
+    assert Qk.is_cuda and Qk.dtype == torch.float32 and Qk.stride(1) == 1
+    assert labels.is_cuda and labels.dtype == torch.int32 and labels.numel() == Qk.shape[0]
+    n, k = Qk.shape
+    it = ctypes.c_int32(0)
+    st = load().ancka_discretize_noalloc(_ptr(Qk), n, k, Qk.stride(0), max_iter, _ptr(labels),
+                                         ctypes.byref(it), _stream())
+    _check("ancka_discretize_noalloc", st)
+    return it.value

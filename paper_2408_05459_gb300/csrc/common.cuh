@@ -238,5 +238,8 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& c, const int
 ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, int32_t ldq,
                         int32_t max_iter, int32_t* labels, int32_t* iters_dev, int32_t* flags_dev,
                         cudaStream_t s);
+size_t discretize_scratch_bytes(int64_t n, int32_t k);
+ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, int64_t n, int32_t k, int32_t ldq,
+                                int32_t max_iter, int32_t* labels, int32_t** iters_dev, cudaStream_t s);
 
 }  // namespace ancka

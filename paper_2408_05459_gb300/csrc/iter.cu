@@ -1066,3 +1066,54 @@ ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, in
 }
 
 }  // namespace ancka
+
+namespace ancka {
+
+namespace {
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+// Bytes of caller-provided scratch Discretize needs for an n x k block.
+size_t discretize_scratch_bytes(int64_t n, int32_t k) {
+  const size_t ldk = (size_t)round_up(k, 4);
+  const size_t nblk = (size_t)ceil_div(n, 2048);
+  return align256((size_t)n * ldk * sizeof(float)) + align256(nblk * k * k * sizeof(float)) +
+         align256((size_t)k * k * sizeof(float)) + align256((size_t)k * sizeof(int32_t)) + 256;
+}
+
+// Discretize on a caller-provided scratch block of at least
+// discretize_scratch_bytes(n, k) bytes (256-byte aligned); the per-call state
+// is reset by kernels and a memset, nothing is allocated.  *iters_dev points
+// into the scratch afterwards.
+ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, int64_t n, int32_t k, int32_t ldq,
+                                int32_t max_iter, int32_t* labels, int32_t** iters_dev, cudaStream_t s) {
+  if (bytes < discretize_scratch_bytes(n, k)) {
+    set_error("Discretize scratch too small");
+    return ANCKA_ERR_INVALID_ARG;
+  }
+  const int ldk = (int)round_up(k, 4);
+  char* p = static_cast<char*>(scratch);
+  float* Qt = reinterpret_cast<float*>(p);
+  p += align256((size_t)n * ldk * sizeof(float));
+  DiscState st;
+  st.rows_per_blk = 2048;
+  st.nblk = (int)ceil_div(n, st.rows_per_blk);
+  st.partial = reinterpret_cast<float*>(p);
+  p += align256((size_t)st.nblk * k * k * sizeof(float));
+  st.Rf = reinterpret_cast<float*>(p);
+  p += align256((size_t)k * k * sizeof(float));
+  st.counts = reinterpret_cast<int32_t*>(p);
+  p += align256((size_t)k * sizeof(int32_t));
+  st.obj_prev = reinterpret_cast<double*>(p);
+  st.iter = reinterpret_cast<int32_t*>(p + 8);
+  st.done = reinterpret_cast<int32_t*>(p + 12);
+  int32_t* it = reinterpret_cast<int32_t*>(p + 16);
+  ANCKA_CUDA(cudaMemsetAsync(it, 0, sizeof(int32_t), s));
+  k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qk, ldq, 0, n, k, Qt, ldk);
+  ANCKA_LAUNCHED();
+  ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, max_iter, labels, it, nullptr, s));
+  *iters_dev = it;
+  return ANCKA_OK;
+}
+
+}  // namespace ancka
