@@ -157,12 +157,14 @@ ancka_status validate_knn_args(const float* X, int64_t n, int32_t d, int32_t K, 
     set_error("BF16 tensor-core contraction is not available in this build");
     return ANCKA_ERR_UNSUPPORTED;
   }
-  if (prec == ANCKA_PREC_BF16 && K <= kCandC / 2 && round_up(d, 64) > knn_tc_max_dp()) {
+  if (prec == ANCKA_PREC_BF16 && K <= kCandC / 2 - 4 && round_up(d, 64) > knn_tc_max_dp()) {
     set_error("BF16 contraction keeps the query block in shared memory: d must be <= %d", knn_tc_max_dp());
     return ANCKA_ERR_UNSUPPORTED;
   }
   return ANCKA_OK;
 }
+
+int max_candidate_K(int prec) { return prec == ANCKA_PREC_BF16 ? kCandC / 2 - 4 : kCandC / 2; }
 
 // the KNN lists with every step on the device
 ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
@@ -171,8 +173,9 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
   PrepOut pr;
   ANCKA_TRY(prep_rows(ws, X, n, d, prec, &pr, s));
   if (zero_row) *zero_row = pr.zero_row;
-  // the candidate list certifies K when a few slots of slack remain
-  if (K <= kCandC / 2) {
+  // the candidate lists certify K when a few slots of slack remain: one list
+  // of 32 (CUDA-core contraction) or two of 16 (tensor-core contraction)
+  if (K <= max_candidate_K(prec)) {
     float* cv;
     int32_t* ci;
     ANCKA_TRY(ws.alloc(&cv, (size_t)n * kCandC));
@@ -200,9 +203,12 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
       acc = (float)(1.01 * g / (1.0 - g));
     }
     if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
-    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, acc, cv, ci, idx, sim, ncand, nfb, counts, s));
+    // the tensor-core kernel leaves two 16-entry lists per row (one per half
+    // of the key columns), the CUDA-core kernel one 32-entry list
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, acc, cv, ci, prec == ANCKA_PREC_BF16 ? 2 : 1, idx, sim, ncand, nfb,
+                         counts, s));
   } else {
-    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, 0.f, nullptr, nullptr, idx, sim, ncand, nfb, counts, s));
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, 0.f, nullptr, nullptr, 1, idx, sim, ncand, nfb, counts, s));
   }
   return ANCKA_OK;
 }
@@ -278,8 +284,8 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       if (st == ANCKA_OK && !sim) st = ws.alloc(&sim, (size_t)n * K);
       if (st == ANCKA_OK)
         st = knn_impl(ws, X, n, d, K, p->knn_prec, idx, sim, &zero_row, &ncand, &nfb, info != nullptr, s,
-                      info && K <= kCandC / 2 ? cev : nullptr);
-      contract_timed = info && K <= kCandC / 2;
+                      info && K <= max_candidate_K(p->knn_prec) ? cev : nullptr);
+      contract_timed = info && K <= max_candidate_K(p->knn_prec);
     } else if (st == ANCKA_OK) {
       Phase ph(tp, s, 0);
       k_check_knn<<<(unsigned)ceil_div(n * K, 256), 256, 0, s>>>(knn_idx_in, n, K, bad);
@@ -428,7 +434,7 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
   ancka_status st;
   int64_t nc = 0, nf = 0;
   cudaEvent_t cev[2] = {nullptr, nullptr};
-  const bool timed = info && K <= kCandC / 2;
+  const bool timed = info && K <= max_candidate_K(prec);
   if (timed) {
     cudaEventCreate(&cev[0]);
     cudaEventCreate(&cev[1]);
@@ -545,12 +551,19 @@ ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq
   {
     Workspace ws(s);
     int32_t* it;
+    int32_t* derr = nullptr;
     ANCKA_TRY(ws.zeros(&it, 1));
-    st = discretize(ws, Qk, n, k, ldq, max_iter, labels, it, nullptr, s);
-    if (st == ANCKA_OK && iters) {
+    st = discretize(ws, Qk, n, k, ldq, max_iter, labels, it, nullptr, &derr, s);
+    if (st == ANCKA_OK) {
+      int32_t he = 0;
       ANCKA_CUDA(cudaMemcpyAsync(&hit, it, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaMemcpyAsync(&he, derr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       ANCKA_CUDA(cudaStreamSynchronize(s));
-      *iters = hit;
+      if (he) {
+        set_error("Discretize: a grid barrier wait expired");
+        st = ANCKA_ERR_TIMEOUT;
+      }
+      if (iters) *iters = hit;
     }
   }
   return st;

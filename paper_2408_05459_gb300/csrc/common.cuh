@@ -189,7 +189,7 @@ int knn_tc_max_dp();
 // rerank.cu: certified exact re-rank + exhaustive fallback
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
                         const PrepOut& pr, float acc_coef, const float* cand_val,
-                        const int32_t* cand_idx, int32_t* out_idx, float* out_sim,
+                        const int32_t* cand_idx, int lists, int32_t* out_idx, float* out_sim,
                         int64_t* n_candidates, int64_t* n_fallback, bool want_counts,
                         cudaStream_t s);
 
@@ -237,9 +237,10 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& c, const int
                        cudaStream_t s);
 ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, int32_t ldq,
                         int32_t max_iter, int32_t* labels, int32_t* iters_dev, int32_t* flags_dev,
-                        cudaStream_t s);
+                        int32_t** err_dev, cudaStream_t s);
 size_t discretize_scratch_bytes(int64_t n, int32_t k);
 ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, int64_t n, int32_t k, int32_t ldq,
-                                int32_t max_iter, int32_t* labels, int32_t** iters_dev, cudaStream_t s);
+                                int32_t max_iter, int32_t* labels, int32_t** iters_dev, int32_t** err_dev,
+                                cudaStream_t s);
 
 }  // namespace ancka

@@ -275,15 +275,17 @@ ancka_status apply_rinv(const float* Z, int ld, int64_t n, int w, const float* R
 // Discretize
 // ---------------------------------------------------------------------------
 struct DiscState {
-  float* Rf;          // k x k FP32 copy of R for the argmax kernel
-  int32_t* counts;    // k
-  double* obj_prev;   // 1
-  int32_t* iter;      // 1
-  int32_t* done;      // 1
-  float* partial;     // nblk x k x k
-  int nblk;
-  int rows_per_blk;
+  float* Rf;            // k x k FP32 R, written by CTA 0, read by every CTA
+  int32_t* counts;      // k: cluster sizes of the current Y
+  double* obj_prev;     // 1
+  int32_t* done;        // 1
+  float* partial;       // kDiscMaxGrid x k x k per-CTA sums
+  unsigned int* bar;    // 2: grid barrier count and generation
+  int32_t* err;         // 1: grid barrier expired
 };
+
+constexpr int kDiscThreads = 512;
+constexpr int kDiscMaxGrid = 320;
 
 __global__ void k_rownorm(const float* __restrict__ Q, int ldq, int off, int64_t n, int k,
                           float* __restrict__ Qt, int ldt) {
@@ -296,264 +298,305 @@ __global__ void k_rownorm(const float* __restrict__ Q, int ldq, int off, int64_t
   for (int c = 0; c < ldt; ++c) Qt[i * ldt + c] = c < k ? q[c] * inv : 0.f;
 }
 
-__global__ void k_disc_init(float* Rf, int32_t* counts, double* obj_prev, int32_t* iter, int32_t* done,
-                            int k) {
+__global__ void k_disc_init(float* Rf, int32_t* counts, double* obj_prev, int32_t* done, unsigned int* bar,
+                            int32_t* err, int k) {
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rf[e] = (e / k == e % k) ? 1.f : 0.f;
   for (int e = threadIdx.x; e < k; e += blockDim.x) counts[e] = 0;
   if (threadIdx.x == 0) {
     *obj_prev = 0.0;
-    *iter = 0;
     *done = 0;
+    bar[0] = 0;
+    bar[1] = 0;
+    *err = 0;
   }
 }
 
-// labels[i] = argmax_c (Qt[i] R)[c], ties to the lowest c; per-CTA histogram
-template <int G>
-__global__ void __launch_bounds__(256)
-k_disc_argmax(const float* __restrict__ Qt, int ldt, int64_t n, int k, const float* __restrict__ Rf,
-              int32_t* __restrict__ labels, int32_t* __restrict__ counts, const int32_t* __restrict__ done) {
-  if (*done) return;
-  __shared__ __align__(16) float Rs[64 * 64];
-  __shared__ int32_t hist[64];
-  const int ldr = ldt;
-  for (int e = threadIdx.x; e < k * ldr; e += blockDim.x) {
-    const int a = e / ldr, c = e % ldr;
-    Rs[a * ldr + c] = c < k ? Rf[a * k + c] : 0.f;
-  }
-  for (int e = threadIdx.x; e < 64; e += blockDim.x) hist[e] = 0;
-  __syncthreads();
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = t / G;
-  const int g = (int)(t % G);
-  const int nv4 = ldt / 4;
-  float best = -INFINITY;
-  int bc = 0x7fffffff;
-  if (i < n && g < nv4) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float* q = Qt + i * ldt;
-    for (int a = 0; a < k; ++a) {
-      const float qa = q[a];
-      const float4 r = *reinterpret_cast<const float4*>(&Rs[a * ldr + 4 * g]);
-      acc.x = fmaf(qa, r.x, acc.x);
-      acc.y = fmaf(qa, r.y, acc.y);
-      acc.z = fmaf(qa, r.z, acc.z);
-      acc.w = fmaf(qa, r.w, acc.w);
-    }
-    const float v[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll
-    for (int q4 = 0; q4 < 4; ++q4) {
-      const int c = 4 * g + q4;
-      if (c < k && v[q4] > best) {
-        best = v[q4];
-        bc = c;
-      }
-    }
-  }
-  // reduce within the G-lane group: max value, lowest column on ties
-#pragma unroll
-  for (int off = 1; off < G; off <<= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
-    if (ob > best || (ob == best && oc < bc)) {
-      best = ob;
-      bc = oc;
-    }
-  }
-  if (i < n && g == 0) {
-    if (bc == 0x7fffffff) bc = 0;  // all-NaN row
-    labels[i] = bc;
-    atomicAdd(&hist[bc], 1);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < k; e += blockDim.x)
-    if (hist[e]) atomicAdd(&counts[e], hist[e]);
-}
-
-// per-CTA k x k sums M'[l][c] = sum_{i in chunk, y_i = l} Qt[i][c]; thread
-// (slice, c) owns column c of its slice, rows in order (deterministic).
-__global__ void __launch_bounds__(256)
-k_disc_msum(const float* __restrict__ Qt, int ldt, int64_t n, int k, const int32_t* __restrict__ labels,
-            int rows_per_blk, float* __restrict__ partial, const int32_t* __restrict__ done) {
-  if (*done) return;
-  extern __shared__ float sM[];  // nsl x k x k
-  const int nsl = blockDim.x / k;
-  const int kk = k * k;
-  for (int e = threadIdx.x; e < nsl * kk; e += blockDim.x) sM[e] = 0.f;
-  __syncthreads();
-  const int sl = threadIdx.x / k, c = threadIdx.x % k;
-  const int64_t b0 = (int64_t)blockIdx.x * rows_per_blk;
-  const int64_t b1 = (b0 + rows_per_blk < n) ? b0 + rows_per_blk : n;
-  if (sl < nsl) {
-    const int64_t per = ceil_div(b1 - b0 > 0 ? b1 - b0 : 0, (int64_t)nsl);
-    const int64_t s0 = b0 + sl * per;
-    const int64_t s1 = (s0 + per < b1) ? s0 + per : b1;
-    float* my = sM + sl * kk;
-    for (int64_t i = s0; i < s1; ++i) my[labels[i] * k + c] += Qt[i * ldt + c];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-    float s = 0.f;
-    for (int q = 0; q < nsl; ++q) s += sM[q * kk + e];
-    partial[(int64_t)blockIdx.x * kk + e] = s;
-  }
-}
-
-// One CTA of 1024 threads: M = Y~^T Q~ in FP64, one-sided Jacobi SVD
-// (Hestenes; round-robin pair schedule, one warp per pair), R = V U^T,
-// obj = n - 2 tr(Omega), and the stop test of Alg. 5.
-__global__ void __launch_bounds__(1024)
-k_disc_svd(const float* __restrict__ partial, int nblk, int k, int64_t n, int32_t* __restrict__ counts,
-           float* __restrict__ Rf, double* __restrict__ obj_prev, int32_t* __restrict__ iter,
-           int32_t* __restrict__ done, int32_t* __restrict__ iters_out, int32_t* __restrict__ flags,
-           int max_iter) {
-  if (*done) return;
-  extern __shared__ double dsm[];  // A: k x kp, V: kp x kp (kp = k rounded up to even)
-  __shared__ double sig[65];
-  __shared__ int rotated;
-  const int kp = (k + 1) & ~1;
-  double* A = dsm;
-  double* V = dsm + k * kp;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  // M[l][c] = (sum over blocks) / count_l
-  for (int e = threadIdx.x; e < k * kp; e += blockDim.x) {
-    const int l = e / kp, c = e % kp;
-    double s = 0.0;
-    if (c < k) {
-      for (int b = 0; b < nblk; ++b) s += (double)partial[(int64_t)b * k * k + l * k + c];
-      const int cnt = counts[l];
-      s = cnt > 0 ? s / (double)cnt : 0.0;
-    }
-    A[l * kp + c] = s;
-  }
-  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) V[e] = (e / kp == e % kp) ? 1.0 : 0.0;
-  __syncthreads();
-  bool empty = false;
-  for (int l = 0; l < k; ++l) empty |= counts[l] == 0;
-  int sweep = 0;
-  for (; sweep < 60; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
-    for (int r = 0; r < kp - 1; ++r) {
-      if (wp < kp / 2) {
-        int p, q;
-        if (wp == 0) {
-          p = kp - 1;
-          q = r;
-        } else {
-          p = (r + wp) % (kp - 1);
-          q = (r - wp + kp - 1) % (kp - 1);
-        }
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int row = lane; row < k; row += 32) {
-          const double x = A[row * kp + p], y = A[row * kp + q];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
-        }
-        al = warp_sum_d(al);
-        be = warp_sum_d(be);
-        ga = warp_sum_d(ga);
-        if (al > 0.0 && be > 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-          for (int row = lane; row < k; row += 32) {
-            const double x = A[row * kp + p], y = A[row * kp + q];
-            A[row * kp + p] = cs * x - sn * y;
-            A[row * kp + q] = sn * x + cs * y;
-          }
-          for (int row = lane; row < kp; row += 32) {
-            const double x = V[row * kp + p], y = V[row * kp + q];
-            V[row * kp + p] = cs * x - sn * y;
-            V[row * kp + q] = sn * x + cs * y;
-          }
-          if (lane == 0) rotated = 1;
-        }
-      }
-      __syncthreads();
-    }
-    if (!rotated) break;
-    __syncthreads();
-  }
-  // singular values and U (stored back into A's columns)
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    double s = 0.0;
-    for (int row = 0; row < k; ++row) s += A[row * kp + c] * A[row * kp + c];
-    sig[c] = sqrt(s);
-  }
-  __syncthreads();
-  double smax = 0.0;
-  for (int c = 0; c < k; ++c) smax = fmax(smax, sig[c]);
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int row = e / k, c = e % k;
-    const double sc = sig[c];
-    A[row * kp + c] = (sc > 1e-13 * smax && sc > 0.0) ? A[row * kp + c] / sc : 0.0;
-  }
+// Software grid barrier for a cooperative launch (all CTAs co-resident).
+// Bounded: on expiry it records the error and returns false.
+__device__ bool grid_barrier(unsigned int* bar, int32_t* err) {
+  __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    // rank-deficient M (empty clusters): complete U to an orthonormal basis
-    for (int c = 0; c < k; ++c) {
-      if (sig[c] > 1e-13 * smax && sig[c] > 0.0) continue;
-      for (int cand = 0; cand < k; ++cand) {
-        double u[64];
-        for (int row = 0; row < k; ++row) u[row] = (row == cand) ? 1.0 : 0.0;
-        for (int rep = 0; rep < 2; ++rep)
-          for (int o = 0; o < k; ++o) {
-            if (o == c) continue;
-            double dot = 0.0;
-            for (int row = 0; row < k; ++row) dot += A[row * kp + o] * u[row];
-            for (int row = 0; row < k; ++row) u[row] -= dot * A[row * kp + o];
-          }
-        double nn = 0.0;
-        for (int row = 0; row < k; ++row) nn += u[row] * u[row];
-        if (nn > 0.25) {
-          nn = 1.0 / sqrt(nn);
-          for (int row = 0; row < k; ++row) A[row * kp + c] = u[row] * nn;
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > 4000000000LL || *(volatile int32_t*)err) {
+          atomicExch(err, 1);
+          ok = 0;
           break;
         }
       }
     }
+    __threadfence();
+    ok_s = ok;
   }
   __syncthreads();
-  // R = V U^T  (R[a][b] = sum_j V[a][j] U[b][j])
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int a = e / k, b = e % k;
-    double s = 0.0;
-    for (int j = 0; j < k; ++j) s += V[a * kp + j] * A[b * kp + j];
-    Rf[e] = (float)s;
-  }
-  if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int c = 0; c < k; ++c) tr += sig[c];
-    const double obj = (double)n - 2.0 * tr;
-    const int it = *iter;
-    if (it > 0 && fabs(obj - *obj_prev) <= 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(obj))) *done = 1;
-    *obj_prev = obj;
-    *iter = it + 1;
-    if (it + 1 >= max_iter) *done = 1;
-    if (iters_out) *iters_out = it + 1;
-    if (flags) {
-      if (empty) atomicOr(flags, 1);
-      if (sweep >= 60) atomicOr(flags, 2);
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < k; e += blockDim.x) counts[e] = 0;
+  return ok_s != 0;
 }
 
-ancka_status disc_argmax(const float* Qt, int ldt, int64_t n, int k, const DiscState& st, int32_t* labels,
-                         cudaStream_t s) {
-  const int G = pick_g(ldt / 4);
-  const unsigned grid = grid_for(n * G, 256);
-  switch (G) {
-    case 1: k_disc_argmax<1><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
-    case 2: k_disc_argmax<2><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
-    case 4: k_disc_argmax<4><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
-    case 8: k_disc_argmax<8><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
-    default: k_disc_argmax<16><<<grid, 256, 0, s>>>(Qt, ldt, n, k, st.Rf, labels, st.counts, st.done); break;
+// One-sided Jacobi SVD (Hestenes) of the k x k matrix in A (row-major, kp
+// columns, kp = k rounded up to even, padding column zero) in FP32: V
+// accumulates the rotations (A V = U Sigma).  Round-robin pair schedule, one
+// warp per pair, lanes over rows.  Returns the number of sweeps.
+__device__ int jacobi_svd_f32(float* A, float* V, int k, int kp, int* rotated) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) V[e] = (e / kp == e % kp) ? 1.f : 0.f;
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) *rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < kp - 1; ++r) {
+      for (int pr = wp; pr < kp / 2; pr += nw) {
+        int p, q;
+        if (pr == 0) {
+          p = kp - 1;
+          q = r;
+        } else {
+          p = (r + pr) % (kp - 1);
+          q = (r - pr + kp - 1) % (kp - 1);
+        }
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int row = lane; row < k; row += 32) {
+          const float x = A[row * kp + p], y = A[row * kp + q];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (al > 0.f && be > 0.f && fabsf(ga) > 1e-6f * sqrtf(al * be)) {
+          const float zeta = (be - al) / (2.f * ga);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+          for (int row = lane; row < k; row += 32) {
+            const float x = A[row * kp + p], y = A[row * kp + q];
+            A[row * kp + p] = cs * x - sn * y;
+            A[row * kp + q] = sn * x + cs * y;
+          }
+          for (int row = lane; row < kp; row += 32) {
+            const float x = V[row * kp + p], y = V[row * kp + q];
+            V[row * kp + p] = cs * x - sn * y;
+            V[row * kp + q] = sn * x + cs * y;
+          }
+          if (lane == 0) *rotated = 1;
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+    if (!*rotated) break;
+    __syncthreads();
   }
-  ANCKA_LAUNCHED();
-  return ANCKA_OK;
+  return sweep;
+}
+
+// Discretize (Def. 2, Alg. 5) as one persistent cooperative kernel.  Per
+// iteration: every CTA takes a contiguous row range, sets Y = argmax(Q~ R)
+// (ties to the lowest column), adds its cluster counts and writes its k x k
+// partial sums of Q~ rows per cluster (fixed order); after a grid barrier
+// CTA 0 forms M = Y~^T Q~ (partials summed in FP64), takes the SVD
+// M = U Omega V^T, sets R = V U^T and obj = n - 2 tr(Omega), and decides the
+// stop (|obj - obj_prev| <= 4 eps max(1,|obj|)); a second barrier publishes R.
+__global__ void __launch_bounds__(kDiscThreads)
+k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_iter, int32_t* __restrict__ labels,
+             DiscState st, int32_t* __restrict__ iters_out, int32_t* __restrict__ flags) {
+  extern __shared__ float dsm_f[];
+  __shared__ int32_t hist[64];
+  __shared__ int rotated;
+  const int kk = k * k;
+  const int nsl_cap = 16384 / kk;
+  const int nsl = max(1, min((int)blockDim.x / k, nsl_cap > 0 ? nsl_cap : 1));
+  float* Rs = dsm_f;                 // k x ldt
+  float* sM = dsm_f + 64 * 64;       // nsl x k x k
+  const int64_t per = ceil_div(n, (int64_t)gridDim.x);
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = (r0 + per < n) ? r0 + per : n;
+  const int nv4 = ldt / 4;
+  int G = 1;
+  while (G < nv4) G <<= 1;           // lanes per row (power of two <= 16)
+  for (int it = 0; it < max_iter; ++it) {
+    // ---------------- phase A: Y = argmax(Q~ R), counts, partial sums -----
+    for (int e = threadIdx.x; e < k * ldt; e += blockDim.x) {
+      const int a = e / ldt, c = e % ldt;
+      Rs[a * ldt + c] = c < k ? __ldcg(st.Rf + a * k + c) : 0.f;
+    }
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) hist[e] = 0;
+    __syncthreads();
+    const int rows_per_pass = blockDim.x / G;
+    for (int64_t base = r0; base < r1; base += rows_per_pass) {
+      const int64_t i = base + threadIdx.x / G;
+      const int g = threadIdx.x % G;
+      float best = -INFINITY;
+      int bc = 0x7fffffff;
+      if (i < r1 && g < nv4) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float* q = Qt + i * ldt;
+        for (int a = 0; a < k; ++a) {
+          const float qa = q[a];
+          const float4 r = *reinterpret_cast<const float4*>(&Rs[a * ldt + 4 * g]);
+          acc.x = fmaf(qa, r.x, acc.x);
+          acc.y = fmaf(qa, r.y, acc.y);
+          acc.z = fmaf(qa, r.z, acc.z);
+          acc.w = fmaf(qa, r.w, acc.w);
+        }
+        const float v[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const int c = 4 * g + q4;
+          if (c < k && v[q4] > best) {
+            best = v[q4];
+            bc = c;
+          }
+        }
+      }
+      for (int off = 1; off < G; off <<= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+        if (ob > best || (ob == best && oc < bc)) {
+          best = ob;
+          bc = oc;
+        }
+      }
+      if (i < r1 && g == 0) {
+        if (bc == 0x7fffffff) bc = 0;
+        labels[i] = bc;
+        atomicAdd(&hist[bc], 1);
+      }
+    }
+    for (int e = threadIdx.x; e < nsl * kk; e += blockDim.x) sM[e] = 0.f;
+    __syncthreads();
+    for (int e = threadIdx.x; e < k; e += blockDim.x)
+      if (hist[e]) atomicAdd(&st.counts[e], hist[e]);
+    {
+      const int sl = threadIdx.x / k, c = threadIdx.x % k;
+      if (sl < nsl) {
+        const int64_t sper = ceil_div(r1 - r0 > 0 ? r1 - r0 : 0, (int64_t)nsl);
+        const int64_t s0 = r0 + sl * sper;
+        const int64_t s1 = (s0 + sper < r1) ? s0 + sper : r1;
+        float* my = sM + sl * kk;
+        for (int64_t i = s0; i < s1; ++i) my[labels[i] * k + c] += Qt[i * ldt + c];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      float t = 0.f;
+      for (int q = 0; q < nsl; ++q) t += sM[q * kk + e];
+      st.partial[(int64_t)blockIdx.x * kk + e] = t;
+    }
+    if (!grid_barrier(st.bar, st.err)) return;
+    // ---------------- phase B (CTA 0): SVD, R, objective, stop -------------
+    if (blockIdx.x == 0) {
+      const int kp = (k + 1) & ~1;
+      float* A = dsm_f;          // k x kp
+      float* V = dsm_f + 64 * 64;  // kp x kp
+      __shared__ float sig[64];
+      __shared__ int32_t cnt_s[64];
+      for (int e = threadIdx.x; e < k; e += blockDim.x) cnt_s[e] = __ldcg(st.counts + e);
+      __syncthreads();
+      // M = (sum over CTAs of the partials) / counts: T threads per entry sum
+      // strided CTA subsets in FP64, combined in a fixed order
+      {
+        double* red = reinterpret_cast<double*>(dsm_f + 2 * 64 * 64);  // up to 4096 doubles
+        const int T = max(1, min((int)blockDim.x / kk, 32));
+        for (int e = threadIdx.x; e < kk * T; e += blockDim.x) {
+          const int entry = e / T, sub = e % T;
+          double t = 0.0;
+          for (int b = sub; b < (int)gridDim.x; b += T) t += (double)__ldcg(st.partial + (int64_t)b * kk + entry);
+          red[e] = t;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < k * kp; e += blockDim.x) {
+          const int l = e / kp, c = e % kp;
+          double t = 0.0;
+          if (c < k) {
+            for (int sub = 0; sub < T; ++sub) t += red[(l * k + c) * T + sub];
+            t = cnt_s[l] > 0 ? t / (double)cnt_s[l] : 0.0;
+          }
+          A[l * kp + c] = (float)t;
+        }
+        __syncthreads();
+      }
+      const int sweeps = jacobi_svd_f32(A, V, k, kp, &rotated);
+      for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        float t = 0.f;
+        for (int row = 0; row < k; ++row) t = fmaf(A[row * kp + c], A[row * kp + c], t);
+        sig[c] = sqrtf(t);
+      }
+      __syncthreads();
+      float smax = 0.f;
+      for (int c = 0; c < k; ++c) smax = fmaxf(smax, sig[c]);
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        const int row = e / k, c = e % k;
+        const float sc = sig[c];
+        A[row * kp + c] = (sc > 1e-6f * smax && sc > 0.f) ? A[row * kp + c] / sc : 0.f;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        // rank-deficient M (empty clusters): complete U to an orthonormal basis
+        for (int c = 0; c < k; ++c) {
+          if (sig[c] > 1e-6f * smax && sig[c] > 0.f) continue;
+          for (int cand = 0; cand < k; ++cand) {
+            float u[64];
+            for (int row = 0; row < k; ++row) u[row] = (row == cand) ? 1.f : 0.f;
+            for (int rep = 0; rep < 2; ++rep)
+              for (int o = 0; o < k; ++o) {
+                if (o == c) continue;
+                float dot = 0.f;
+                for (int row = 0; row < k; ++row) dot = fmaf(A[row * kp + o], u[row], dot);
+                for (int row = 0; row < k; ++row) u[row] -= dot * A[row * kp + o];
+              }
+            float nn = 0.f;
+            for (int row = 0; row < k; ++row) nn = fmaf(u[row], u[row], nn);
+            if (nn > 0.25f) {
+              nn = rsqrtf(nn);
+              for (int row = 0; row < k; ++row) A[row * kp + c] = u[row] * nn;
+              break;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // R = V U^T
+        const int a = e / k, b = e % k;
+        float t = 0.f;
+        for (int j = 0; j < k; ++j) t = fmaf(V[a * kp + j], A[b * kp + j], t);
+        st.Rf[e] = t;
+      }
+      if (threadIdx.x == 0) {
+        double tr = 0.0;
+        bool empty = false;
+        for (int c = 0; c < k; ++c) {
+          tr += (double)sig[c];
+          empty |= cnt_s[c] == 0;
+        }
+        const double obj = (double)n - 2.0 * tr;
+        int dn = 0;
+        if (it > 0 && fabs(obj - *st.obj_prev) <= 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(obj))) dn = 1;
+        if (it + 1 >= max_iter) dn = 1;
+        *st.obj_prev = obj;
+        *st.done = dn;
+        if (iters_out) *iters_out = it + 1;
+        if (flags) {
+          if (empty) atomicOr(flags, 1);
+          if (sweeps >= 60) atomicOr(flags, 2);
+        }
+      }
+      for (int e = threadIdx.x; e < k; e += blockDim.x) st.counts[e] = 0;
+    }
+    if (!grid_barrier(st.bar, st.err)) return;
+    if (__ldcg(st.done)) break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -837,39 +880,47 @@ ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma
 }
 
 ancka_status make_disc_state(Workspace& ws, int64_t n, int k, DiscState* st) {
+  (void)n;
   ANCKA_TRY(ws.alloc(&st->Rf, (size_t)k * k));
   ANCKA_TRY(ws.alloc(&st->counts, (size_t)k));
   ANCKA_TRY(ws.alloc(&st->obj_prev, 1));
-  ANCKA_TRY(ws.alloc(&st->iter, 1));
   ANCKA_TRY(ws.alloc(&st->done, 1));
-  st->rows_per_blk = 2048;
-  st->nblk = (int)ceil_div(n, st->rows_per_blk);
-  ANCKA_TRY(ws.alloc(&st->partial, (size_t)st->nblk * k * k));
+  ANCKA_TRY(ws.alloc(&st->partial, (size_t)kDiscMaxGrid * k * k));
+  ANCKA_TRY(ws.alloc(&st->bar, 2));
+  ANCKA_TRY(ws.alloc(&st->err, 1));
   return ANCKA_OK;
 }
 
+size_t disc_smem_bytes() { return (size_t)(64 * 64 + 16384) * sizeof(float); }
+
+// Launch Discretize on a row-normalised block (one cooperative launch).
 ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64_t n, int k, int max_iter,
                             int32_t* labels, int32_t* iters_out, int32_t* flags, cudaStream_t s) {
-  k_disc_init<<<1, 256, 0, s>>>(st.Rf, st.counts, st.obj_prev, st.iter, st.done, k);
+  k_disc_init<<<1, 256, 0, s>>>(st.Rf, st.counts, st.obj_prev, st.done, st.bar, st.err, k);
   ANCKA_LAUNCHED();
-  const int nsl = 256 / k;
-  const size_t smem = (size_t)nsl * k * k * sizeof(float);
-  const int kp = (k + 1) & ~1;
-  const size_t svd_smem = (size_t)(k * kp + kp * kp) * sizeof(double);
-  static bool configured = false;
-  if (!configured) {
-    ANCKA_CUDA(cudaFuncSetAttribute(k_disc_msum, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 4096));
-    ANCKA_CUDA(cudaFuncSetAttribute(k_disc_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
-    configured = true;
+  const size_t smem = disc_smem_bytes();
+  static int max_grid = 0;
+  if (max_grid == 0) {
+    ANCKA_CUDA(cudaFuncSetAttribute(k_discretize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, occ = 0;
+    ANCKA_CUDA(cudaGetDevice(&dev));
+    ANCKA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ANCKA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_discretize, kDiscThreads, smem));
+    max_grid = sms * (occ > 2 ? 2 : occ);
+    if (max_grid > kDiscMaxGrid) max_grid = kDiscMaxGrid;
+    if (max_grid < 1) {
+      set_error("Discretize kernel cannot be resident");
+      return ANCKA_ERR_UNSUPPORTED;
+    }
   }
-  for (int it = 0; it < max_iter; ++it) {
-    ANCKA_TRY(disc_argmax(Qt, ldt, n, k, st, labels, s));
-    k_disc_msum<<<st.nblk, 256, smem, s>>>(Qt, ldt, n, k, labels, st.rows_per_blk, st.partial, st.done);
-    ANCKA_LAUNCHED();
-    k_disc_svd<<<1, 1024, svd_smem, s>>>(st.partial, st.nblk, k, n, st.counts, st.Rf, st.obj_prev, st.iter, st.done,
-                                  iters_out, flags, max_iter);
-    ANCKA_LAUNCHED();
-  }
+  int grid = (int)ceil_div(n, 2048);
+  if (grid > max_grid) grid = max_grid;
+  if (grid < 1) grid = 1;
+  DiscState stc = st;
+  void* args[] = {(void*)&Qt, (void*)&ldt, (void*)&n, (void*)&k, (void*)&max_iter, (void*)&labels,
+                  (void*)&stc, (void*)&iters_out, (void*)&flags};
+  ANCKA_CUDA(cudaLaunchCooperativeKernel((const void*)k_discretize, dim3(grid), dim3(kDiscThreads), args, smem, s));
+  ANCKA_LAUNCHED();
   return ANCKA_OK;
 }
 
@@ -1043,9 +1094,14 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   if (Q_out) ANCKA_CUDA(cudaMemcpy2DAsync(Q_out, sizeof(float) * wq, Q, sizeof(float) * ld, sizeof(float) * wq, n,
                                          cudaMemcpyDeviceToDevice, s));
   // a singular Gram matrix is reported (numeric failure of CholeskyQR)
-  int32_t cs = 0;
+  int32_t cs = 0, de = 0;
   ANCKA_CUDA(cudaMemcpyAsync(&cs, chol_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaMemcpyAsync(&de, st.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (de) {
+    set_error("Discretize: a grid barrier wait expired");
+    return ANCKA_ERR_TIMEOUT;
+  }
   if (cs) {
     set_error("CholeskyQR: Gram matrix of Z is not positive definite (rank-deficient block)");
     return ANCKA_ERR_NUMERIC;
@@ -1054,7 +1110,8 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
 }
 
 ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, int32_t ldq, int32_t max_iter,
-                        int32_t* labels, int32_t* iters_dev, int32_t* flags_dev, cudaStream_t s) {
+                        int32_t* labels, int32_t* iters_dev, int32_t* flags_dev, int32_t** err_dev,
+                        cudaStream_t s) {
   const int ldk = (int)round_up(k, 4);
   float* Qt;
   ANCKA_TRY(ws.alloc(&Qt, (size_t)n * ldk));
@@ -1062,6 +1119,7 @@ ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, in
   ANCKA_LAUNCHED();
   DiscState st;
   ANCKA_TRY(make_disc_state(ws, n, k, &st));
+  *err_dev = st.err;
   return run_discretize(st, Qt, ldk, n, k, max_iter, labels, iters_dev, flags_dev, s);
 }
 
@@ -1076,17 +1134,17 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // Bytes of caller-provided scratch Discretize needs for an n x k block.
 size_t discretize_scratch_bytes(int64_t n, int32_t k) {
   const size_t ldk = (size_t)round_up(k, 4);
-  const size_t nblk = (size_t)ceil_div(n, 2048);
-  return align256((size_t)n * ldk * sizeof(float)) + align256(nblk * k * k * sizeof(float)) +
+  return align256((size_t)n * ldk * sizeof(float)) + align256((size_t)kDiscMaxGrid * k * k * sizeof(float)) +
          align256((size_t)k * k * sizeof(float)) + align256((size_t)k * sizeof(int32_t)) + 256;
 }
 
 // Discretize on a caller-provided scratch block of at least
 // discretize_scratch_bytes(n, k) bytes (256-byte aligned); the per-call state
-// is reset by kernels and a memset, nothing is allocated.  *iters_dev points
-// into the scratch afterwards.
+// is reset by a kernel and a memset, nothing is allocated.  *iters_dev and
+// *err_dev point into the scratch afterwards.
 ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, int64_t n, int32_t k, int32_t ldq,
-                                int32_t max_iter, int32_t* labels, int32_t** iters_dev, cudaStream_t s) {
+                                int32_t max_iter, int32_t* labels, int32_t** iters_dev, int32_t** err_dev,
+                                cudaStream_t s) {
   if (bytes < discretize_scratch_bytes(n, k)) {
     set_error("Discretize scratch too small");
     return ANCKA_ERR_INVALID_ARG;
@@ -1096,23 +1154,23 @@ ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, in
   float* Qt = reinterpret_cast<float*>(p);
   p += align256((size_t)n * ldk * sizeof(float));
   DiscState st;
-  st.rows_per_blk = 2048;
-  st.nblk = (int)ceil_div(n, st.rows_per_blk);
   st.partial = reinterpret_cast<float*>(p);
-  p += align256((size_t)st.nblk * k * k * sizeof(float));
+  p += align256((size_t)kDiscMaxGrid * k * k * sizeof(float));
   st.Rf = reinterpret_cast<float*>(p);
   p += align256((size_t)k * k * sizeof(float));
   st.counts = reinterpret_cast<int32_t*>(p);
   p += align256((size_t)k * sizeof(int32_t));
   st.obj_prev = reinterpret_cast<double*>(p);
-  st.iter = reinterpret_cast<int32_t*>(p + 8);
-  st.done = reinterpret_cast<int32_t*>(p + 12);
-  int32_t* it = reinterpret_cast<int32_t*>(p + 16);
+  st.done = reinterpret_cast<int32_t*>(p + 8);
+  st.bar = reinterpret_cast<unsigned int*>(p + 16);
+  st.err = reinterpret_cast<int32_t*>(p + 24);
+  int32_t* it = reinterpret_cast<int32_t*>(p + 28);
   ANCKA_CUDA(cudaMemsetAsync(it, 0, sizeof(int32_t), s));
   k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qk, ldq, 0, n, k, Qt, ldk);
   ANCKA_LAUNCHED();
   ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, max_iter, labels, it, nullptr, s));
   *iters_dev = it;
+  *err_dev = st.err;
   return ANCKA_OK;
 }
 

@@ -8,9 +8,12 @@
 //              tcgen05.mma.cta_group::1.kind::f16 (M=128, N=256, K=16) into
 //              two ping-pong FP32 accumulators, commits stage releases and
 //              accumulator-ready signals;
-//   warps 2-5  epilogue: tcgen05.ld (32x32b) of the accumulator row owned by
-//              the thread (TMEM lane = query row), threshold test and insert
-//              into a register-resident list of the kCandC best scores.
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, each owning half of
+//              every tile's 256 columns; tcgen05.ld (32x32b) of the thread's
+//              accumulator row (TMEM lane = query row), threshold test and
+//              insert into a register-resident list of its 16 best scores.
+//              Row i thus leaves two 16-entry lists (one per column half),
+//              kCandC = 32 candidates in total.
 // The MMA of tile t+1 overlaps the epilogue of tile t.  n x n scores never
 // leave the SM.  Every mbarrier wait is bounded: on expiry the kernel records
 // an error code, stops all roles, drains its own copies and MMAs (bounded),
@@ -26,7 +29,9 @@ namespace {
 constexpr int kTM = 128;                 // query rows per CTA = TMEM lanes
 constexpr int kTN = 256;                 // key rows per tile = accumulator columns
 constexpr int kTK = 64;                  // features per stage: one 128-byte swizzle row
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kListC = kCandC / 2;     // per-thread list (two per row)
 constexpr int kABytes = kTM * kTK * 2;   // 16 KB per 64-feature block of A
 constexpr int kBBytes = kTN * kTK * 2;   // 32 KB per stage of B
 constexpr int kMaxStages = 8;
@@ -120,9 +125,9 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Issue a load of 32 consecutive FP32 accumulator columns of this thread's
+// TMEM lane; the registers are valid only after tmem_wait() + pin().
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -131,9 +136,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// make every later use of r depend on this point (after the wait)
+__device__ __forceinline__ void pin(uint32_t (&r)[32]) {
 #pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+  for (int q = 0; q < 32; ++q) asm volatile("" : "+r"(r[q]));
+}
+
+// Fold one 32-key chunk (scores in r, keys j0..j0+31) into the row's list.
+template <int C>
+__device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], int64_t j0, int64_t n, int64_t i,
+                                           float (&lv)[C], int32_t (&li)[C], float& thr, int& mp) {
+  // skip the chunk when no lane of the warp has a key above its threshold
+  float mx = __uint_as_float(r[0]);
+#pragma unroll
+  for (int e = 1; e < 32; ++e) mx = fmaxf(mx, __uint_as_float(r[e]));
+  if (!__any_sync(0xffffffffu, mx > thr)) return;
+  // pass mask against the threshold at chunk start (it only rises, so the
+  // mask is a superset); padding keys and the row itself removed
+  uint32_t pm = 0;
+#pragma unroll
+  for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(r[e]) > thr ? 1u : 0u) << e;
+  if (j0 + 32 > n) pm &= (j0 >= n) ? 0u : ((1u << (uint32_t)(n - j0)) - 1u);
+  if (i >= j0 && i < j0 + 32) pm &= ~(1u << (uint32_t)(i - j0));
+  // one insert per passing key; lanes without keys idle
+  while (__any_sync(0xffffffffu, pm != 0)) {
+    if (pm) {
+      const int e = __ffs(pm) - 1;
+      pm &= pm - 1;
+      float val = __uint_as_float(r[0]);
+#pragma unroll
+      for (int q = 1; q < 32; ++q)
+        if (e == q) val = __uint_as_float(r[q]);
+      if (val > thr) list_insert<C>(lv, li, thr, mp, val, (int32_t)(j0 + e));
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -158,8 +196,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     mbar_init(&bars->a_full, 1);
     mbar_init(&bars->tfull[0], 1);
     mbar_init(&bars->tfull[1], 1);
-    mbar_init(&bars->tempty[0], 4);
-    mbar_init(&bars->tempty[1], 4);
+    mbar_init(&bars->tempty[0], kEpiWarps);
+    mbar_init(&bars->tempty[1], kEpiWarps);
     mbar_init(&bars->drain, 1);
     bars->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -252,10 +290,12 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       }
     }
   } else {
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int ew = warp - 2;   // epilogue warp 0..7
+    const int q = warp & 3;    // TMEM lane quarter this warp may access
+    const int h = ew >> 2;     // column half of every tile
     const int r = q * 32 + lane;
     const int64_t i = ib + r;
-    constexpr int C = kCandC;
+    constexpr int C = kListC;
     float lv[C];
     int32_t li[C];
 #pragma unroll
@@ -272,31 +312,15 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       bool ok = mbar_wait(&bars->tfull[b], use & 1, abort, err, 5);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int64_t jb = (int64_t)t * kTN;
+      const int64_t jb = (int64_t)t * kTN + h * (kTN / 2);
+      const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * (kTN / 2));
 #pragma unroll 1
-      for (int c = 0; c < kTN / 32; ++c) {
-        float v[32];
-        tmem_ld32(lane_base + (uint32_t)(b * kTN + c * 32), v);
-        // pass mask against the threshold at chunk start (it only rises, so
-        // the mask is a superset); padding keys and the row itself removed
-        uint32_t pm = 0;
-#pragma unroll
-        for (int e = 0; e < 32; ++e) pm |= (v[e] > thr ? 1u : 0u) << e;
-        const int64_t j0 = jb + c * 32;
-        if (j0 + 32 > n) pm &= (j0 >= n) ? 0u : ((1u << (uint32_t)(n - j0)) - 1u);
-        if (i >= j0 && i < j0 + 32) pm &= ~(1u << (uint32_t)(i - j0));
-        // one insert per passing key; lanes without keys idle
-        while (__any_sync(0xffffffffu, pm != 0)) {
-          if (pm) {
-            const int e = __ffs(pm) - 1;
-            pm &= pm - 1;
-            float val = v[0];
-#pragma unroll
-            for (int q = 1; q < 32; ++q)
-              if (e == q) val = v[q];
-            if (val > thr) list_insert<C>(lv, li, thr, mp, val, (int32_t)(j0 + e));
-          }
-        }
+      for (int c = 0; c < kTN / 64; ++c) {
+        uint32_t rv[32];
+        tmem_ld32_issue(tb + (uint32_t)(c * 32), rv);
+        tmem_wait();
+        pin(rv);
+        fold_chunk<C>(rv, jb + c * 32, n, i, lv, li, thr, mp);
       }
       tc_fence_before();
       __syncwarp();
@@ -305,8 +329,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     if (i < n) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        cand_val[i * kCandC + c] = lv[c];
-        cand_idx[i * kCandC + c] = li[c];
+        cand_val[i * kCandC + h * C + c] = lv[c];
+        cand_idx[i * kCandC + h * C + c] = li[c];
       }
     }
   }

@@ -79,10 +79,16 @@ extern "C" ancka_status ancka_discretize_noalloc(const float* Qk, int64_t n, int
   void* scratch = nullptr;
   ANCKA_TRY(scratch_for_current_device(&scratch));
   int32_t* it_dev = nullptr;
-  ANCKA_TRY(discretize_scratch(scratch, kNoAllocScratchBytes, Qk, n, k, ldq, max_iter, labels, &it_dev, s));
-  if (iters) {
-    ANCKA_CUDA(cudaMemcpyAsync(iters, it_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    ANCKA_CUDA(cudaStreamSynchronize(s));
+  int32_t* err_dev = nullptr;
+  ANCKA_TRY(discretize_scratch(scratch, kNoAllocScratchBytes, Qk, n, k, ldq, max_iter, labels, &it_dev, &err_dev, s));
+  int32_t hit = 0, he = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&hit, it_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaMemcpyAsync(&he, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (he) {
+    set_error("ancka_discretize_noalloc: a grid barrier wait expired");
+    return ANCKA_ERR_TIMEOUT;
   }
+  if (iters) *iters = hit;
   return ANCKA_OK;
 }

@@ -1,7 +1,10 @@
 // Exact KNN lists from low-precision candidates (Section 3.1, reading R2).
 //
-// Row i comes out of the contraction with its kCandC best approximate scores
-// s^_ij and the worst kept one, thr_i.  With the per-pair error bound
+// Row i comes out of the contraction with kCandC approximate scores s^_ij:
+// one list of its 32 best (CUDA-core kernel) or two lists of the 16 best of
+// each half of the key columns (tensor-core kernel).  thr_i = the largest
+// minimum over the full lists bounds every key not kept.  With the per-pair
+// error bound
 //     |cos_ij - s^_ij| <= m_ij = e_i (1 + e_j) + e_j + acc (1 + e_i)(1 + e_j)
 // (e = quantisation bound of the row copies, acc = accumulation bound of the
 // contraction) the K-th largest lower bound lb_i = K-th max (s^ - m) is a
@@ -65,7 +68,7 @@ __device__ __forceinline__ double exact_cos(const float* __restrict__ xi, const 
 __global__ void __launch_bounds__(kWarps * 32)
 k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __restrict__ err,
          const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ nrm2,
-         const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx,
+         const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx, int lists,
          int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ fb_rows,
          int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand) {
   __shared__ unsigned int block_cand;
@@ -93,13 +96,23 @@ k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __re
     const unsigned kmask = __ballot_sync(0xffffffffu, rank == K - 1);
     const float lb = __shfl_sync(0xffffffffu, lower, __ffs(kmask) - 1);
     bool ok = nvalid >= K;
-    if (nvalid < n - 1) {  // there are nodes outside the candidate list
-      float thr = valid ? v : INFINITY;
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) thr = fminf(thr, __shfl_xor_sync(0xffffffffu, thr, off));
-      const float mmax = ei * (1.f + emax) + emax + acc_coef * (1.f + ei) * (1.f + emax);
-      // strict: every outside node's cosine is < lb <= the true K-th value
-      ok = ok && (thr + mmax < lb);
+    // The candidates come as `lists` lists of 32/lists lanes, each the best
+    // scores of its own share of the keys.  A full list bounds the keys of its
+    // share that it did not keep by its minimum; a list that is not full kept
+    // every key of its share.
+    {
+      const int per = 32 / lists;
+      float gmin = valid ? v : INFINITY;
+      for (int off = per / 2; off >= 1; off >>= 1) gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, off));
+      const unsigned gmask = per == 32 ? 0xffffffffu : (((1u << per) - 1u) << ((lane / per) * per));
+      const bool gfull = __popc(vmask & gmask) == per;
+      float U = gfull ? gmin : -INFINITY;
+      for (int off = per; off < 32; off <<= 1) U = fmaxf(U, __shfl_xor_sync(0xffffffffu, U, off));
+      if (__any_sync(0xffffffffu, gfull)) {
+        const float mmax = ei * (1.f + emax) + emax + acc_coef * (1.f + ei) * (1.f + emax);
+        // strict: every outside node's cosine is < lb <= the true K-th value
+        ok = ok && (U + mmax < lb);
+      }
     }
     if (!ok) {
       if (lane == 0) fb_rows[atomicAdd(fb_count, 1)] = (int32_t)i;
@@ -138,6 +151,8 @@ k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __re
 // thread 0 merges the warp lists.
 constexpr int kExWarps = 8;
 constexpr int kMaxK = 64;
+constexpr int kSlices = 64;           // key slices per flagged row
+constexpr int kSlicedMaxRows = 1024;  // flagged rows handled by the sliced kernels
 
 __global__ void __launch_bounds__(kExWarps * 32)
 k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const double* __restrict__ nrm2,
@@ -148,6 +163,7 @@ k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const dou
   __shared__ int head[kExWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t count = rows ? (int64_t)*row_count : all_rows;
+  if (rows && count <= kSlicedMaxRows) return;  // few rows: the sliced kernels take them
   for (int64_t r = blockIdx.x; r < count; r += gridDim.x) {
     const int64_t i = rows ? rows[r] : r;
     for (int t = threadIdx.x; t < kExWarps * kMaxK; t += blockDim.x) {
@@ -191,11 +207,93 @@ k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const dou
   }
 }
 
+// Few flagged rows: each row is split into kSlices key slices handled by
+// separate CTAs (the whole GPU streams X once per row instead of one SM);
+// every CTA writes the exact top-K of its slice, k_exh_merge combines them.
+__global__ void __launch_bounds__(kExWarps * 32)
+k_exh_sliced(const float* __restrict__ X, int64_t n, int d, int K, const double* __restrict__ nrm2,
+             const int32_t* __restrict__ rows, const int32_t* __restrict__ row_count, double* __restrict__ pv,
+             int32_t* __restrict__ pi) {
+  __shared__ double lv[kExWarps][kMaxK];
+  __shared__ int32_t li[kExWarps][kMaxK];
+  __shared__ int head[kExWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t count = *row_count;
+  if (count > kSlicedMaxRows) return;
+  for (int64_t item = blockIdx.x; item < count * kSlices; item += gridDim.x) {
+    const int64_t r = item / kSlices;
+    const int sl = (int)(item % kSlices);
+    const int64_t i = rows[r];
+    const int64_t j0 = n * sl / kSlices, j1 = n * (sl + 1) / kSlices;
+    for (int t = threadIdx.x; t < kExWarps * kMaxK; t += blockDim.x) {
+      lv[t / kMaxK][t % kMaxK] = -INFINITY;
+      li[t / kMaxK][t % kMaxK] = INT32_MAX;
+    }
+    __syncthreads();
+    const float* xi = X + i * (int64_t)d;
+    const double n2i = nrm2[i];
+    for (int64_t j = j0 + w; j < j1; j += kExWarps) {
+      if (j == i) continue;
+      const double cs = exact_cos(xi, X + j * (int64_t)d, d, n2i, nrm2[j]);
+      if (lane == 0 && before(cs, (int32_t)j, lv[w][K - 1], li[w][K - 1])) {
+        int p = K - 1;
+        while (p > 0 && before(cs, (int32_t)j, lv[w][p - 1], li[w][p - 1])) {
+          lv[w][p] = lv[w][p - 1];
+          li[w][p] = li[w][p - 1];
+          --p;
+        }
+        lv[w][p] = cs;
+        li[w][p] = (int32_t)j;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < kExWarps; ++q) head[q] = 0;
+      for (int o = 0; o < K; ++o) {
+        int best = 0;
+        for (int q = 1; q < kExWarps; ++q)
+          if (before(lv[q][head[q]], li[q][head[q]], lv[best][head[best]], li[best][head[best]])) best = q;
+        pv[(r * kSlices + sl) * K + o] = lv[best][head[best]];
+        pi[(r * kSlices + sl) * K + o] = li[best][head[best]];
+        if (head[best] < K - 1) ++head[best];
+        else { lv[best][head[best]] = -INFINITY; li[best][head[best]] = INT32_MAX; }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_exh_merge(const int32_t* __restrict__ rows, const int32_t* __restrict__ row_count, int K,
+                            const double* __restrict__ pv, const int32_t* __restrict__ pi,
+                            int32_t* __restrict__ out_idx, float* __restrict__ out_sim) {
+  const int64_t count = *row_count;
+  if (count > kSlicedMaxRows) return;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rows[r];
+    int head[kSlices];
+    for (int q = 0; q < kSlices; ++q) head[q] = 0;
+    const double* v = pv + r * kSlices * K;
+    const int32_t* x = pi + r * kSlices * K;
+    for (int o = 0; o < K; ++o) {
+      int best = -1;
+      for (int q = 0; q < kSlices; ++q) {
+        if (head[q] >= K) continue;
+        if (best < 0 || before(v[q * K + head[q]], x[q * K + head[q]], v[best * K + head[best]], x[best * K + head[best]]))
+          best = q;
+      }
+      out_idx[i * K + o] = x[best * K + head[best]];
+      out_sim[i * K + o] = (float)v[best * K + head[best]];
+      ++head[best];
+    }
+  }
+}
+
 }  // namespace
 
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
                         const PrepOut& pr, float acc_coef, const float* cand_val,
-                        const int32_t* cand_idx, int32_t* out_idx, float* out_sim,
+                        const int32_t* cand_idx, int lists, int32_t* out_idx, float* out_sim,
                         int64_t* n_candidates, int64_t* n_fallback, bool want_counts,
                         cudaStream_t s) {
   int32_t *fb_rows, *fb_count;
@@ -206,8 +304,17 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
   const bool use_candidates = cand_val != nullptr;
   if (use_candidates) {
     k_rerank<<<(unsigned)ceil_div(n, kWarps), kWarps * 32, 0, s>>>(
-        X, n, d, K, pr.err, pr.err_max, acc_coef, pr.nrm2, cand_val, cand_idx, out_idx, out_sim,
+        X, n, d, K, pr.err, pr.err_max, acc_coef, pr.nrm2, cand_val, cand_idx, lists, out_idx, out_sim,
         fb_rows, fb_count, ncand);
+    ANCKA_LAUNCHED();
+    // flagged rows: sliced over the whole GPU when few, one CTA per row when many
+    double* pv;
+    int32_t* pi;
+    ANCKA_TRY(ws.alloc(&pv, (size_t)kSlicedMaxRows * kSlices * K));
+    ANCKA_TRY(ws.alloc(&pi, (size_t)kSlicedMaxRows * kSlices * K));
+    k_exh_sliced<<<1216, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, fb_rows, fb_count, pv, pi);
+    ANCKA_LAUNCHED();
+    k_exh_merge<<<8, 128, 0, s>>>(fb_rows, fb_count, K, pv, pi, out_idx, out_sim);
     ANCKA_LAUNCHED();
     k_knn_exhaustive<<<304, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, fb_rows, fb_count, 0, out_idx,
                                                    out_sim);
