@@ -40,12 +40,14 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_contract_traffic.txt")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--knn-probe", default=None, metavar="N,D",
+                    help="only run the BF16 KNN twice on a seeded N x D Gaussian matrix (profiling aid)")
     return ap.parse_args()
 
 
@@ -79,7 +81,7 @@ def recorded_traffic(kernel_file):
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) while the timed region runs."""
+    """nvidia-smi samples (20 ms) while the timed region runs."""
 
     def __init__(self, index):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -87,7 +89,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(index)], stdout=subprocess.PIPE,
+                                       "-lms", "20", "-i", str(index)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -173,6 +175,25 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def knn_probe(args):
+    """Kernel-focused run for profiling: ancka_knn (BF16) twice on a seeded
+    N x D standard-normal matrix; prints the second call's contraction time."""
+    import torch
+    from paper_2408_05459_gb300 import ancka, build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    ancka.load()
+    n, d = (int(v) for v in args.knn_probe.split(","))
+    X = torch.as_tensor(np.random.default_rng(0).standard_normal((n, d)).astype(np.float32), device="cuda")
+    for _ in range(2):
+        _, _, info = ancka.knn(X, 10, "bf16")
+    torch.cuda.synchronize()
+    ms = info["ms_contract"]
+    print(json.dumps({"probe": "knn_bf16", "n": n, "d": d, "ms_contract": round(ms, 3),
+                      "tflops": round(2.0 * n * n * d / (ms * 1e-3) / 1e12, 1),
+                      "knn_fallback_rows": info["knn_fallback_rows"]}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -180,6 +201,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.knn_probe:
+        return knn_probe(args)
 
     import torch
     from paper_2408_05459_gb300 import ancka, build as B
