@@ -190,6 +190,7 @@ def knn_probe(args):
     torch.cuda.synchronize()
     ms = info["ms_contract"]
     print(json.dumps({"probe": "knn_bf16", "n": n, "d": d, "ms_contract": round(ms, 3),
+                      "ms_knn": round(info["ms_knn"], 3), "knn_exhaustive_rows": info["knn_exhaustive_rows"],
                       "tflops": round(2.0 * n * n * d / (ms * 1e-3) / 1e12, 1),
                       "knn_fallback_rows": info["knn_fallback_rows"]}), flush=True)
 

@@ -117,6 +117,7 @@ typedef struct {
 typedef struct {
   int64_t knn_candidates;      /* (row, candidate) pairs re-ranked exactly */
   int64_t knn_fallback_rows;   /* rows whose candidates could not be certified */
+  int64_t knn_exhaustive_rows; /* of those, rows recomputed by an exhaustive exact scan */
   int32_t iters_run;           /* orthogonal iterations executed */
   int32_t n_phi;               /* entries of phi[] used: phi(Y0), then one per Discretize */
   double phi[ANCKA_MAX_TRACE];

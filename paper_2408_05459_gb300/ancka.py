@@ -44,6 +44,7 @@ class Outputs(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("knn_candidates", ctypes.c_int64), ("knn_fallback_rows", ctypes.c_int64),
+                ("knn_exhaustive_rows", ctypes.c_int64),
                 ("iters_run", ctypes.c_int32), ("n_phi", ctypes.c_int32),
                 ("phi", ctypes.c_double * MAX_TRACE), ("disc_iters", ctypes.c_int32 * MAX_TRACE),
                 ("taken", ctypes.c_int32 * MAX_TRACE), ("phi_best", ctypes.c_double),
@@ -55,6 +56,7 @@ class Info(ctypes.Structure):
     def to_dict(self) -> dict:
         n = self.n_phi
         return dict(knn_candidates=self.knn_candidates, knn_fallback_rows=self.knn_fallback_rows,
+                    knn_exhaustive_rows=self.knn_exhaustive_rows,
                     iters_run=self.iters_run, n_phi=n, phi=list(self.phi[:n]), disc_iters=list(self.disc_iters[:n]),
                     taken=list(self.taken[:n]), phi_best=self.phi_best, numeric_flags=self.numeric_flags,
                     ms_knn=self.ms_knn, ms_build=self.ms_build, ms_init=self.ms_init, ms_iter=self.ms_iter,

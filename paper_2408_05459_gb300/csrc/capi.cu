@@ -169,7 +169,7 @@ int max_candidate_K(int prec) { return prec == ANCKA_PREC_BF16 ? kCandC / 2 - 4 
 // the KNN lists with every step on the device
 ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
                       int32_t* idx, float* sim, int32_t** zero_row, int64_t* ncand, int64_t* nfb,
-                      bool counts, cudaStream_t s, cudaEvent_t* contract_ev = nullptr) {
+                      int64_t* nex, bool counts, cudaStream_t s, cudaEvent_t* contract_ev = nullptr) {
   PrepOut pr;
   ANCKA_TRY(prep_rows(ws, X, n, d, prec, &pr, s));
   if (zero_row) *zero_row = pr.zero_row;
@@ -205,10 +205,11 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
     if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
     // the tensor-core kernel leaves two 16-entry lists per row (one per half
     // of the key columns), the CUDA-core kernel one 32-entry list
-    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, acc, cv, ci, prec == ANCKA_PREC_BF16 ? 2 : 1, idx, sim, ncand, nfb,
-                         counts, s));
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, acc, cv, ci, prec == ANCKA_PREC_BF16 ? 2 : 1, prec, idx, sim, ncand,
+                         nfb, nex, counts, s));
   } else {
-    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, 0.f, nullptr, nullptr, 1, idx, sim, ncand, nfb, counts, s));
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, 0.f, nullptr, nullptr, 1, ANCKA_PREC_FP32, idx, sim, ncand, nfb, nex,
+                         counts, s));
   }
   return ANCKA_OK;
 }
@@ -275,7 +276,7 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     int32_t* idx = (out && out->knn_idx) ? out->knn_idx : nullptr;
     float* sim = (out && out->knn_sim) ? out->knn_sim : nullptr;
     int32_t* zero_row = nullptr;
-    int64_t ncand = 0, nfb = 0;
+    int64_t ncand = 0, nfb = 0, nex = 0;
     int32_t* bad;
     st = ws.zeros(&bad, 1);
     if (st == ANCKA_OK && !knn_idx_in) {
@@ -283,7 +284,7 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       if (!idx) st = ws.alloc(&idx, (size_t)n * K);
       if (st == ANCKA_OK && !sim) st = ws.alloc(&sim, (size_t)n * K);
       if (st == ANCKA_OK)
-        st = knn_impl(ws, X, n, d, K, p->knn_prec, idx, sim, &zero_row, &ncand, &nfb, info != nullptr, s,
+        st = knn_impl(ws, X, n, d, K, p->knn_prec, idx, sim, &zero_row, &ncand, &nfb, &nex, info != nullptr, s,
                       info && K <= max_candidate_K(p->knn_prec) ? cev : nullptr);
       contract_timed = info && K <= max_candidate_K(p->knn_prec);
     } else if (st == ANCKA_OK) {
@@ -351,6 +352,7 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       info->iters_run = p->T;
       info->knn_candidates = ncand;
       info->knn_fallback_rows = nfb;
+      info->knn_exhaustive_rows = nex;
     }
   }  // workspace released (stream-ordered)
   if (info) {
@@ -432,7 +434,7 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
     cudaEventRecord(a, s);
   }
   ancka_status st;
-  int64_t nc = 0, nf = 0;
+  int64_t nc = 0, nf = 0, ne = 0;
   cudaEvent_t cev[2] = {nullptr, nullptr};
   const bool timed = info && K <= max_candidate_K(prec);
   if (timed) {
@@ -441,7 +443,7 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
   }
   {
     Workspace ws(s);
-    st = knn_impl(ws, X, n, d, K, prec, out_idx, out_sim, nullptr, &nc, &nf, info != nullptr, s,
+    st = knn_impl(ws, X, n, d, K, prec, out_idx, out_sim, nullptr, &nc, &nf, &ne, info != nullptr, s,
                   timed ? cev : nullptr);
   }
   if (info) {
@@ -454,6 +456,7 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
     info->ms_total = ms;
     info->knn_candidates = nc;
     info->knn_fallback_rows = nf;
+    info->knn_exhaustive_rows = ne;
     if (timed) {
       float mc = 0.f;
       if (st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;

@@ -185,13 +185,20 @@ ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, 
                                  int32_t* err, cudaStream_t s);
 bool knn_tc_available();
 int knn_tc_max_dp();
+// collect pass: for the n_a query rows listed in `rows`, every key j != row
+// with a BF16 score >= thr[r] is appended to buf[r * cap ..] (cnt[r] counts,
+// also past cap)
+ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
+                              const float* thr, int32_t* cnt, int32_t* buf, int cap, int32_t* err, cudaStream_t s);
 
 // rerank.cu: certified exact re-rank + exhaustive fallback
+// lists: 1 (one 32-list per row) or 2 (two 16-lists); collect_prec ==
+// ANCKA_PREC_BF16 sends uncertified rows through the tensor-core collect pass
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
                         const PrepOut& pr, float acc_coef, const float* cand_val,
-                        const int32_t* cand_idx, int lists, int32_t* out_idx, float* out_sim,
-                        int64_t* n_candidates, int64_t* n_fallback, bool want_counts,
-                        cudaStream_t s);
+                        const int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx,
+                        float* out_sim, int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive,
+                        bool want_counts, cudaStream_t s);
 
 // graph.cu: walk structures
 struct Csr {

@@ -20,6 +20,8 @@
 // frees TMEM and returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ancka {
@@ -174,10 +176,43 @@ __device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], int64_t j0, 
   }
 }
 
+// Collect mode: append every key whose score reaches the row's fixed
+// threshold t to the row's buffer (cap entries; the counter keeps counting
+// past cap so the caller can see an overflow).
+__device__ __forceinline__ void collect_chunk(const uint32_t (&r)[32], int64_t j0, int64_t n, int64_t i, float t,
+                                              int64_t ra, int32_t* __restrict__ cnt, int32_t* __restrict__ buf,
+                                              int cap) {
+  float mx = __uint_as_float(r[0]);
+#pragma unroll
+  for (int e = 1; e < 32; ++e) mx = fmaxf(mx, __uint_as_float(r[e]));
+  if (!__any_sync(0xffffffffu, mx >= t)) return;
+  uint32_t pm = 0;
+#pragma unroll
+  for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(r[e]) >= t ? 1u : 0u) << e;
+  if (j0 + 32 > n) pm &= (j0 >= n) ? 0u : ((1u << (uint32_t)(n - j0)) - 1u);
+  if (i >= j0 && i < j0 + 32) pm &= ~(1u << (uint32_t)(i - j0));
+  while (pm) {
+    const int e = __ffs(pm) - 1;
+    pm &= pm - 1;
+    const int pos = atomicAdd(&cnt[ra], 1);
+    if (pos < cap) buf[ra * (int64_t)cap + pos] = (int32_t)(j0 + e);
+  }
+}
+
+struct CollectArgs {
+  const int32_t* a_rows;  // global row of each compact query row
+  int64_t n_a;            // compact query rows
+  const float* thr;       // per compact row threshold
+  int32_t* cnt;           // per compact row counter
+  int32_t* buf;           // n_a x cap keys
+  int cap;
+};
+
+template <bool kCollect>
 __global__ void __launch_bounds__(kThreads, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-         int64_t n_pad, int kb_count, int nstages, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
-         int* __restrict__ err) {
+         int64_t n_pad, int kb_count, int nstages, int tps, float* __restrict__ cand_val,
+         int32_t* __restrict__ cand_idx, CollectArgs ca, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -185,7 +220,11 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   Bars* bars = reinterpret_cast<Bars*>(sB + nstages * kBBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ib = (int64_t)blockIdx.x * kTM;
-  const int ntiles = (int)ceil_div(n_pad, kTN);
+  // this CTA's key tiles: [t_begin, t_begin + ntiles) (collect mode splits
+  // the sweep over blockIdx.y; list mode sweeps all keys)
+  const int all_tiles = (int)ceil_div(n_pad, kTN);
+  const int t_begin = (int)blockIdx.y * tps;
+  const int ntiles = max(0, min(all_tiles, t_begin + tps) - t_begin);
   volatile int* abort = &bars->abort;
 
   if (threadIdx.x == 0) {
@@ -233,7 +272,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           }
           pending[stage] = false;
           mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
-          tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, t * kTN, &bars->full[stage]);
+          tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, (t_begin + t) * kTN, &bars->full[stage]);
           pending[stage] = true;
           pend_par[stage] = phase;
           if (++stage == nstages) {
@@ -294,7 +333,11 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     const int q = warp & 3;    // TMEM lane quarter this warp may access
     const int h = ew >> 2;     // column half of every tile
     const int r = q * 32 + lane;
-    const int64_t i = ib + r;
+    // list mode: query row ib + r; collect mode: compact row ra -> global row
+    const int64_t ra = ib + r;
+    const bool row_ok = kCollect ? (ra < ca.n_a) : (ra < n);
+    const int64_t i = kCollect ? (row_ok ? (int64_t)ca.a_rows[ra] : -1) : ra;
+    const float t_row = kCollect && row_ok ? ca.thr[ra] : INFINITY;
     constexpr int C = kListC;
     float lv[C];
     int32_t li[C];
@@ -312,7 +355,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       bool ok = mbar_wait(&bars->tfull[b], use & 1, abort, err, 5);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int64_t jb = (int64_t)t * kTN + h * (kTN / 2);
+      const int64_t jb = (int64_t)(t_begin + t) * kTN + h * (kTN / 2);
       const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * (kTN / 2));
 #pragma unroll 1
       for (int c = 0; c < kTN / 64; ++c) {
@@ -320,13 +363,17 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         tmem_ld32_issue(tb + (uint32_t)(c * 32), rv);
         tmem_wait();
         pin(rv);
-        fold_chunk<C>(rv, jb + c * 32, n, i, lv, li, thr, mp);
+        if constexpr (kCollect) {
+          collect_chunk(rv, jb + c * 32, n, i, t_row, ra, ca.cnt, ca.buf, ca.cap);
+        } else {
+          fold_chunk<C>(rv, jb + c * 32, n, i, lv, li, thr, mp);
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->tempty[b]);
     }
-    if (i < n) {
+    if (!kCollect && row_ok) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         cand_val[i * kCandC + h * C + c] = lv[c];
@@ -402,9 +449,56 @@ ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, 
   CUtensorMap ta, tb;
   ANCKA_TRY(make_map(&ta, pr.xb, pr.dp, pr.n_pad, kTM));
   ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN));
-  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_knn_tc<<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(ta, tb, n, pr.n_pad, kb_count, nstages, cand_val,
-                                                            cand_idx, err);
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CollectArgs none{};
+  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
+  k_knn_tc<false><<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(ta, tb, n, pr.n_pad, kb_count, nstages,
+                                                                   all_tiles, cand_val, cand_idx, none, err);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+namespace {
+__global__ void k_gather_rows(const __nv_bfloat16* __restrict__ xb, int dp, const int32_t* __restrict__ rows,
+                              int64_t n_a, int64_t n_a_pad, __nv_bfloat16* __restrict__ out) {
+  const int64_t r = blockIdx.x;
+  if (r >= n_a_pad) return;
+  const uint4* src = r < n_a ? reinterpret_cast<const uint4*>(xb + (int64_t)rows[r] * dp) : nullptr;
+  uint4* dst = reinterpret_cast<uint4*>(out + r * dp);
+  for (int c = threadIdx.x; c < dp / 8; c += blockDim.x) dst[c] = src ? src[c] : make_uint4(0, 0, 0, 0);
+}
+}  // namespace
+
+ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
+                              const float* thr, int32_t* cnt, int32_t* buf, int cap, int32_t* err, cudaStream_t s) {
+  const int kb_count = pr.dp / kTK;
+  const size_t fixed = 1024 + (size_t)kb_count * kABytes + sizeof(Bars);
+  int nstages = (int)((kMaxSmem - fixed) / kBBytes);
+  if (nstages > kMaxStages) nstages = kMaxStages;
+  size_t smem = fixed + (size_t)nstages * kBBytes;
+  if (smem < 120 * 1024) smem = 120 * 1024;
+  const int64_t n_a_pad = round_up(n_a, kTM);
+  __nv_bfloat16* af;
+  ANCKA_TRY(ws.alloc(&af, (size_t)n_a_pad * pr.dp));
+  k_gather_rows<<<(unsigned)n_a_pad, 64, 0, s>>>(pr.xb, pr.dp, rows, n_a, n_a_pad, af);
+  ANCKA_LAUNCHED();
+  CUtensorMap ta, tb;
+  ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM));
+  ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN));
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CollectArgs ca{rows, n_a, thr, cnt, buf, cap};
+  // split the key sweep so that about two waves of CTAs run
+  int sms = 152, dev = 0;
+  ANCKA_CUDA(cudaGetDevice(&dev));
+  ANCKA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
+  const int64_t qblocks = n_a_pad / kTM;
+  int splits = (int)std::max<int64_t>(1, std::min<int64_t>(all_tiles, (2 * sms) / std::max<int64_t>(1, qblocks)));
+  const int tps = (int)ceil_div(all_tiles, splits);
+  splits = (int)ceil_div(all_tiles, tps);
+  k_knn_tc<true><<<dim3((unsigned)qblocks, (unsigned)splits), kThreads, smem, s>>>(ta, tb, n, pr.n_pad, kb_count,
+                                                                                  nstages, tps, nullptr, nullptr, ca,
+                                                                                  err);
   ANCKA_LAUNCHED();
   return ANCKA_OK;
 }

@@ -70,7 +70,7 @@ k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __re
          const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ nrm2,
          const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx, int lists,
          int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ fb_rows,
-         int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand) {
+         float* __restrict__ fb_thr, int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand) {
   __shared__ unsigned int block_cand;
   if (threadIdx.x == 0) block_cand = 0;
   __syncthreads();
@@ -96,6 +96,7 @@ k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __re
     const unsigned kmask = __ballot_sync(0xffffffffu, rank == K - 1);
     const float lb = __shfl_sync(0xffffffffu, lower, __ffs(kmask) - 1);
     bool ok = nvalid >= K;
+    const float mmax = ei * (1.f + emax) + emax + acc_coef * (1.f + ei) * (1.f + emax);
     // The candidates come as `lists` lists of 32/lists lanes, each the best
     // scores of its own share of the keys.  A full list bounds the keys of its
     // share that it did not keep by its minimum; a list that is not full kept
@@ -109,13 +110,17 @@ k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __re
       float U = gfull ? gmin : -INFINITY;
       for (int off = per; off < 32; off <<= 1) U = fmaxf(U, __shfl_xor_sync(0xffffffffu, U, off));
       if (__any_sync(0xffffffffu, gfull)) {
-        const float mmax = ei * (1.f + emax) + emax + acc_coef * (1.f + ei) * (1.f + emax);
         // strict: every outside node's cosine is < lb <= the true K-th value
         ok = ok && (U + mmax < lb);
       }
     }
     if (!ok) {
-      if (lane == 0) fb_rows[atomicAdd(fb_count, 1)] = (int32_t)i;
+      // a key j can be in the list only if s^_ij >= lb - m_ij >= lb - mmax
+      if (lane == 0) {
+        const int pos = atomicAdd(fb_count, 1);
+        fb_rows[pos] = (int32_t)i;
+        if (fb_thr) fb_thr[pos] = nvalid >= K ? lb - mmax : -INFINITY;
+      }
     } else {
       const bool inR = valid && upper >= lb;
       unsigned rmask = __ballot_sync(0xffffffffu, inR);
@@ -207,6 +212,59 @@ k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const dou
   }
 }
 
+// Exact re-rank of the keys collected for flagged rows (every key whose
+// low-precision score reached the row's threshold): batches of 32 exact
+// cosines are sorted and merged into a running (value desc, index asc) top-32.
+// A row whose buffer overflowed (or holds fewer than K keys) goes to the
+// exhaustive kernels.
+__global__ void __launch_bounds__(kWarps * 32)
+k_rerank_collected(const float* __restrict__ X, int d, int K, const double* __restrict__ nrm2,
+                   const int32_t* __restrict__ rows, const int32_t* __restrict__ n_rows_p,
+                   const int32_t* __restrict__ cnt, const int32_t* __restrict__ buf, int cap,
+                   int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ ov_rows,
+                   int32_t* __restrict__ ov_count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (r >= *n_rows_p) return;
+  const int64_t i = rows[r];
+  const int c = cnt[r];
+  if (c > cap || c < K) {
+    if (lane == 0) ov_rows[atomicAdd(ov_count, 1)] = (int32_t)i;
+    return;
+  }
+  const float* xi = X + i * (int64_t)d;
+  const double n2i = nrm2[i];
+  double tv = -INFINITY;
+  int32_t tj = INT32_MAX;
+  for (int q0 = 0; q0 < c; q0 += 32) {
+    const int32_t mine = (q0 + lane < c) ? buf[r * (int64_t)cap + q0 + lane] : -1;
+    double nv = -INFINITY;
+    int32_t nj = INT32_MAX;
+    const int nb = min(32, c - q0);
+    for (int t = 0; t < nb; ++t) {
+      const int32_t jt = __shfl_sync(0xffffffffu, mine, t);
+      const double cs = exact_cos(xi, X + (int64_t)jt * d, d, n2i, nrm2[jt]);
+      if (lane == t) {
+        nv = cs;
+        nj = jt;
+      }
+    }
+    warp_sort(nv, nj);
+    // best of the running list and the reversed new batch (a bitonic sequence)
+    const double rv = __shfl_sync(0xffffffffu, nv, 31 - lane);
+    const int32_t rj = __shfl_sync(0xffffffffu, nj, 31 - lane);
+    if (before(rv, rj, tv, tj)) {
+      tv = rv;
+      tj = rj;
+    }
+    warp_sort(tv, tj);
+  }
+  if (lane < K) {
+    out_idx[i * K + lane] = tj;
+    out_sim[i * K + lane] = (float)tv;
+  }
+}
+
 // Few flagged rows: each row is split into kSlices key slices handled by
 // separate CTAs (the whole GPU streams X once per row instead of one SM);
 // every CTA writes the exact top-K of its slice, k_exh_merge combines them.
@@ -293,9 +351,9 @@ __global__ void k_exh_merge(const int32_t* __restrict__ rows, const int32_t* __r
 
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
                         const PrepOut& pr, float acc_coef, const float* cand_val,
-                        const int32_t* cand_idx, int lists, int32_t* out_idx, float* out_sim,
-                        int64_t* n_candidates, int64_t* n_fallback, bool want_counts,
-                        cudaStream_t s) {
+                        const int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx,
+                        float* out_sim, int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive,
+                        bool want_counts, cudaStream_t s) {
   int32_t *fb_rows, *fb_count;
   unsigned long long* ncand;
   ANCKA_TRY(ws.alloc(&fb_rows, (size_t)n));
@@ -303,27 +361,65 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
   ANCKA_TRY(ws.zeros(&ncand, 1));
   const bool use_candidates = cand_val != nullptr;
   if (use_candidates) {
+    float* fb_thr = nullptr;
+    if (collect_prec == ANCKA_PREC_BF16) ANCKA_TRY(ws.alloc(&fb_thr, (size_t)n));
     k_rerank<<<(unsigned)ceil_div(n, kWarps), kWarps * 32, 0, s>>>(
         X, n, d, K, pr.err, pr.err_max, acc_coef, pr.nrm2, cand_val, cand_idx, lists, out_idx, out_sim,
-        fb_rows, fb_count, ncand);
+        fb_rows, fb_thr, fb_count, ncand);
     ANCKA_LAUNCHED();
-    // flagged rows: sliced over the whole GPU when few, one CTA per row when many
+    int32_t* ex_rows = fb_rows;
+    int32_t* ex_count = fb_count;
+    if (collect_prec == ANCKA_PREC_BF16) {
+      // flagged rows: collect every key above the row's certified threshold
+      // with the tensor-core contraction, then re-rank those exactly
+      int32_t nf = 0;
+      ANCKA_CUDA(cudaMemcpyAsync(&nf, fb_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaStreamSynchronize(s));
+      ANCKA_TRY(ws.zeros(&ex_count, 1));
+      ANCKA_TRY(ws.alloc(&ex_rows, (size_t)(nf > 0 ? nf : 1)));
+      if (nf > 0) {
+        constexpr int kCap = 2048;
+        int32_t *cnt, *buf, *terr;
+        ANCKA_TRY(ws.zeros(&cnt, (size_t)nf));
+        ANCKA_TRY(ws.alloc(&buf, (size_t)nf * kCap));
+        ANCKA_TRY(ws.zeros(&terr, 1));
+        ANCKA_TRY(knn_collect_bf16(ws, pr, n, fb_rows, nf, fb_thr, cnt, buf, kCap, terr, s));
+        k_rerank_collected<<<(unsigned)ceil_div(nf, kWarps), kWarps * 32, 0, s>>>(
+            X, d, K, pr.nrm2, fb_rows, fb_count, cnt, buf, kCap, out_idx, out_sim, ex_rows, ex_count);
+        ANCKA_LAUNCHED();
+        int32_t hterr = 0;
+        ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        ANCKA_CUDA(cudaStreamSynchronize(s));
+        if (hterr) {
+          set_error("tensor-core collect pass: a pipeline wait expired (role %d)", hterr);
+          return ANCKA_ERR_TIMEOUT;
+        }
+      }
+    }
+    // rows left: sliced over the whole GPU when few, one CTA per row when many
     double* pv;
     int32_t* pi;
     ANCKA_TRY(ws.alloc(&pv, (size_t)kSlicedMaxRows * kSlices * K));
     ANCKA_TRY(ws.alloc(&pi, (size_t)kSlicedMaxRows * kSlices * K));
-    k_exh_sliced<<<1216, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, fb_rows, fb_count, pv, pi);
+    k_exh_sliced<<<1216, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, ex_rows, ex_count, pv, pi);
     ANCKA_LAUNCHED();
-    k_exh_merge<<<8, 128, 0, s>>>(fb_rows, fb_count, K, pv, pi, out_idx, out_sim);
+    k_exh_merge<<<8, 128, 0, s>>>(ex_rows, ex_count, K, pv, pi, out_idx, out_sim);
     ANCKA_LAUNCHED();
-    k_knn_exhaustive<<<304, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, fb_rows, fb_count, 0, out_idx,
+    k_knn_exhaustive<<<304, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, ex_rows, ex_count, 0, out_idx,
                                                    out_sim);
     ANCKA_LAUNCHED();
+    if (want_counts) {
+      int32_t ex = 0;
+      ANCKA_CUDA(cudaMemcpyAsync(&ex, ex_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaStreamSynchronize(s));
+      if (n_exhaustive) *n_exhaustive = ex;
+    }
   } else {
     const unsigned g = (unsigned)(n < 4096 ? n : 4096);
     k_knn_exhaustive<<<g, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, nullptr, nullptr, n, out_idx,
                                                  out_sim);
     ANCKA_LAUNCHED();
+    if (n_exhaustive) *n_exhaustive = n;
   }
   if (want_counts) {
     int32_t fb = 0;

@@ -96,3 +96,14 @@ def test_knn_deterministic(ak):
         a = _run(ak, X, 9, prec)
         b = _run(ak, X, 9, prec)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_knn_collect_pass_dense_rows(ak):
+    """Dense random rows: many rows cannot be certified from the two 16-entry
+    lists and go through the collect pass; all lists must still be exact."""
+    X = np.random.default_rng(12).standard_normal((12000, 256)).astype(np.float32)
+    idx, sim, info = _run(ak, X, 10, "bf16")
+    assert info["knn_fallback_rows"] > 0
+    assert info["knn_exhaustive_rows"] <= max(1, info["knn_fallback_rows"] // 10)
+    c = compare_knn(X, 10, np.arange(12000), idx, sim)
+    assert c["exact_rows"] + c["near_tie_rows"] == 12000
