@@ -47,7 +47,26 @@ struct SpmmArgs {
   int ldo = 0;
   int64_t nrows = 0;
   int nv4 = 0;  // float4 chunks per row
+  const int32_t* long_rows = nullptr;  // rows with more than long_min entries
+  const int32_t* n_long = nullptr;     // their count (device)
+  int64_t n_long_host = -1;            // the same count on the host (-1: not known)
+  int64_t long_min = 0;                // rows with more entries than this are long
 };
+
+__device__ __forceinline__ void fma4(float4& acc, float w, const float4& x) {
+  acc.x = fmaf(w, x.x, acc.x);
+  acc.y = fmaf(w, x.y, acc.y);
+  acc.z = fmaf(w, x.z, acc.z);
+  acc.w = fmaf(w, x.w, acc.w);
+}
+
+// A row is long when it has more than max(kLongRowMin, 4 x the mean row
+// length) entries; long rows go to k_spmm_long.
+constexpr int64_t kLongRowMin = 256;
+
+__device__ __forceinline__ int64_t row_entries(const SpmmArgs& a, int64_t i) {
+  return (a.ptrA[i + 1] - a.ptrA[i]) + (a.ptrB ? a.ptrB[i + 1] - a.ptrB[i] : 0);
+}
 
 template <int G>
 __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
@@ -55,16 +74,34 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
   const int64_t i = t / G;
   const int g = (int)(t % G);
   if (i >= a.nrows || g >= a.nv4) return;
+  if (row_entries(a, i) > a.long_min) return;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int64_t p = a.ptrA[i], e = a.ptrA[i + 1]; p < e; ++p) {
-    const int32_t j = a.colA[p];
-    float w = a.valA ? a.valA[p] : 1.f;
-    if (a.csA) w *= a.csA[j];
-    const float4 x = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g);
-    acc.x = fmaf(w, x.x, acc.x);
-    acc.y = fmaf(w, x.y, acc.y);
-    acc.z = fmaf(w, x.z, acc.z);
-    acc.w = fmaf(w, x.w, acc.w);
+  {
+    // four entries per step: independent index/row loads in flight, the FMAs
+    // applied in entry order (same result as one entry per step)
+    int64_t p = a.ptrA[i];
+    const int64_t e = a.ptrA[i + 1];
+    for (; p + 4 <= e; p += 4) {
+      int32_t j[4];
+      float w[4];
+      float4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = a.colA[p + u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        w[u] = a.valA ? a.valA[p + u] : 1.f;
+        if (a.csA) w[u] *= a.csA[j[u]];
+        x[u] = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j[u] * a.ldA + 4 * g);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) fma4(acc, w[u], x[u]);
+    }
+    for (; p < e; ++p) {
+      const int32_t j = a.colA[p];
+      float w = a.valA ? a.valA[p] : 1.f;
+      if (a.csA) w *= a.csA[j];
+      fma4(acc, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
+    }
   }
   if (a.rsA) {
     const float r = a.rsA[i];
@@ -74,15 +111,20 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
     acc.w *= r;
   }
   if (a.ptrB) {
-    for (int64_t p = a.ptrB[i], e = a.ptrB[i + 1]; p < e; ++p) {
-      const int32_t j = a.colB[p];
-      const float w = a.valB[p];
-      const float4 x = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j * a.ldB + 4 * g);
-      acc.x = fmaf(w, x.x, acc.x);
-      acc.y = fmaf(w, x.y, acc.y);
-      acc.z = fmaf(w, x.z, acc.z);
-      acc.w = fmaf(w, x.w, acc.w);
+    int64_t p = a.ptrB[i];
+    const int64_t e = a.ptrB[i + 1];
+    for (; p + 4 <= e; p += 4) {
+      int32_t j[4];
+      float4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = a.colB[p + u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j[u] * a.ldB + 4 * g);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) fma4(acc, a.valB[p + u], x[u]);
     }
+    for (; p < e; ++p)
+      fma4(acc, a.valB[p], *reinterpret_cast<const float4*>(a.srcB + (int64_t)a.colB[p] * a.ldB + 4 * g));
   }
   acc.x *= a.coef;
   acc.y *= a.coef;
@@ -102,37 +144,148 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
   *reinterpret_cast<float4*>(a.out + i * a.ldo + 4 * g) = acc;
 }
 
-ancka_status spmm(const SpmmArgs& a, cudaStream_t s) {
-  const int nv4 = a.nv4;
-  const int G = nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16;
-  const unsigned grid = grid_for(a.nrows * G, 256);
-  switch (G) {
-    case 1: k_spmm<1><<<grid, 256, 0, s>>>(a); break;
-    case 2: k_spmm<2><<<grid, 256, 0, s>>>(a); break;
-    case 4: k_spmm<4><<<grid, 256, 0, s>>>(a); break;
-    case 8: k_spmm<8><<<grid, 256, 0, s>>>(a); break;
-    default: k_spmm<16><<<grid, 256, 0, s>>>(a); break;
+// Long rows (hubs of skewed degree
+// distributions): one CTA per row, 256/G teams of G lanes split the entries,
+// partial sums combined by a fixed-order tree in shared memory.
+template <int G>
+__global__ void __launch_bounds__(256) k_spmm_long(SpmmArgs a) {
+  constexpr int kTeams = 256 / G;
+  __shared__ float4 redA[kTeams][G];
+  __shared__ float4 redB[kTeams][G];
+  const int team = threadIdx.x / G, g = threadIdx.x % G;
+  const int64_t nl = a.n_long ? *a.n_long : 0;
+  for (int64_t q = blockIdx.x; q < nl; q += gridDim.x) {
+    const int64_t i = a.long_rows[q];
+    float4 accA = make_float4(0.f, 0.f, 0.f, 0.f), accB = accA;
+    if (g < a.nv4) {
+      for (int64_t p = a.ptrA[i] + team, e = a.ptrA[i + 1]; p < e; p += kTeams) {
+        const int32_t j = a.colA[p];
+        float w = a.valA ? a.valA[p] : 1.f;
+        if (a.csA) w *= a.csA[j];
+        fma4(accA, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
+      }
+      if (a.ptrB)
+        for (int64_t p = a.ptrB[i] + team, e = a.ptrB[i + 1]; p < e; p += kTeams)
+          fma4(accB, a.valB[p], *reinterpret_cast<const float4*>(a.srcB + (int64_t)a.colB[p] * a.ldB + 4 * g));
+    }
+    redA[team][g] = accA;
+    redB[team][g] = accB;
+    __syncthreads();
+    for (int half = kTeams / 2; half >= 1; half >>= 1) {
+      if (team < half) {
+        float4 x = redA[team][g], y = redA[team + half][g];
+        redA[team][g] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+        x = redB[team][g];
+        y = redB[team + half][g];
+        redB[team][g] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+      }
+      __syncthreads();
+    }
+    if (team == 0 && g < a.nv4) {
+      float4 acc = redA[0][g];
+      if (a.rsA) {
+        const float r = a.rsA[i];
+        acc.x *= r;
+        acc.y *= r;
+        acc.z *= r;
+        acc.w *= r;
+      }
+      const float4 b = redB[0][g];
+      acc = make_float4((acc.x + b.x) * a.coef, (acc.y + b.y) * a.coef, (acc.z + b.z) * a.coef,
+                        (acc.w + b.w) * a.coef);
+      if (a.oh_col) {
+        const int c = a.oh_col[i];
+        if (c >= 4 * g && c < 4 * g + 4) {
+          const float add = a.oh_coef * (a.oh_scale ? a.oh_scale[c] : 1.f);
+          const int q = c - 4 * g;
+          if (q == 0) acc.x += add;
+          else if (q == 1) acc.y += add;
+          else if (q == 2) acc.z += add;
+          else acc.w += add;
+        }
+      }
+      *reinterpret_cast<float4*>(a.out + i * a.ldo + 4 * g) = acc;
+    }
+    __syncthreads();
   }
+}
+
+__global__ void k_find_long(const int64_t* __restrict__ ptrA, const int64_t* __restrict__ ptrB, int64_t nrows,
+                            int64_t long_min, int32_t* __restrict__ rows, int32_t* __restrict__ count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  const int64_t e = (ptrA[i + 1] - ptrA[i]) + (ptrB ? ptrB[i + 1] - ptrB[i] : 0);
+  if (e > long_min) rows[atomicAdd(count, 1)] = (int32_t)i;
+}
+
+struct LongRows {
+  int32_t* rows = nullptr;
+  int32_t* count = nullptr;
+  int64_t count_host = -1;
+  int64_t min_entries = 0;
+};
+
+// long rows of (ptrA [, ptrB]) (nnz entries in all), listed once per call
+// (list order does not affect the result)
+ancka_status find_long_rows(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, int64_t nrows, int64_t nnz,
+                            LongRows* out, cudaStream_t s) {
+  const int64_t mean = nrows > 0 ? ceil_div(nnz, nrows) : 0;
+  out->min_entries = 4 * mean > kLongRowMin ? 4 * mean : kLongRowMin;
+  ANCKA_TRY(ws.alloc(&out->rows, (size_t)(nrows > 0 ? nrows : 1)));
+  ANCKA_TRY(ws.zeros(&out->count, 1));
+  k_find_long<<<(unsigned)ceil_div(nrows > 0 ? nrows : 1, 256), 256, 0, s>>>(ptrA, ptrB, nrows, out->min_entries,
+                                                                              out->rows, out->count);
   ANCKA_LAUNCHED();
   return ANCKA_OK;
 }
 
+ancka_status spmm(const SpmmArgs& a, cudaStream_t s) {
+  const int nv4 = a.nv4;
+  const int G = nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16;
+  const unsigned grid = grid_for(a.nrows * G, 256);
+  if (!a.long_rows || a.n_long_host < 0) {
+    set_error("internal: SpMM without a long-row list");
+    return ANCKA_ERR_INTERNAL;
+  }
+  // the long-row kernel walks the device-side list; skipped when it is empty
+  const unsigned lgrid = (unsigned)(a.n_long_host < 1216 ? a.n_long_host : 1216);
+  switch (G) {
+    case 1: k_spmm<1><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<1><<<lgrid, 256, 0, s>>>(a); break;
+    case 2: k_spmm<2><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<2><<<lgrid, 256, 0, s>>>(a); break;
+    case 4: k_spmm<4><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<4><<<lgrid, 256, 0, s>>>(a); break;
+    case 8: k_spmm<8><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<8><<<lgrid, 256, 0, s>>>(a); break;
+    default: k_spmm<16><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<16><<<lgrid, 256, 0, s>>>(a); break;
+  }
+  ANCKA_LAUNCHED();
+  if (lgrid) count_launch();
+  return ANCKA_OK;
+}
+
 // ---------------------------------------------------------------------------
-// Gram partials: per CTA, sum over its row chunk of t_r t_r^T (upper triangle)
-// with t_r = Z[r] (or Z[r] Rinv when Rinv is given); 32-row tiles in FP32,
-// tiles accumulated in FP64.
+// Gram partials: per CTA, sum over its row chunk of z_r z_r^T (upper
+// triangle), accumulated in FP32 over the chunk (~256 rows); the partials
+// are summed in FP64 across CTAs.  CholeskyQR2's second pass restores
+// orthogonality lost to rounding in the first Gram.
 // ---------------------------------------------------------------------------
 constexpr int kGramThreads = 256, kGramTile = 32, kGramPairs = 9;  // 9*256 >= 65*66/2
 
+__device__ void chol_inv_block(const double* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
+                               int32_t* __restrict__ status, double* csm);
+
+// Gram partials of Z; the CTA that finishes last (atomic ticket) sums the
+// partials and factors them (chol_inv_block), so one launch does both.
 __global__ void __launch_bounds__(kGramThreads)
-k_gram_partial(const float* __restrict__ Z, int ldz, int64_t n, int w, double* __restrict__ partial) {
+k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, double* __restrict__ partial,
+            unsigned int* __restrict__ ticket, float* __restrict__ Rinv_out, int32_t* __restrict__ status) {
   __shared__ float T[kGramTile][kMaxW + 1];
+  __shared__ unsigned int my_ticket;
+  extern __shared__ double csm[];
   const int64_t per = ceil_div(n, (int64_t)gridDim.x);
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = (r0 + per < n) ? r0 + per : n;
   const int np = w * (w + 1) / 2;
   int pa[kGramPairs], pb[kGramPairs];
-  double accd[kGramPairs];
+  float accf[kGramPairs];
 #pragma unroll
   for (int q = 0; q < kGramPairs; ++q) {
     int p = threadIdx.x + q * kGramThreads;
@@ -143,7 +296,7 @@ k_gram_partial(const float* __restrict__ Z, int ldz, int64_t n, int w, double* _
     }
     pa[q] = a;
     pb[q] = a + p;
-    accd[q] = 0.0;
+    accf[q] = 0.f;
   }
   for (int64_t rb = r0; rb < r1; rb += kGramTile) {
     __syncthreads();
@@ -156,11 +309,11 @@ k_gram_partial(const float* __restrict__ Z, int ldz, int64_t n, int w, double* _
 #pragma unroll
     for (int q = 0; q < kGramPairs; ++q) {
       if (threadIdx.x + q * kGramThreads < np) {
-        float acc = 0.f;
+        float acc = accf[q];
         const int a = pa[q], b = pb[q];
 #pragma unroll 8
         for (int r = 0; r < kGramTile; ++r) acc = fmaf(T[r][a], T[r][b], acc);
-        accd[q] += (double)acc;
+        accf[q] = acc;
       }
     }
   }
@@ -168,31 +321,56 @@ k_gram_partial(const float* __restrict__ Z, int ldz, int64_t n, int w, double* _
   for (int q = 0; q < kGramPairs; ++q) {
     if (threadIdx.x + q * kGramThreads < np) {
       double* P = partial + (int64_t)blockIdx.x * w * w;
-      P[pa[q] * w + pb[q]] = accd[q];
-      P[pb[q] * w + pa[q]] = accd[q];
+      P[pa[q] * w + pb[q]] = (double)accf[q];
+      P[pb[q] * w + pa[q]] = (double)accf[q];
     }
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) my_ticket = atomicAdd(ticket, 1u);
+  __syncthreads();
+  if (my_ticket != gridDim.x - 1) return;
+  __threadfence();
+  chol_inv_block(partial, gridDim.x, w, Rinv_out, status, csm);
+  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
 }
 
-// One CTA: G = sum of partials (fixed order), upper Cholesky G = R^T R in
-// FP64, Rinv = R^-1 (upper), written as FP32.  A non-positive pivot marks the
-// status and is replaced by a tiny one so the run finishes.
-__global__ void __launch_bounds__(256)
-k_chol_inv(const double* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
-           int32_t* __restrict__ status) {
-  extern __shared__ double csm[];  // G, R, X: w*w doubles each
+// One CTA: G = sum of the per-CTA partials (fixed order, FP64), upper
+// Cholesky G = R^T R in FP64, Rinv = R^-1 (upper), written as FP32.  A
+// non-positive pivot marks the status and is replaced by a tiny one so the
+// run finishes.  csm: G, R (w*w doubles each), X (max(w*w, 256) doubles).
+__device__ void chol_inv_block(const double* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
+                               int32_t* __restrict__ status, double* csm) {
   const int ww = w * w;
   double* G = csm;
   double* R = csm + ww;
   double* X = csm + 2 * ww;
-  for (int e = threadIdx.x; e < ww; e += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * ww + e];
-    G[e] = s;
-    R[e] = 0.0;
-    X[e] = 0.0;
+  {
+    // T threads per entry, each summing a strided subset of the CTA partials
+    // with eight loads in flight; subsets and lanes combined in fixed order
+    const int T = max(1, min((int)blockDim.x / ww, 8));
+    for (int e = threadIdx.x; e < ww * T; e += blockDim.x) {
+      const int entry = e / T, sub = e % T;
+      double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      int bb = sub;
+      for (; bb + 7 * T < nblk; bb += 8 * T) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] += __ldcg(partial + (int64_t)(bb + u * T) * ww + entry);
+      }
+      for (; bb < nblk; bb += T) acc[0] += __ldcg(partial + (int64_t)bb * ww + entry);
+      X[e] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ww; e += blockDim.x) {
+      double t = 0.0;
+      for (int sub = 0; sub < T; ++sub) t += X[e * T + sub];
+      G[e] = t;
+      R[e] = 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ww; e += blockDim.x) X[e] = 0.0;
+    __syncthreads();
   }
-  __syncthreads();
   for (int j = 0; j < w; ++j) {
     if (threadIdx.x == 0) {
       double d = G[j * w + j];
@@ -527,6 +705,9 @@ k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_it
         }
         __syncthreads();
       }
+      // every SVD starts from V = I: the stop rule needs an unchanged M to
+      // give a bit-identical objective (a warm start from the previous V
+      // would not)
       const int sweeps = jacobi_svd_f32(A, V, k, kp, &rotated);
       for (int c = threadIdx.x; c < k; c += blockDim.x) {
         float t = 0.f;
@@ -754,6 +935,9 @@ struct Ctx {
   float alpha;
   float* E;       // hypergraph edge buffer (m x max(ld, ldk))
   cudaStream_t s;
+  LongRows lr_walk;   // (topo, knn): Eq. zt node side
+  LongRows lr_edges;  // (edges): hypergraph hyperedge side
+  LongRows lr_topo;   // (topo): InitBCM node side
 };
 
 // Z = P Q (Eq. zt); with oh_labels: Z = coef P Q + oh_coef h(Y)
@@ -785,6 +969,10 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
     e.ldo = ld;
     e.nrows = w.m;
     e.nv4 = ld / 4;
+    e.long_rows = c.lr_edges.rows;
+    e.n_long = c.lr_edges.count;
+    e.n_long_host = c.lr_edges.count_host;
+    e.long_min = c.lr_edges.min_entries;
     ANCKA_TRY(spmm(e, c.s));
     a.ptrA = w.topo.ptr;
     a.colA = w.topo.col;
@@ -799,6 +987,10 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
     a.srcA = Q;
     a.ldA = ld;
   }
+  a.long_rows = c.lr_walk.rows;
+  a.n_long = c.lr_walk.count;
+  a.n_long_host = c.lr_walk.count_host;
+  a.long_min = c.lr_walk.min_entries;
   return spmm(a, c.s);
 }
 
@@ -824,6 +1016,10 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
     e.ldo = c.ldk;
     e.nrows = w.m;
     e.nv4 = c.ldk / 4;
+    e.long_rows = c.lr_edges.rows;
+    e.n_long = c.lr_edges.count;
+    e.n_long_host = c.lr_edges.count_host;
+    e.long_min = c.lr_edges.min_entries;
     ANCKA_TRY(spmm(e, c.s));
     a.ptrA = w.topo.ptr;  // sum_{e ni i} y_e / |e|
     a.colA = w.topo.col;
@@ -837,6 +1033,10 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
     a.srcA = Pi;
     a.ldA = c.ldk;
   }
+  a.long_rows = c.lr_topo.rows;
+  a.n_long = c.lr_topo.count;
+  a.n_long_host = c.lr_topo.count_host;
+  a.long_min = c.lr_topo.min_entries;
   return spmm(a, c.s);
 }
 
@@ -924,24 +1124,20 @@ ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64
   return ANCKA_OK;
 }
 
-// CholeskyQR2: Q = Z R^-1 twice (diag(R) > 0), result in *out
+// CholeskyQR2: Q = Z R^-1 twice (diag(R) > 0), result in Z
 ancka_status cholqr2(Workspace& ws, const Ctx& c, float* Z, float* Q, int w, double* gpart, int gblk,
-                     float* Rinv, int32_t* status) {
+                     unsigned int* ticket, float* Rinv, int32_t* status) {
   cudaStream_t s = c.s;
-  const size_t csmem = (size_t)3 * w * w * sizeof(double);
+  const size_t csmem = (size_t)(2 * w * w + (w * w > 256 ? w * w : 256)) * sizeof(double);
   static bool configured = false;
   if (!configured) {
-    ANCKA_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 65 * 65 * 8));
+    ANCKA_CUDA(cudaFuncSetAttribute(k_gram_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 65 * 65 * 8));
     configured = true;
   }
-  k_gram_partial<<<gblk, kGramThreads, 0, s>>>(Z, c.ld, c.n, w, gpart);
-  ANCKA_LAUNCHED();
-  k_chol_inv<<<1, 256, csmem, s>>>(gpart, gblk, w, Rinv, status);
+  k_gram_chol<<<gblk, kGramThreads, csmem, s>>>(Z, c.ld, c.n, w, gpart, ticket, Rinv, status);
   ANCKA_LAUNCHED();
   ANCKA_TRY(apply_rinv(Z, c.ld, c.n, w, Rinv, Q, s));
-  k_gram_partial<<<gblk, kGramThreads, 0, s>>>(Q, c.ld, c.n, w, gpart);
-  ANCKA_LAUNCHED();
-  k_chol_inv<<<1, 256, csmem, s>>>(gpart, gblk, w, Rinv, status);
+  k_gram_chol<<<gblk, kGramThreads, csmem, s>>>(Q, c.ld, c.n, w, gpart, ticket, Rinv, status);
   ANCKA_LAUNCHED();
   ANCKA_TRY(apply_rinv(Q, c.ld, c.n, w, Rinv, Z, s));
   (void)ws;
@@ -988,7 +1184,21 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   ANCKA_TRY(ws.alloc(&Qt, (size_t)n * ldk));
   ANCKA_TRY(ws.alloc(&Rinv, (size_t)wq * wq));
   if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(ws.alloc(&E, (size_t)(w.m > 0 ? w.m : 1) * (ld > ldk ? ld : ldk)));
-  Ctx c{w, n, k, ld, ldk, cfg.alpha, E, s};
+  Ctx c{w, n, k, ld, ldk, cfg.alpha, E, s, {}, {}, {}};
+  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, w.knn.ptr, n, w.topo.nnz + w.knn.nnz, &c.lr_walk, s));
+  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, n, w.topo.nnz, &c.lr_topo, s));
+  if (w.kind == ANCKA_HYPERGRAPH)
+    ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, &c.lr_edges, s));
+  {
+    int32_t h[3] = {0, 0, 0};
+    ANCKA_CUDA(cudaMemcpyAsync(&h[0], c.lr_walk.count, 4, cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&h[1], c.lr_topo.count, 4, cudaMemcpyDeviceToHost, s));
+    if (c.lr_edges.count) ANCKA_CUDA(cudaMemcpyAsync(&h[2], c.lr_edges.count, 4, cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    c.lr_walk.count_host = h[0];
+    c.lr_topo.count_host = h[1];
+    c.lr_edges.count_host = h[2];
+  }
   Scratch sc;
   ANCKA_TRY(ws.alloc(&sc.cnt, 64));
   ANCKA_TRY(ws.alloc(&sc.inv, 64));
@@ -997,9 +1207,11 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   sc.tblk = (int)(ceil_div(n, 4096) < 304 ? ceil_div(n, 4096) : 304);
   ANCKA_TRY(ws.alloc(&sc.tpart, (size_t)sc.tblk));
   ANCKA_TRY(ws.alloc(&sc.take, 1));
-  const int gblk = (int)(ceil_div(n, 512) < 304 ? ceil_div(n, 512) : 304);
+  const int gblk = (int)(ceil_div(n, 256) < 608 ? ceil_div(n, 256) : 608);
   double* gpart;
+  unsigned int* gticket;
   ANCKA_TRY(ws.alloc(&gpart, (size_t)gblk * wq * wq));
+  ANCKA_TRY(ws.zeros(&gticket, 1));
   int32_t *y0, *yt, *ybest, *chol_status;
   ANCKA_TRY(ws.alloc(&y0, (size_t)n));
   ANCKA_TRY(ws.alloc(&yt, (size_t)n));
@@ -1064,7 +1276,7 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     {
       PhaseTimer pt(tr, s, 3);
       ANCKA_TRY(apply_walk(c, Q, ld, Z, 1.f, nullptr, nullptr, 0.f));   // Z = P Q
-      ANCKA_TRY(cholqr2(ws, c, Z, Q, wq, gpart, gblk, Rinv, chol_status));  // result in Z
+      ANCKA_TRY(cholqr2(ws, c, Z, Q, wq, gpart, gblk, gticket, Rinv, chol_status));  // result in Z
       float* tt = Q;
       Q = Z;
       Z = tt;
@@ -1135,7 +1347,8 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 size_t discretize_scratch_bytes(int64_t n, int32_t k) {
   const size_t ldk = (size_t)round_up(k, 4);
   return align256((size_t)n * ldk * sizeof(float)) + align256((size_t)kDiscMaxGrid * k * k * sizeof(float)) +
-         align256((size_t)k * k * sizeof(float)) + align256((size_t)k * sizeof(int32_t)) + 256;
+         align256((size_t)k * k * sizeof(float)) +
+         align256((size_t)k * sizeof(int32_t)) + 256;
 }
 
 // Discretize on a caller-provided scratch block of at least

@@ -58,7 +58,19 @@ __device__ __forceinline__ double exact_cos(const float* __restrict__ xi, const 
                                             int d, double n2i, double n2j) {
   const int lane = threadIdx.x & 31;
   float s = 0.f, c = 0.f;
-  for (int t = lane; t < d; t += 32) dot2_step(s, c, xi[t], xj[t]);
+  // eight strided loads per lane in flight before the compensated steps;
+  // padding contributes exact zeros, which leave (s, c) unchanged
+  for (int t0 = lane; t0 < d; t0 += 32 * 8) {
+    float a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + 32 * u;
+      a[u] = t < d ? xi[t] : 0.f;
+      b[u] = t < d ? xj[t] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) dot2_step(s, c, a[u], b[u]);
+  }
   dot2_warp_reduce(s, c);
   if (n2i <= 0.0 || n2j <= 0.0) return 0.0;
   double dot = (double)s + (double)c;
