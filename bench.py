@@ -298,7 +298,7 @@ def main():
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
            "knn_tflops": round(achieved, 2), "labelings_per_s": round(world / (ms / 1e3), 3),
-           "phases_ms": {k: round(info[k], 3) for k in ("ms_knn", "ms_contract", "ms_build", "ms_init", "ms_iter",
+           "phases_ms": {k: round(info[k], 3) for k in ("ms_knn", "ms_contract", "ms_rerank", "ms_build", "ms_init", "ms_iter",
                                                         "ms_disc", "ms_mhc", "ms_total")},
            "knn_candidates": info["knn_candidates"], "knn_fallback_rows": info["knn_fallback_rows"],
            "step_ms": [round(x, 3) for x in durs]}

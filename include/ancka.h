@@ -134,6 +134,7 @@ typedef struct {
   float ms_mhc;                /* all CalMHC calls and the keep-best step */
   float ms_total;
   float ms_contract;           /* the candidate similarity contraction kernel alone */
+  float ms_rerank;             /* exact re-rank, certificate and fallback after the contraction */
 } ancka_info;
 
 /* Fill *p with the defaults above. */

@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
                 ("numeric_flags", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("ms_knn", ctypes.c_float), ("ms_build", ctypes.c_float), ("ms_init", ctypes.c_float),
                 ("ms_iter", ctypes.c_float), ("ms_disc", ctypes.c_float), ("ms_mhc", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("ms_contract", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("ms_contract", ctypes.c_float),
+                ("ms_rerank", ctypes.c_float)]
 
     def to_dict(self) -> dict:
         n = self.n_phi
@@ -61,7 +62,7 @@ class Info(ctypes.Structure):
                     taken=list(self.taken[:n]), phi_best=self.phi_best, numeric_flags=self.numeric_flags,
                     ms_knn=self.ms_knn, ms_build=self.ms_build, ms_init=self.ms_init, ms_iter=self.ms_iter,
                     ms_disc=self.ms_disc, ms_mhc=self.ms_mhc, ms_total=self.ms_total,
-                    ms_contract=self.ms_contract)
+                    ms_contract=self.ms_contract, ms_rerank=self.ms_rerank)
 
 
 class AnckaError(RuntimeError):

@@ -186,6 +186,7 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
       int32_t* terr;
       ANCKA_TRY(ws.zeros(&terr, 1));
       ANCKA_TRY(knn_candidates_bf16(pr, n, cv, ci, terr, s));
+      if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
       int32_t hterr = 0;
       ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       ANCKA_CUDA(cudaStreamSynchronize(s));
@@ -198,15 +199,16 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
       acc = (float)((pr.dp / 16 + 2) * 2.384185791015625e-07);  // 2^-22 per step
     } else {
       ANCKA_TRY(knn_candidates_fp32(pr, n, cv, ci, s));
+      if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
       // sequential FMA accumulation over dp terms: gamma_dp with u = 2^-24
       const double g = pr.dp * 5.960464477539063e-08;
       acc = (float)(1.01 * g / (1.0 - g));
     }
-    if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
     // the tensor-core kernel leaves two 16-entry lists per row (one per half
     // of the key columns), the CUDA-core kernel one 32-entry list
     ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, acc, cv, ci, prec == ANCKA_PREC_BF16 ? 2 : 1, prec, idx, sim, ncand,
                          nfb, nex, counts, s));
+    if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[2], s));
   } else {
     ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, 0.f, nullptr, nullptr, 1, ANCKA_PREC_FP32, idx, sim, ncand, nfb, nex,
                          counts, s));
@@ -260,13 +262,14 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
   Timer timer;
   Timer* tp = info ? &timer : nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
-  cudaEvent_t cev[2] = {nullptr, nullptr};
+  cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
   bool contract_timed = false;
   if (info) {
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
     cudaEventCreate(&cev[0]);
     cudaEventCreate(&cev[1]);
+    cudaEventCreate(&cev[2]);
     cudaEventRecord(t0, s);
   }
   ancka_status st = ANCKA_OK;
@@ -363,11 +366,14 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     float mc = 0.f;
     if (contract_timed && st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess)
       info->ms_contract = mc;
+    if (contract_timed && st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[1], cev[2]) == cudaSuccess)
+      info->ms_rerank = mc;
     cudaGetLastError();  // an event of a failed call may never have been recorded
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     cudaEventDestroy(cev[0]);
     cudaEventDestroy(cev[1]);
+    cudaEventDestroy(cev[2]);
   }
   if (st == ANCKA_OK) {
     cudaError_t e = cudaGetLastError();
@@ -435,11 +441,12 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
   }
   ancka_status st;
   int64_t nc = 0, nf = 0, ne = 0;
-  cudaEvent_t cev[2] = {nullptr, nullptr};
+  cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
   const bool timed = info && K <= max_candidate_K(prec);
   if (timed) {
     cudaEventCreate(&cev[0]);
     cudaEventCreate(&cev[1]);
+    cudaEventCreate(&cev[2]);
   }
   {
     Workspace ws(s);
@@ -460,9 +467,11 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
     if (timed) {
       float mc = 0.f;
       if (st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;
+      if (st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[1], cev[2]) == cudaSuccess) info->ms_rerank = mc;
       cudaGetLastError();
       cudaEventDestroy(cev[0]);
       cudaEventDestroy(cev[1]);
+      cudaEventDestroy(cev[2]);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);

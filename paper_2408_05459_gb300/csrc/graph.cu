@@ -209,6 +209,8 @@ __global__ void k_knn_len(const int32_t* __restrict__ in_cnt, int64_t n, int K,
 }
 
 // row i: K out-entries, then in-entries; A_K values, D_K, beta_i, P values.
+// One warp per row: lanes take the entries round-robin, D_K is a fixed-order
+// butterfly sum, and each lane rescales the entries it wrote.
 __global__ void k_knn_fill(const int32_t* __restrict__ idx, const float* __restrict__ sim,
                            const uint8_t* __restrict__ mutual, const uint64_t* __restrict__ skeys,
                            const int64_t* __restrict__ in_start, const int32_t* __restrict__ in_cnt,
@@ -216,21 +218,22 @@ __global__ void k_knn_fill(const int32_t* __restrict__ idx, const float* __restr
                            int32_t* __restrict__ col, float* __restrict__ val,
                            const int32_t* __restrict__ zero_row, const int32_t* __restrict__ degree,
                            float beta, float* __restrict__ beta_out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t o = ptr[i];
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;  // uniform over the warp
+  const int64_t o = ptr[i];
   double D = 0.0;
-  for (int p = 0; p < K; ++p) {
-    int64_t q = i * K + p;
-    float a = mutual[q] ? 2.f * sim[q] : sim[q];
+  for (int p = lane; p < K; p += 32) {
+    const int64_t q = i * K + p;
+    const float a = mutual[q] ? 2.f * sim[q] : sim[q];
     col[o + p] = idx[q];
     val[o + p] = a;
     D += a;
   }
-  int64_t b = in_start[i];
-  int32_t c = in_cnt[i];
-  for (int32_t t = 0; t < c; ++t) {
-    int32_t src = (int32_t)(skeys[b + t] & kLowMask);
+  const int64_t b = in_start[i];
+  const int32_t c = in_cnt[i];
+  for (int32_t t = lane; t < c; t += 32) {
+    const int32_t src = (int32_t)(skeys[b + t] & kLowMask);
     float f = 0.f;
     for (int p = 0; p < K; ++p)
       if (idx[(int64_t)src * K + p] == (int32_t)i) f = sim[(int64_t)src * K + p];
@@ -238,12 +241,15 @@ __global__ void k_knn_fill(const int32_t* __restrict__ idx, const float* __restr
     val[o + K + t] = f;
     D += f;
   }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) D += __shfl_xor_sync(0xffffffffu, D, off);
   // Eq. beta_i, then reading R3 (a non-positive KNN degree disables the KNN walk)
   float bi = zero_row[i] ? 0.f : (degree[i] == 0 ? 1.f : beta);
   if (!(D > 0.0)) bi = 0.f;
-  beta_out[i] = bi;
-  float scale = D > 0.0 ? (float)((double)bi / D) : 0.f;
-  for (int64_t p = o; p < o + K + c; ++p) val[p] *= scale;
+  if (lane == 0) beta_out[i] = bi;
+  const float scale = D > 0.0 ? (float)((double)bi / D) : 0.f;
+  for (int p = lane; p < K; p += 32) val[o + p] *= scale;
+  for (int32_t t = lane; t < c; t += 32) val[o + K + t] *= scale;
 }
 
 __global__ void k_topo_rowscale(const float* __restrict__ beta, const float* __restrict__ inv_deg,
@@ -426,7 +432,7 @@ ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* 
   ANCKA_TRY(ws.alloc(&c.col, (size_t)tot));
   ANCKA_TRY(ws.alloc(&c.val, (size_t)tot));
   ANCKA_TRY(ws.alloc(&w->beta, (size_t)n));
-  k_knn_fill<<<grid_for(n, 128), 128, 0, s>>>(idx, sim, mutual, skeys, in_start, in_cnt, n, K, c.ptr,
+  k_knn_fill<<<grid_for(n * 32, 256), 256, 0, s>>>(idx, sim, mutual, skeys, in_start, in_cnt, n, K, c.ptr,
                                               c.col, c.val, zero_row, w->degree, beta, w->beta);
   ANCKA_LAUNCHED();
   ANCKA_TRY(ws.alloc(&w->rs_topo, (size_t)n));

@@ -262,113 +262,173 @@ ancka_status spmm(const SpmmArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Gram partials: per CTA, sum over its row chunk of z_r z_r^T (upper
-// triangle), accumulated in FP32 over the chunk (~256 rows); the partials
-// are summed in FP64 across CTAs.  CholeskyQR2's second pass restores
-// orthogonality lost to rounding in the first Gram.
+// Gram matrix of the n x w block Z, then its Cholesky inverse.
+// Each CTA stages 128-row tiles of Z in shared memory; a thread owns a 4 x 4
+// block of Gram entries and a subset of the tile's rows, sums them in FP32
+// within the tile and carries the running total as a float-float pair
+// (hi + lo, compensated), so accuracy does not degrade with n.  The CTA's
+// subsets are combined in a fixed order into the packed upper triangle.
+// CholeskyQR2's second pass restores orthogonality lost to rounding in the
+// first Gram.
 // ---------------------------------------------------------------------------
-constexpr int kGramThreads = 256, kGramTile = 32, kGramPairs = 9;  // 9*256 >= 65*66/2
+constexpr int kGramThreads = 256, kGramRows = 128, kGramLd = kMaxW;
 
-__device__ void chol_inv_block(const double* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
-                               int32_t* __restrict__ status, double* csm);
+__device__ __forceinline__ int tri_index(int a, int b, int w) { return a * w - a * (a - 1) / 2 + (b - a); }
+
+// (hi, lo) += (bh, bl): float-float addition (TwoSum, then renormalise)
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// block pair index q -> (A, B), A <= B < nb
+__device__ __forceinline__ void block_pair(int q, int nb, int& A, int& B) {
+  A = 0;
+  while (q >= nb - A) {
+    q -= nb - A;
+    ++A;
+  }
+  B = A + q;
+}
+
+__device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
+                               int32_t* __restrict__ status, double* csm, float2* scratch);
 
 // Gram partials of Z; the CTA that finishes last (atomic ticket) sums the
 // partials and factors them (chol_inv_block), so one launch does both.
 __global__ void __launch_bounds__(kGramThreads)
-k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, double* __restrict__ partial,
+k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, float2* __restrict__ partial,
             unsigned int* __restrict__ ticket, float* __restrict__ Rinv_out, int32_t* __restrict__ status) {
-  __shared__ float T[kGramTile][kMaxW + 1];
+  __shared__ __align__(16) float T[kGramRows * kGramLd];
   __shared__ unsigned int my_ticket;
   extern __shared__ double csm[];
   const int64_t per = ceil_div(n, (int64_t)gridDim.x);
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = (r0 + per < n) ? r0 + per : n;
-  const int np = w * (w + 1) / 2;
-  int pa[kGramPairs], pb[kGramPairs];
-  float accf[kGramPairs];
+  const int nb = (w + 3) / 4, nbp = nb * (nb + 1) / 2;
+  const int S = max(1, kGramThreads / nbp);
+  const int t = threadIdx.x;
+  const bool active = t < nbp * S;
+  const int bp = active ? t % nbp : 0, sub = active ? t / nbp : 0;
+  int A, B;
+  block_pair(bp, nb, A, B);
+  float hi[16], lo[16];
 #pragma unroll
-  for (int q = 0; q < kGramPairs; ++q) {
-    int p = threadIdx.x + q * kGramThreads;
-    int a = 0;
-    while (p >= w - a && a < w) {
-      p -= w - a;
-      ++a;
-    }
-    pa[q] = a;
-    pb[q] = a + p;
-    accf[q] = 0.f;
-  }
-  for (int64_t rb = r0; rb < r1; rb += kGramTile) {
+  for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
+  for (int64_t rb = r0; rb < r1; rb += kGramRows) {
+    const int rows = (int)((r1 - rb) < kGramRows ? (r1 - rb) : kGramRows);
     __syncthreads();
-    for (int e = threadIdx.x; e < kGramTile * w; e += kGramThreads) {
-      const int r = e / w, c = e % w;
-      const int64_t row = rb + r;
-      T[r][c] = row < r1 ? Z[row * ldz + c] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kGramPairs; ++q) {
-      if (threadIdx.x + q * kGramThreads < np) {
-        float acc = accf[q];
-        const int a = pa[q], b = pb[q];
-#pragma unroll 8
-        for (int r = 0; r < kGramTile; ++r) acc = fmaf(T[r][a], T[r][b], acc);
-        accf[q] = acc;
+    for (int e = t; e < kGramRows * nb; e += kGramThreads) {
+      const int r = e / nb, c = 4 * (e % nb);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) {
+        v = *reinterpret_cast<const float4*>(Z + (rb + r) * ldz + c);
+        if (c + 1 >= w) v.y = 0.f;  // columns >= w read as zero
+        if (c + 2 >= w) v.z = 0.f;
+        if (c + 3 >= w) v.w = 0.f;
       }
+      *reinterpret_cast<float4*>(&T[r * kGramLd + c]) = v;
+    }
+    __syncthreads();
+    if (active) {
+      float acc[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+      for (int r = sub; r < rows; r += S) {
+        const float4 xa = *reinterpret_cast<const float4*>(&T[r * kGramLd + 4 * A]);
+        const float4 xb = *reinterpret_cast<const float4*>(&T[r * kGramLd + 4 * B]);
+        const float a4[4] = {xa.x, xa.y, xa.z, xa.w}, b4[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i * 4 + j] = fmaf(a4[i], b4[j], acc[i * 4 + j]);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) ff_add(hi[e], lo[e], acc[e], 0.f);
     }
   }
+  __syncthreads();
+  float2* red = reinterpret_cast<float2*>(T);  // nbp * 16 * S <= 4096 pairs
+  if (active) {
 #pragma unroll
-  for (int q = 0; q < kGramPairs; ++q) {
-    if (threadIdx.x + q * kGramThreads < np) {
-      double* P = partial + (int64_t)blockIdx.x * w * w;
-      P[pa[q] * w + pb[q]] = (double)accf[q];
-      P[pb[q] * w + pa[q]] = (double)accf[q];
+    for (int e = 0; e < 16; ++e) red[(bp * 16 + e) * S + sub] = make_float2(hi[e], lo[e]);
+  }
+  __syncthreads();
+  const int np = w * (w + 1) / 2;
+  for (int e = t; e < nbp * 16; e += kGramThreads) {
+    int Aq, Bq;
+    block_pair(e / 16, nb, Aq, Bq);
+    const int a = 4 * Aq + (e % 16) / 4, b = 4 * Bq + (e % 4);
+    if (a >= w || b >= w || a > b) continue;
+    float h = 0.f, l = 0.f;
+    for (int q = 0; q < S; ++q) {
+      const float2 v = red[e * S + q];
+      ff_add(h, l, v.x, v.y);
     }
+    partial[(int64_t)blockIdx.x * np + tri_index(a, b, w)] = make_float2(h, l);
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) my_ticket = atomicAdd(ticket, 1u);
+  if (t == 0) my_ticket = atomicAdd(ticket, 1u);
   __syncthreads();
   if (my_ticket != gridDim.x - 1) return;
   __threadfence();
-  chol_inv_block(partial, gridDim.x, w, Rinv_out, status, csm);
-  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
+  chol_inv_block(partial, gridDim.x, w, Rinv_out, status, csm, reinterpret_cast<float2*>(T));
+  if (t == 0) *ticket = 0u;  // ready for the next launch
 }
 
-// One CTA: G = sum of the per-CTA partials (fixed order, FP64), upper
-// Cholesky G = R^T R in FP64, Rinv = R^-1 (upper), written as FP32.  A
-// non-positive pivot marks the status and is replaced by a tiny one so the
-// run finishes.  csm: G, R (w*w doubles each), X (max(w*w, 256) doubles).
-__device__ void chol_inv_block(const double* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
-                               int32_t* __restrict__ status, double* csm) {
-  const int ww = w * w;
+// One CTA: G = sum of the per-CTA partials (float-float, fixed order, then
+// FP64), upper Cholesky G = R^T R in FP64, Rinv = R^-1 (upper), written as
+// FP32.  A non-positive pivot marks the status and is replaced by a tiny one
+// so the run finishes.  csm: G, R, X (w*w doubles each); scratch: up to
+// max(w(w+1)/2, 256) float pairs.
+__device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
+                               int32_t* __restrict__ status, double* csm, float2* scratch) {
+  const int ww = w * w, np = w * (w + 1) / 2;
   double* G = csm;
   double* R = csm + ww;
   double* X = csm + 2 * ww;
   {
-    // T threads per entry, each summing a strided subset of the CTA partials
-    // with eight loads in flight; subsets and lanes combined in fixed order
-    const int T = max(1, min((int)blockDim.x / ww, 8));
-    for (int e = threadIdx.x; e < ww * T; e += blockDim.x) {
-      const int entry = e / T, sub = e % T;
-      double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // Tn threads per entry, each summing a strided subset of the CTA
+    // partials with four loads in flight; subsets combined in fixed order
+    const int Tn = max(1, min((int)blockDim.x / np, 16));
+    for (int e = threadIdx.x; e < np * Tn; e += blockDim.x) {
+      const int entry = e / Tn, sub = e % Tn;
+      float h = 0.f, l = 0.f;
       int bb = sub;
-      for (; bb + 7 * T < nblk; bb += 8 * T) {
+      for (; bb + 3 * Tn < nblk; bb += 4 * Tn) {
+        float2 v[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] += __ldcg(partial + (int64_t)(bb + u * T) * ww + entry);
+        for (int u = 0; u < 4; ++u) v[u] = __ldcg(partial + (int64_t)(bb + u * Tn) * np + entry);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ff_add(h, l, v[u].x, v[u].y);
       }
-      for (; bb < nblk; bb += T) acc[0] += __ldcg(partial + (int64_t)bb * ww + entry);
-      X[e] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+      for (; bb < nblk; bb += Tn) {
+        const float2 v = __ldcg(partial + (int64_t)bb * np + entry);
+        ff_add(h, l, v.x, v.y);
+      }
+      scratch[e] = make_float2(h, l);
     }
-    __syncthreads();
     for (int e = threadIdx.x; e < ww; e += blockDim.x) {
-      double t = 0.0;
-      for (int sub = 0; sub < T; ++sub) t += X[e * T + sub];
-      G[e] = t;
       R[e] = 0.0;
+      X[e] = 0.0;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < ww; e += blockDim.x) X[e] = 0.0;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      float h = 0.f, l = 0.f;
+      for (int sub = 0; sub < Tn; ++sub) ff_add(h, l, scratch[e * Tn + sub].x, scratch[e * Tn + sub].y);
+      int a = 0, q = e;
+      while (q >= w - a) {
+        q -= w - a;
+        ++a;
+      }
+      const double g = (double)h + (double)l;
+      G[a * w + a + q] = g;
+      G[(a + q) * w + a] = g;
+    }
     __syncthreads();
   }
   for (int j = 0; j < w; ++j) {
@@ -450,20 +510,28 @@ ancka_status apply_rinv(const float* Z, int ld, int64_t n, int w, const float* R
 }
 
 // ---------------------------------------------------------------------------
-// Discretize
+// Discretize (Def. 2, Alg. 5)
 // ---------------------------------------------------------------------------
 struct DiscState {
-  float* Rf;            // k x k FP32 R, written by CTA 0, read by every CTA
-  int32_t* counts;      // k: cluster sizes of the current Y
-  double* obj_prev;     // 1
-  int32_t* done;        // 1
-  float* partial;       // kDiscMaxGrid x k x k per-CTA sums
+  float* part;          // kDiscMaxGrid x k x k: per-CTA sums of Q~ rows per cluster
+  int32_t* partc;       // kDiscMaxGrid x k: per-CTA cluster sizes
+  float2* S;            // k x k: float-float totals of part
+  int32_t* cnt;         // k: cluster sizes of the current Y
   unsigned int* bar;    // 2: grid barrier count and generation
   int32_t* err;         // 1: grid barrier expired
 };
 
 constexpr int kDiscThreads = 512;
 constexpr int kDiscMaxGrid = 320;
+// dynamic shared memory, in floats: a region of 4 x 64 x 65 (the row tile
+// in phase A; M, X, X', P or Jacobi's A and V in phase B), the tile's
+// labels, the slice sums, R with rows padded to a multiple of 16 columns
+constexpr int kDiscLd = 65;
+constexpr int kDiscRegion = 4 * 64 * kDiscLd;
+constexpr int kDiscLabels = 512;
+constexpr int kDiscSlices = 16384;
+constexpr int kDiscR = 64 * 64;
+constexpr int kNsMaxIter = 60;
 
 __global__ void k_rownorm(const float* __restrict__ Q, int ldq, int off, int64_t n, int k,
                           float* __restrict__ Qt, int ldt) {
@@ -476,13 +544,8 @@ __global__ void k_rownorm(const float* __restrict__ Q, int ldq, int off, int64_t
   for (int c = 0; c < ldt; ++c) Qt[i * ldt + c] = c < k ? q[c] * inv : 0.f;
 }
 
-__global__ void k_disc_init(float* Rf, int32_t* counts, double* obj_prev, int32_t* done, unsigned int* bar,
-                            int32_t* err, int k) {
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rf[e] = (e / k == e % k) ? 1.f : 0.f;
-  for (int e = threadIdx.x; e < k; e += blockDim.x) counts[e] = 0;
+__global__ void k_disc_init(unsigned int* bar, int32_t* err) {
   if (threadIdx.x == 0) {
-    *obj_prev = 0.0;
-    *done = 0;
     bar[0] = 0;
     bar[1] = 0;
     *err = 0;
@@ -521,13 +584,17 @@ __device__ bool grid_barrier(unsigned int* bar, int32_t* err) {
   return ok_s != 0;
 }
 
-// One-sided Jacobi SVD (Hestenes) of the k x k matrix in A (row-major, kp
-// columns, kp = k rounded up to even, padding column zero) in FP32: V
-// accumulates the rotations (A V = U Sigma).  Round-robin pair schedule, one
-// warp per pair, lanes over rows.  Returns the number of sweeps.
-__device__ int jacobi_svd_f32(float* A, float* V, int k, int kp, int* rotated) {
+// One-sided Jacobi SVD (Hestenes) of the k x k matrix A in FP32, stored by
+// columns (column stride lda, kp = k rounded up to even columns, a padding
+// column is zero); V (kp x kp, by columns) accumulates the rotations, so
+// A V = U Sigma on return.  Round-robin pair schedule, one warp per pair,
+// lanes over rows (consecutive addresses).  Returns the number of sweeps.
+__device__ int jacobi_svd_f32(float* A, float* V, int k, int kp, int lda, int* rotated) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) V[e] = (e / kp == e % kp) ? 1.f : 0.f;
+  // rotation threshold on |a_p . a_q| / (|a_p| |a_q|): above the rounding
+  // level of a k-term FP32 dot product, so the sweeps end
+  const float tol = fmaxf(1e-6f, 2.f * (float)k * 5.9604645e-8f);
+  for (int e = threadIdx.x; e < kp * lda; e += blockDim.x) V[e] = (e / lda == e % lda) ? 1.f : 0.f;
   __syncthreads();
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
@@ -543,9 +610,11 @@ __device__ int jacobi_svd_f32(float* A, float* V, int k, int kp, int* rotated) {
           p = (r + pr) % (kp - 1);
           q = (r - pr + kp - 1) % (kp - 1);
         }
+        float* ap = A + p * lda;
+        float* aq = A + q * lda;
         float al = 0.f, be = 0.f, ga = 0.f;
         for (int row = lane; row < k; row += 32) {
-          const float x = A[row * kp + p], y = A[row * kp + q];
+          const float x = ap[row], y = aq[row];
           al = fmaf(x, x, al);
           be = fmaf(y, y, be);
           ga = fmaf(x, y, ga);
@@ -553,19 +622,21 @@ __device__ int jacobi_svd_f32(float* A, float* V, int k, int kp, int* rotated) {
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (al > 0.f && be > 0.f && fabsf(ga) > 1e-6f * sqrtf(al * be)) {
+        if (al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
           const float zeta = (be - al) / (2.f * ga);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           const float cs = rsqrtf(1.f + t * t), sn = cs * t;
           for (int row = lane; row < k; row += 32) {
-            const float x = A[row * kp + p], y = A[row * kp + q];
-            A[row * kp + p] = cs * x - sn * y;
-            A[row * kp + q] = sn * x + cs * y;
+            const float x = ap[row], y = aq[row];
+            ap[row] = cs * x - sn * y;
+            aq[row] = sn * x + cs * y;
           }
+          float* vp = V + p * lda;
+          float* vq = V + q * lda;
           for (int row = lane; row < kp; row += 32) {
-            const float x = V[row * kp + p], y = V[row * kp + q];
-            V[row * kp + p] = cs * x - sn * y;
-            V[row * kp + q] = sn * x + cs * y;
+            const float x = vp[row], y = vq[row];
+            vp[row] = cs * x - sn * y;
+            vq[row] = sn * x + cs * y;
           }
           if (lane == 0) *rotated = 1;
         }
@@ -579,204 +650,339 @@ __device__ int jacobi_svd_f32(float* A, float* V, int k, int kp, int* rotated) {
   return sweep;
 }
 
+// R = V U^T from M = U Omega V^T by Jacobi (M row-major in M, stride
+// kDiscLd), with U completed to an orthonormal basis where Omega has zero
+// entries (empty clusters).  A, V, u: scratch.  R goes to Rs (stride ldr).
+// Returns the number of sweeps.
+__device__ int polar_jacobi(const float* M, int k, float* A, float* V, float* u, float* Rs, int ldr, int* rotated) {
+  __shared__ float sig[64];
+  const int kp = (k + 1) & ~1;
+  for (int e = threadIdx.x; e < kp * kDiscLd; e += blockDim.x) {
+    const int c = e / kDiscLd, l = e % kDiscLd;
+    A[e] = (c < k && l < k) ? M[l * kDiscLd + c] : 0.f;
+  }
+  __syncthreads();
+  const int sweeps = jacobi_svd_f32(A, V, k, kp, kDiscLd, rotated);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    float t = 0.f;
+    for (int row = 0; row < k; ++row) t = fmaf(A[c * kDiscLd + row], A[c * kDiscLd + row], t);
+    sig[c] = sqrtf(t);
+  }
+  __syncthreads();
+  float smax = 0.f;
+  for (int c = 0; c < k; ++c) smax = fmaxf(smax, sig[c]);
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int c = e / k, row = e % k;
+    const float sc = sig[c];
+    A[c * kDiscLd + row] = (sc > 1e-6f * smax && sc > 0.f) ? A[c * kDiscLd + row] / sc : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // rank-deficient M: complete U to an orthonormal basis (Gram-Schmidt of
+    // unit vectors, twice, against the columns already set)
+    for (int c = 0; c < k; ++c) {
+      if (sig[c] > 1e-6f * smax && sig[c] > 0.f) continue;
+      for (int cand = 0; cand < k; ++cand) {
+        for (int row = 0; row < k; ++row) u[row] = (row == cand) ? 1.f : 0.f;
+        for (int rep = 0; rep < 2; ++rep)
+          for (int o = 0; o < k; ++o) {
+            if (o == c) continue;
+            float dot = 0.f;
+            for (int row = 0; row < k; ++row) dot = fmaf(A[o * kDiscLd + row], u[row], dot);
+            for (int row = 0; row < k; ++row) u[row] -= dot * A[o * kDiscLd + row];
+          }
+        float nn = 0.f;
+        for (int row = 0; row < k; ++row) nn = fmaf(u[row], u[row], nn);
+        if (nn > 0.25f) {
+          nn = rsqrtf(nn);
+          for (int row = 0; row < k; ++row) A[c * kDiscLd + row] = u[row] * nn;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * ldr; e += blockDim.x) {  // R[a][b] = sum_j V[a][j] U[b][j]
+    const int a = e / ldr, b = e % ldr;
+    float t = 0.f;
+    if (b < k)
+      for (int j = 0; j < k; ++j) t = fmaf(V[j * kDiscLd + a], A[j * kDiscLd + b], t);
+    Rs[e] = t;
+  }
+  __syncthreads();
+  return sweeps;
+}
+
+// R = polar(M)^T by the Newton-Schulz iteration X <- X (3I - X^T X) / 2 from
+// X = M / s, s >= ||M||_2 (min of the Frobenius norm and sqrt(||M||_1
+// ||M||_inf)); every singular value of X then lies in (0, 1] and converges to
+// 1, so X -> U V^T for M = U Omega V^T.  Stops once max |X^T X - I| < tol
+// (after one more step).  Returns false (R untouched) if M is zero or the
+// iteration has not converged after kNsMaxIter steps.
+__device__ bool polar_newton_schulz(const float* M, int k, float* X, float* Xn, float* P, float* Rs, int ldr) {
+  __shared__ float rsum[64], csum[64], f2s[64];
+  __shared__ unsigned int dev_s[3];
+  __shared__ float scale_s;
+  const int kk = k * k;
+  if (threadIdx.x < k) {  // row / column absolute sums and squared row norms
+    float rs = 0.f, cs = 0.f, f2 = 0.f;
+    for (int c = 0; c < k; ++c) {
+      const float x = M[threadIdx.x * kDiscLd + c];
+      rs += fabsf(x);
+      cs += fabsf(M[c * kDiscLd + threadIdx.x]);
+      f2 = fmaf(x, x, f2);
+    }
+    rsum[threadIdx.x] = rs;
+    csum[threadIdx.x] = cs;
+    f2s[threadIdx.x] = f2;
+  }
+  if (threadIdx.x < 3) dev_s[threadIdx.x] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float n1 = 0.f, ninf = 0.f, fro2 = 0.f;
+    for (int l = 0; l < k; ++l) {
+      ninf = fmaxf(ninf, rsum[l]);
+      n1 = fmaxf(n1, csum[l]);
+      fro2 += f2s[l];
+    }
+    const float s = fminf(sqrtf(fro2), sqrtf(n1 * ninf));
+    scale_s = (s > 0.f && isfinite(s)) ? 1.f / s : 0.f;
+  }
+  __syncthreads();
+  const float inv = scale_s;
+  if (inv == 0.f) return false;
+  const float tol = 1e-6f + 8.f * (float)k * 5.9604645e-8f;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    const int r = e / k, c = e % k;
+    X[r * kDiscLd + c] = M[r * kDiscLd + c] * inv;
+  }
+  __syncthreads();
+  bool conv = false;
+  for (int t = 0; t < kNsMaxIter; ++t) {
+    const int slot = t % 3;
+    if (threadIdx.x == 0) dev_s[(t + 1) % 3] = 0u;
+    float dl = 0.f;
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // P = X^T X
+      const int a = e / k, b = e % k;
+      float p = 0.f;
+      for (int r = 0; r < k; ++r) p = fmaf(X[r * kDiscLd + a], X[r * kDiscLd + b], p);
+      P[a * kDiscLd + b] = p;
+      dl = fmaxf(dl, fabsf(p - (a == b ? 1.f : 0.f)));
+    }
+    for (int off = 16; off >= 1; off >>= 1) dl = fmaxf(dl, __shfl_xor_sync(0xffffffffu, dl, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&dev_s[slot], __float_as_uint(dl));  // dl >= 0 (or NaN: never converges)
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // X' = 1.5 X - 0.5 X P
+      const int r = e / k, b = e % k;
+      float s = 0.f;
+      for (int a = 0; a < k; ++a) s = fmaf(X[r * kDiscLd + a], P[a * kDiscLd + b], s);
+      Xn[r * kDiscLd + b] = fmaf(-0.5f, s, 1.5f * X[r * kDiscLd + b]);
+    }
+    __syncthreads();
+    float* tmp = X;
+    X = Xn;
+    Xn = tmp;
+    if (__uint_as_float(dev_s[slot]) < tol) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv) return false;
+  for (int e = threadIdx.x; e < k * ldr; e += blockDim.x) {  // R = X^T
+    const int a = e / ldr, b = e % ldr;
+    Rs[e] = b < k ? X[b * kDiscLd + a] : 0.f;
+  }
+  __syncthreads();
+  return true;
+}
+
 // Discretize (Def. 2, Alg. 5) as one persistent cooperative kernel.  Per
-// iteration: every CTA takes a contiguous row range, sets Y = argmax(Q~ R)
-// (ties to the lowest column), adds its cluster counts and writes its k x k
-// partial sums of Q~ rows per cluster (fixed order); after a grid barrier
-// CTA 0 forms M = Y~^T Q~ (partials summed in FP64), takes the SVD
-// M = U Omega V^T, sets R = V U^T and obj = n - 2 tr(Omega), and decides the
-// stop (|obj - obj_prev| <= 4 eps max(1,|obj|)); a second barrier publishes R.
+// iteration:
+//  A. every CTA takes a contiguous row range in tiles staged in shared
+//     memory, sets Y = argmax(Q~ R) (ties to the lowest column), and sums
+//     its Q~ rows per cluster (fixed order) with its cluster sizes;
+//  R. after a grid barrier the CTAs total the per-CTA sums, one warp per
+//     entry (float-float, fixed order);
+//  B. after a second barrier every CTA forms M = Y~^T Q~ (the totals over
+//     the cluster sizes), takes R = V U^T for M = U Omega V^T (Newton-Schulz,
+//     or Jacobi for rank-deficient M) and obj = n - 2 tr(Omega), and stops
+//     once |obj - obj_prev| <= 4 eps max(1, |obj|).  All CTAs compute the
+//     same R and the same decision from the same totals.
 __global__ void __launch_bounds__(kDiscThreads)
 k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_iter, int32_t* __restrict__ labels,
              DiscState st, int32_t* __restrict__ iters_out, int32_t* __restrict__ flags) {
-  extern __shared__ float dsm_f[];
+  extern __shared__ __align__(16) float dsm_f[];
   __shared__ int32_t hist[64];
+  __shared__ int32_t cnt_s[64];
+  __shared__ double trl[64];
   __shared__ int rotated;
+  __shared__ int done_s;
+  const int tid = threadIdx.x;
   const int kk = k * k;
-  const int nsl_cap = 16384 / kk;
-  const int nsl = max(1, min((int)blockDim.x / k, nsl_cap > 0 ? nsl_cap : 1));
-  float* Rs = dsm_f;                 // k x ldt
-  float* sM = dsm_f + 64 * 64;       // nsl x k x k
+  const int nsl = max(1, min((int)blockDim.x / k, kDiscSlices / kk));
+  const int ldr = (k + 15) & ~15;
+  const int lds = ldt + 1;
+  const int TPR = k > 16 ? 2 : 1;          // threads per row in the argmax
+  const int TR = (int)blockDim.x / TPR;    // rows per tile
+  float* region = dsm_f;
+  int32_t* labt = reinterpret_cast<int32_t*>(dsm_f + kDiscRegion);
+  float* sM = dsm_f + kDiscRegion + kDiscLabels;
+  float* Rs = sM + kDiscSlices;
   const int64_t per = ceil_div(n, (int64_t)gridDim.x);
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = (r0 + per < n) ? r0 + per : n;
   const int nv4 = ldt / 4;
-  int G = 1;
-  while (G < nv4) G <<= 1;           // lanes per row (power of two <= 16)
+  for (int e = tid; e < k * ldr; e += blockDim.x) Rs[e] = (e / ldr == e % ldr) ? 1.f : 0.f;  // R = I
+  double obj_prev = 0.0;
   for (int it = 0; it < max_iter; ++it) {
-    // ---------------- phase A: Y = argmax(Q~ R), counts, partial sums -----
-    for (int e = threadIdx.x; e < k * ldt; e += blockDim.x) {
-      const int a = e / ldt, c = e % ldt;
-      Rs[a * ldt + c] = c < k ? __ldcg(st.Rf + a * k + c) : 0.f;
-    }
-    for (int e = threadIdx.x; e < 64; e += blockDim.x) hist[e] = 0;
+    // ---------------- phase A ----------------------------------------------
+    for (int e = tid; e < 64; e += blockDim.x) hist[e] = 0;
+    for (int e = tid; e < nsl * kk; e += blockDim.x) sM[e] = 0.f;
     __syncthreads();
-    const int rows_per_pass = blockDim.x / G;
-    for (int64_t base = r0; base < r1; base += rows_per_pass) {
-      const int64_t i = base + threadIdx.x / G;
-      const int g = threadIdx.x % G;
-      float best = -INFINITY;
-      int bc = 0x7fffffff;
-      if (i < r1 && g < nv4) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float* q = Qt + i * ldt;
-        for (int a = 0; a < k; ++a) {
-          const float qa = q[a];
-          const float4 r = *reinterpret_cast<const float4*>(&Rs[a * ldt + 4 * g]);
-          acc.x = fmaf(qa, r.x, acc.x);
-          acc.y = fmaf(qa, r.y, acc.y);
-          acc.z = fmaf(qa, r.z, acc.z);
-          acc.w = fmaf(qa, r.w, acc.w);
-        }
-        const float v[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const int c = 4 * g + q4;
-          if (c < k && v[q4] > best) {
-            best = v[q4];
-            bc = c;
-          }
+    for (int64_t tb = r0; tb < r1; tb += TR) {
+      const int rows = (int)((r1 - tb) < TR ? (r1 - tb) : TR);
+      {
+        const float4* src = reinterpret_cast<const float4*>(Qt + tb * ldt);
+        for (int e = tid; e < rows * nv4; e += blockDim.x) {
+          const float4 v = src[e];
+          float* d = region + (e / nv4) * lds + 4 * (e % nv4);
+          d[0] = v.x;
+          d[1] = v.y;
+          d[2] = v.z;
+          d[3] = v.w;
         }
       }
-      for (int off = 1; off < G; off <<= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+      __syncthreads();
+      const int r = tid / TPR, h = tid % TPR;
+      float best = -INFINITY;
+      int bc = 0x7fffffff;
+      if (r < rows) {
+        const float* q = region + r * lds;
+        for (int cb = 16 * h; cb < k; cb += 16 * TPR) {
+          float acc[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+          for (int a = 0; a < k; ++a) {
+            const float qa = q[a];
+            const float4* rr = reinterpret_cast<const float4*>(Rs + a * ldr + cb);
+#pragma unroll
+            for (int j4 = 0; j4 < 4; ++j4) {
+              const float4 rv = rr[j4];
+              acc[4 * j4 + 0] = fmaf(qa, rv.x, acc[4 * j4 + 0]);
+              acc[4 * j4 + 1] = fmaf(qa, rv.y, acc[4 * j4 + 1]);
+              acc[4 * j4 + 2] = fmaf(qa, rv.z, acc[4 * j4 + 2]);
+              acc[4 * j4 + 3] = fmaf(qa, rv.w, acc[4 * j4 + 3]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (cb + j < k && acc[j] > best) {
+              best = acc[j];
+              bc = cb + j;
+            }
+        }
+      }
+      if (TPR == 2) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, 1);
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, 1);
         if (ob > best || (ob == best && oc < bc)) {
           best = ob;
           bc = oc;
         }
       }
-      if (i < r1 && g == 0) {
+      if (r < rows && h == 0) {
         if (bc == 0x7fffffff) bc = 0;
-        labels[i] = bc;
+        labels[tb + r] = bc;
+        labt[r] = bc;
         atomicAdd(&hist[bc], 1);
       }
-    }
-    for (int e = threadIdx.x; e < nsl * kk; e += blockDim.x) sM[e] = 0.f;
-    __syncthreads();
-    for (int e = threadIdx.x; e < k; e += blockDim.x)
-      if (hist[e]) atomicAdd(&st.counts[e], hist[e]);
-    {
-      const int sl = threadIdx.x / k, c = threadIdx.x % k;
-      if (sl < nsl) {
-        const int64_t sper = ceil_div(r1 - r0 > 0 ? r1 - r0 : 0, (int64_t)nsl);
-        const int64_t s0 = r0 + sl * sper;
-        const int64_t s1 = (s0 + sper < r1) ? s0 + sper : r1;
-        float* my = sM + sl * kk;
-        for (int64_t i = s0; i < s1; ++i) my[labels[i] * k + c] += Qt[i * ldt + c];
+      __syncthreads();
+      {
+        const int sl = tid / k, c = tid % k;
+        if (sl < nsl) {
+          const int sper = (rows + nsl - 1) / nsl;
+          const int s0 = sl * sper;
+          const int s1 = (s0 + sper < rows) ? s0 + sper : rows;
+          float* my = sM + sl * kk;
+          for (int t = s0; t < s1; ++t) my[labt[t] * k + c] += region[t * lds + c];
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    for (int e = tid; e < kk; e += blockDim.x) {
       float t = 0.f;
       for (int q = 0; q < nsl; ++q) t += sM[q * kk + e];
-      st.partial[(int64_t)blockIdx.x * kk + e] = t;
+      st.part[(int64_t)blockIdx.x * kk + e] = t;
+    }
+    for (int e = tid; e < k; e += blockDim.x) st.partc[(int64_t)blockIdx.x * k + e] = hist[e];
+    if (!grid_barrier(st.bar, st.err)) return;
+    // ---------------- phase R: totals, one warp per entry ------------------
+    {
+      const int nw = blockDim.x >> 5, wid = tid >> 5, lane = tid & 31;
+      for (int e = blockIdx.x * nw + wid; e < kk + k; e += gridDim.x * nw) {
+        if (e < kk) {
+          float h = 0.f, l = 0.f;
+          for (int b = lane; b < (int)gridDim.x; b += 32) ff_add(h, l, __ldcg(st.part + (int64_t)b * kk + e), 0.f);
+          for (int off = 16; off >= 1; off >>= 1) {  // ff_add is symmetric: every lane ends equal
+            const float oh = __shfl_xor_sync(0xffffffffu, h, off), ol = __shfl_xor_sync(0xffffffffu, l, off);
+            ff_add(h, l, oh, ol);
+          }
+          if (lane == 0) st.S[e] = make_float2(h, l);
+        } else {
+          int c = 0;
+          for (int b = lane; b < (int)gridDim.x; b += 32) c += __ldcg(st.partc + (int64_t)b * k + (e - kk));
+          for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+          if (lane == 0) st.cnt[e - kk] = c;
+        }
+      }
     }
     if (!grid_barrier(st.bar, st.err)) return;
-    // ---------------- phase B (CTA 0): SVD, R, objective, stop -------------
-    if (blockIdx.x == 0) {
-      const int kp = (k + 1) & ~1;
-      float* A = dsm_f;          // k x kp
-      float* V = dsm_f + 64 * 64;  // kp x kp
-      __shared__ float sig[64];
-      __shared__ int32_t cnt_s[64];
-      for (int e = threadIdx.x; e < k; e += blockDim.x) cnt_s[e] = __ldcg(st.counts + e);
-      __syncthreads();
-      // M = (sum over CTAs of the partials) / counts: T threads per entry sum
-      // strided CTA subsets in FP64, combined in a fixed order
-      {
-        double* red = reinterpret_cast<double*>(dsm_f + 2 * 64 * 64);  // up to 4096 doubles
-        const int T = max(1, min((int)blockDim.x / kk, 32));
-        for (int e = threadIdx.x; e < kk * T; e += blockDim.x) {
-          const int entry = e / T, sub = e % T;
-          double t = 0.0;
-          for (int b = sub; b < (int)gridDim.x; b += T) t += (double)__ldcg(st.partial + (int64_t)b * kk + entry);
-          red[e] = t;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < k * kp; e += blockDim.x) {
-          const int l = e / kp, c = e % kp;
-          double t = 0.0;
-          if (c < k) {
-            for (int sub = 0; sub < T; ++sub) t += red[(l * k + c) * T + sub];
-            t = cnt_s[l] > 0 ? t / (double)cnt_s[l] : 0.0;
-          }
-          A[l * kp + c] = (float)t;
-        }
-        __syncthreads();
-      }
-      // every SVD starts from V = I: the stop rule needs an unchanged M to
-      // give a bit-identical objective (a warm start from the previous V
-      // would not)
-      const int sweeps = jacobi_svd_f32(A, V, k, kp, &rotated);
-      for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        float t = 0.f;
-        for (int row = 0; row < k; ++row) t = fmaf(A[row * kp + c], A[row * kp + c], t);
-        sig[c] = sqrtf(t);
-      }
-      __syncthreads();
-      float smax = 0.f;
-      for (int c = 0; c < k; ++c) smax = fmaxf(smax, sig[c]);
-      for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-        const int row = e / k, c = e % k;
-        const float sc = sig[c];
-        A[row * kp + c] = (sc > 1e-6f * smax && sc > 0.f) ? A[row * kp + c] / sc : 0.f;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        // rank-deficient M (empty clusters): complete U to an orthonormal basis
-        for (int c = 0; c < k; ++c) {
-          if (sig[c] > 1e-6f * smax && sig[c] > 0.f) continue;
-          for (int cand = 0; cand < k; ++cand) {
-            float u[64];
-            for (int row = 0; row < k; ++row) u[row] = (row == cand) ? 1.f : 0.f;
-            for (int rep = 0; rep < 2; ++rep)
-              for (int o = 0; o < k; ++o) {
-                if (o == c) continue;
-                float dot = 0.f;
-                for (int row = 0; row < k; ++row) dot = fmaf(A[row * kp + o], u[row], dot);
-                for (int row = 0; row < k; ++row) u[row] -= dot * A[row * kp + o];
-              }
-            float nn = 0.f;
-            for (int row = 0; row < k; ++row) nn = fmaf(u[row], u[row], nn);
-            if (nn > 0.25f) {
-              nn = rsqrtf(nn);
-              for (int row = 0; row < k; ++row) A[row * kp + c] = u[row] * nn;
-              break;
-            }
-          }
-        }
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // R = V U^T
-        const int a = e / k, b = e % k;
-        float t = 0.f;
-        for (int j = 0; j < k; ++j) t = fmaf(V[a * kp + j], A[b * kp + j], t);
-        st.Rf[e] = t;
-      }
-      if (threadIdx.x == 0) {
-        double tr = 0.0;
-        bool empty = false;
-        for (int c = 0; c < k; ++c) {
-          tr += (double)sig[c];
-          empty |= cnt_s[c] == 0;
-        }
-        const double obj = (double)n - 2.0 * tr;
-        int dn = 0;
-        if (it > 0 && fabs(obj - *st.obj_prev) <= 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(obj))) dn = 1;
-        if (it + 1 >= max_iter) dn = 1;
-        *st.obj_prev = obj;
-        *st.done = dn;
+    // ---------------- phase B: every CTA, same result ----------------------
+    float* M = region;
+    for (int e = tid; e < k; e += blockDim.x) cnt_s[e] = __ldcg(st.cnt + e);
+    __syncthreads();
+    for (int e = tid; e < kk; e += blockDim.x) {
+      const int l = e / k, c = e % k;
+      const float2 v = __ldcg(st.S + e);
+      const int cl = cnt_s[l];
+      M[l * kDiscLd + c] = cl > 0 ? (float)(((double)v.x + (double)v.y) / (double)cl) : 0.f;
+    }
+    __syncthreads();
+    bool empty = false;
+    for (int c = 0; c < k; ++c) empty |= cnt_s[c] == 0;
+    int sweeps = 0;
+    bool ok = false;
+    if (!empty) ok = polar_newton_schulz(M, k, region + kDiscLd * 64, region + 2 * kDiscLd * 64,
+                                         region + 3 * kDiscLd * 64, Rs, ldr);
+    if (!ok)
+      sweeps = polar_jacobi(M, k, region + kDiscLd * 64, region + 2 * kDiscLd * 64, region + 3 * kDiscLd * 64, Rs,
+                            ldr, &rotated);
+    // tr(Omega) = tr(M R), rows in FP64, summed in order
+    for (int l = tid; l < k; l += blockDim.x) {
+      double t = 0.0;
+      for (int c = 0; c < k; ++c) t += (double)M[l * kDiscLd + c] * (double)Rs[c * ldr + l];
+      trl[l] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double tr = 0.0;
+      for (int l = 0; l < k; ++l) tr += trl[l];
+      const double obj = (double)n - 2.0 * tr;
+      int dn = 0;
+      if (it > 0 && fabs(obj - obj_prev) <= 4.0 * 2.220446049250313e-16 * fmax(1.0, fabs(obj))) dn = 1;
+      if (it + 1 >= max_iter) dn = 1;
+      obj_prev = obj;
+      done_s = dn;
+      if (blockIdx.x == 0) {
         if (iters_out) *iters_out = it + 1;
         if (flags) {
           if (empty) atomicOr(flags, 1);
           if (sweeps >= 60) atomicOr(flags, 2);
         }
       }
-      for (int e = threadIdx.x; e < k; e += blockDim.x) st.counts[e] = 0;
     }
-    if (!grid_barrier(st.bar, st.err)) return;
-    if (__ldcg(st.done)) break;
+    __syncthreads();
+    if (done_s) break;
   }
 }
 
@@ -1081,22 +1287,21 @@ ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma
 
 ancka_status make_disc_state(Workspace& ws, int64_t n, int k, DiscState* st) {
   (void)n;
-  ANCKA_TRY(ws.alloc(&st->Rf, (size_t)k * k));
-  ANCKA_TRY(ws.alloc(&st->counts, (size_t)k));
-  ANCKA_TRY(ws.alloc(&st->obj_prev, 1));
-  ANCKA_TRY(ws.alloc(&st->done, 1));
-  ANCKA_TRY(ws.alloc(&st->partial, (size_t)kDiscMaxGrid * k * k));
+  ANCKA_TRY(ws.alloc(&st->part, (size_t)kDiscMaxGrid * k * k));
+  ANCKA_TRY(ws.alloc(&st->partc, (size_t)kDiscMaxGrid * k));
+  ANCKA_TRY(ws.alloc(&st->S, (size_t)k * k));
+  ANCKA_TRY(ws.alloc(&st->cnt, (size_t)k));
   ANCKA_TRY(ws.alloc(&st->bar, 2));
   ANCKA_TRY(ws.alloc(&st->err, 1));
   return ANCKA_OK;
 }
 
-size_t disc_smem_bytes() { return (size_t)(64 * 64 + 16384) * sizeof(float); }
+size_t disc_smem_bytes() { return (size_t)(kDiscRegion + kDiscLabels + kDiscSlices + kDiscR) * sizeof(float); }
 
 // Launch Discretize on a row-normalised block (one cooperative launch).
 ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64_t n, int k, int max_iter,
                             int32_t* labels, int32_t* iters_out, int32_t* flags, cudaStream_t s) {
-  k_disc_init<<<1, 256, 0, s>>>(st.Rf, st.counts, st.obj_prev, st.done, st.bar, st.err, k);
+  k_disc_init<<<1, 32, 0, s>>>(st.bar, st.err);
   ANCKA_LAUNCHED();
   const size_t smem = disc_smem_bytes();
   static int max_grid = 0;
@@ -1113,7 +1318,7 @@ ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64
       return ANCKA_ERR_UNSUPPORTED;
     }
   }
-  int grid = (int)ceil_div(n, 2048);
+  int grid = (int)ceil_div(n, 512);
   if (grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
   DiscState stc = st;
@@ -1125,10 +1330,10 @@ ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64
 }
 
 // CholeskyQR2: Q = Z R^-1 twice (diag(R) > 0), result in Z
-ancka_status cholqr2(Workspace& ws, const Ctx& c, float* Z, float* Q, int w, double* gpart, int gblk,
+ancka_status cholqr2(Workspace& ws, const Ctx& c, float* Z, float* Q, int w, float2* gpart, int gblk,
                      unsigned int* ticket, float* Rinv, int32_t* status) {
   cudaStream_t s = c.s;
-  const size_t csmem = (size_t)(2 * w * w + (w * w > 256 ? w * w : 256)) * sizeof(double);
+  const size_t csmem = (size_t)(3 * w * w) * sizeof(double);
   static bool configured = false;
   if (!configured) {
     ANCKA_CUDA(cudaFuncSetAttribute(k_gram_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 65 * 65 * 8));
@@ -1207,10 +1412,10 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   sc.tblk = (int)(ceil_div(n, 4096) < 304 ? ceil_div(n, 4096) : 304);
   ANCKA_TRY(ws.alloc(&sc.tpart, (size_t)sc.tblk));
   ANCKA_TRY(ws.alloc(&sc.take, 1));
-  const int gblk = (int)(ceil_div(n, 256) < 608 ? ceil_div(n, 256) : 608);
-  double* gpart;
+  const int gblk = (int)(ceil_div(n, 512) < 304 ? ceil_div(n, 512) : 304);
+  float2* gpart;
   unsigned int* gticket;
-  ANCKA_TRY(ws.alloc(&gpart, (size_t)gblk * wq * wq));
+  ANCKA_TRY(ws.alloc(&gpart, (size_t)gblk * wq * (wq + 1) / 2));
   ANCKA_TRY(ws.zeros(&gticket, 1));
   int32_t *y0, *yt, *ybest, *chol_status;
   ANCKA_TRY(ws.alloc(&y0, (size_t)n));
@@ -1347,7 +1552,7 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 size_t discretize_scratch_bytes(int64_t n, int32_t k) {
   const size_t ldk = (size_t)round_up(k, 4);
   return align256((size_t)n * ldk * sizeof(float)) + align256((size_t)kDiscMaxGrid * k * k * sizeof(float)) +
-         align256((size_t)k * k * sizeof(float)) +
+         align256((size_t)kDiscMaxGrid * k * sizeof(int32_t)) + align256((size_t)k * k * sizeof(float2)) +
          align256((size_t)k * sizeof(int32_t)) + 256;
 }
 
@@ -1367,17 +1572,17 @@ ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, in
   float* Qt = reinterpret_cast<float*>(p);
   p += align256((size_t)n * ldk * sizeof(float));
   DiscState st;
-  st.partial = reinterpret_cast<float*>(p);
+  st.part = reinterpret_cast<float*>(p);
   p += align256((size_t)kDiscMaxGrid * k * k * sizeof(float));
-  st.Rf = reinterpret_cast<float*>(p);
-  p += align256((size_t)k * k * sizeof(float));
-  st.counts = reinterpret_cast<int32_t*>(p);
+  st.partc = reinterpret_cast<int32_t*>(p);
+  p += align256((size_t)kDiscMaxGrid * k * sizeof(int32_t));
+  st.S = reinterpret_cast<float2*>(p);
+  p += align256((size_t)k * k * sizeof(float2));
+  st.cnt = reinterpret_cast<int32_t*>(p);
   p += align256((size_t)k * sizeof(int32_t));
-  st.obj_prev = reinterpret_cast<double*>(p);
-  st.done = reinterpret_cast<int32_t*>(p + 8);
-  st.bar = reinterpret_cast<unsigned int*>(p + 16);
-  st.err = reinterpret_cast<int32_t*>(p + 24);
-  int32_t* it = reinterpret_cast<int32_t*>(p + 28);
+  st.bar = reinterpret_cast<unsigned int*>(p);
+  st.err = reinterpret_cast<int32_t*>(p + 8);
+  int32_t* it = reinterpret_cast<int32_t*>(p + 12);
   ANCKA_CUDA(cudaMemsetAsync(it, 0, sizeof(int32_t), s));
   k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qk, ldq, 0, n, k, Qt, ldk);
   ANCKA_LAUNCHED();

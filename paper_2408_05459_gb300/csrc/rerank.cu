@@ -31,33 +31,48 @@ __device__ __forceinline__ bool before(double a, int32_t ia, double b, int32_t i
   return a > b || (a == b && ia < ib);
 }
 
+// order-preserving map of a double to an unsigned key (larger value ->
+// larger key; -0 is never produced by cos_from)
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_value(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
 // bitonic sort of one (value, index) pair per lane: lane 0 ends with the
-// first element of the (value desc, index asc) order.
+// first element of the (value desc, index asc) order.  Compares integer keys
+// (the FP64 pipe is narrow on this part).
 __device__ __forceinline__ void warp_sort(double& v, int32_t& j) {
   const int lane = threadIdx.x & 31;
+  unsigned long long key = dkey(v);
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
     for (int s = k >> 1; s > 0; s >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, v, s);
-      int32_t oj = __shfl_xor_sync(0xffffffffu, j, s);
-      bool lower = (lane & s) == 0;
-      bool dir = (lane & k) == 0;
-      bool self_first = before(v, j, ov, oj);
-      bool take = (lower == dir) ? !self_first : self_first;
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, s);
+      const int32_t oj = __shfl_xor_sync(0xffffffffu, j, s);
+      const bool lower = (lane & s) == 0;
+      const bool dir = (lane & k) == 0;
+      const bool self_first = key > ok || (key == ok && j < oj);
+      const bool take = (lower == dir) ? !self_first : self_first;
       if (take) {
-        v = ov;
+        key = ok;
         j = oj;
       }
     }
   }
+  v = dkey_value(key);
 }
 
-// exact cosine of rows i and j with a warp: Dot2 partials, fixed-order merge
-__device__ __forceinline__ double exact_cos(const float* __restrict__ xi, const float* __restrict__ xj,
-                                            int d, double n2i, double n2j) {
+// Dot2 dot product of rows i and j with a warp: (s, c) with s + c the
+// compensated result, the same in every lane (fixed-order merge)
+__device__ __forceinline__ void dot2_rows(const float* __restrict__ xi, const float* __restrict__ xj, int d, float& s,
+                                          float& c) {
   const int lane = threadIdx.x & 31;
-  float s = 0.f, c = 0.f;
+  s = 0.f;
+  c = 0.f;
   // eight strided loads per lane in flight before the compensated steps;
   // padding contributes exact zeros, which leave (s, c) unchanged
   for (int t0 = lane; t0 < d; t0 += 32 * 8) {
@@ -72,14 +87,58 @@ __device__ __forceinline__ double exact_cos(const float* __restrict__ xi, const 
     for (int u = 0; u < 8; ++u) dot2_step(s, c, a[u], b[u]);
   }
   dot2_warp_reduce(s, c);
-  if (n2i <= 0.0 || n2j <= 0.0) return 0.0;
-  double dot = (double)s + (double)c;
-  return dot / (sqrt(n2i) * sqrt(n2j));
+}
+
+// cosine from the compensated dot product and the rows' inverse norms
+// (0 for a zero row), evaluated in double; +0 for a zero result
+__device__ __forceinline__ double cos_from(float s, float c, double ri, double rj) {
+  return ((double)s + (double)c) * ri * rj + 0.0;
+}
+
+// Dot2 dot products of row i with up to four rows j[u] (j[u] < 0: skipped)
+// with one warp: the loads of all four rows are issued before the Dot2
+// steps, and each sees the same per-lane order as dot2_rows.
+__device__ __forceinline__ void dot2_rows4(const float* __restrict__ X, const float* __restrict__ xi, int d,
+                                           const int32_t (&j)[4], float (&s)[4], float (&c)[4]) {
+  const int lane = threadIdx.x & 31;
+  const float* xj[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    xj[u] = X + (int64_t)(j[u] >= 0 ? j[u] : 0) * d;
+    s[u] = 0.f;
+    c[u] = 0.f;
+  }
+  for (int t0 = lane; t0 < d; t0 += 32 * 8) {
+    float a[8], b[4][8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int t = t0 + 32 * v;
+      a[v] = t < d ? xi[t] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const int t = t0 + 32 * v;
+        b[u][v] = (t < d && j[u] >= 0) ? xj[u][t] : 0.f;
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) dot2_step(s[u], c[u], a[v], b[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) dot2_warp_reduce(s[u], c[u]);
+}
+
+__global__ void k_inv_norms(const double* __restrict__ nrm2, int64_t n, double* __restrict__ rinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rinv[i] = nrm2[i] > 0.0 ? 1.0 / sqrt(nrm2[i]) : 0.0;
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
 k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __restrict__ err,
-         const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ nrm2,
+         const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ rinv,
          const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx, int lists,
          int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ fb_rows,
          float* __restrict__ fb_thr, int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand) {
@@ -138,18 +197,27 @@ k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __re
       unsigned rmask = __ballot_sync(0xffffffffu, inR);
       if (lane == 0) atomicAdd(&block_cand, (unsigned)__popc(rmask));
       const float* xi = X + i * (int64_t)d;
-      const double n2i = nrm2[i];
+      const double ri = rinv[i];
       double myv = -INFINITY;
       int32_t myj = INT32_MAX;
-      while (rmask) {
-        const int t = __ffs(rmask) - 1;
-        rmask &= rmask - 1;
-        const int32_t jt = __shfl_sync(0xffffffffu, j, t);
-        const double cs = exact_cos(xi, X + (int64_t)jt * d, d, n2i, nrm2[jt]);
-        if (lane == t) {
-          myv = cs;
-          myj = jt;
+      while (rmask) {  // four candidates per pass
+        int tl[4];
+        int32_t jt[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          tl[u] = rmask ? __ffs(rmask) - 1 : -1;
+          if (rmask) rmask &= rmask - 1;
+          jt[u] = __shfl_sync(0xffffffffu, j, tl[u] >= 0 ? tl[u] : 0);
+          if (tl[u] < 0) jt[u] = -1;
         }
+        float ds[4], dc[4];
+        dot2_rows4(X, xi, d, jt, ds, dc);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (lane == tl[u]) {  // the owner lane alone evaluates its cosine
+            myv = cos_from(ds[u], dc[u], ri, rinv[jt[u]]);
+            myj = jt[u];
+          }
       }
       warp_sort(myv, myj);
       if (lane < K) {
@@ -172,7 +240,7 @@ constexpr int kSlices = 64;           // key slices per flagged row
 constexpr int kSlicedMaxRows = 1024;  // flagged rows handled by the sliced kernels
 
 __global__ void __launch_bounds__(kExWarps * 32)
-k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const double* __restrict__ nrm2,
+k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const double* __restrict__ rinv,
                  const int32_t* __restrict__ rows, const int32_t* __restrict__ row_count,
                  int64_t all_rows, int32_t* __restrict__ out_idx, float* __restrict__ out_sim) {
   __shared__ double lv[kExWarps][kMaxK];
@@ -189,19 +257,23 @@ k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const dou
     }
     __syncthreads();
     const float* xi = X + i * (int64_t)d;
-    const double n2i = nrm2[i];
+    const double ri = rinv[i];
     for (int64_t j = w; j < n; j += kExWarps) {
       if (j == i) continue;
-      const double cs = exact_cos(xi, X + j * (int64_t)d, d, n2i, nrm2[j]);
-      if (lane == 0 && before(cs, (int32_t)j, lv[w][K - 1], li[w][K - 1])) {
-        int p = K - 1;
-        while (p > 0 && before(cs, (int32_t)j, lv[w][p - 1], li[w][p - 1])) {
-          lv[w][p] = lv[w][p - 1];
-          li[w][p] = li[w][p - 1];
-          --p;
+      float ds, dc;
+      dot2_rows(xi, X + j * (int64_t)d, d, ds, dc);
+      if (lane == 0) {
+        const double cs = cos_from(ds, dc, ri, rinv[j]);
+        if (before(cs, (int32_t)j, lv[w][K - 1], li[w][K - 1])) {
+          int p = K - 1;
+          while (p > 0 && before(cs, (int32_t)j, lv[w][p - 1], li[w][p - 1])) {
+            lv[w][p] = lv[w][p - 1];
+            li[w][p] = li[w][p - 1];
+            --p;
+          }
+          lv[w][p] = cs;
+          li[w][p] = (int32_t)j;
         }
-        lv[w][p] = cs;
-        li[w][p] = (int32_t)j;
       }
       __syncwarp();
     }
@@ -230,7 +302,7 @@ k_knn_exhaustive(const float* __restrict__ X, int64_t n, int d, int K, const dou
 // A row whose buffer overflowed (or holds fewer than K keys) goes to the
 // exhaustive kernels.
 __global__ void __launch_bounds__(kWarps * 32)
-k_rerank_collected(const float* __restrict__ X, int d, int K, const double* __restrict__ nrm2,
+k_rerank_collected(const float* __restrict__ X, int d, int K, const double* __restrict__ rinv,
                    const int32_t* __restrict__ rows, const int32_t* __restrict__ n_rows_p,
                    const int32_t* __restrict__ cnt, const int32_t* __restrict__ buf, int cap,
                    int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ ov_rows,
@@ -245,7 +317,7 @@ k_rerank_collected(const float* __restrict__ X, int d, int K, const double* __re
     return;
   }
   const float* xi = X + i * (int64_t)d;
-  const double n2i = nrm2[i];
+  const double ri = rinv[i];
   double tv = -INFINITY;
   int32_t tj = INT32_MAX;
   for (int q0 = 0; q0 < c; q0 += 32) {
@@ -255,9 +327,10 @@ k_rerank_collected(const float* __restrict__ X, int d, int K, const double* __re
     const int nb = min(32, c - q0);
     for (int t = 0; t < nb; ++t) {
       const int32_t jt = __shfl_sync(0xffffffffu, mine, t);
-      const double cs = exact_cos(xi, X + (int64_t)jt * d, d, n2i, nrm2[jt]);
+      float ds, dc;
+      dot2_rows(xi, X + (int64_t)jt * d, d, ds, dc);
       if (lane == t) {
-        nv = cs;
+        nv = cos_from(ds, dc, ri, rinv[jt]);
         nj = jt;
       }
     }
@@ -281,7 +354,7 @@ k_rerank_collected(const float* __restrict__ X, int d, int K, const double* __re
 // separate CTAs (the whole GPU streams X once per row instead of one SM);
 // every CTA writes the exact top-K of its slice, k_exh_merge combines them.
 __global__ void __launch_bounds__(kExWarps * 32)
-k_exh_sliced(const float* __restrict__ X, int64_t n, int d, int K, const double* __restrict__ nrm2,
+k_exh_sliced(const float* __restrict__ X, int64_t n, int d, int K, const double* __restrict__ rinv,
              const int32_t* __restrict__ rows, const int32_t* __restrict__ row_count, double* __restrict__ pv,
              int32_t* __restrict__ pi) {
   __shared__ double lv[kExWarps][kMaxK];
@@ -301,19 +374,23 @@ k_exh_sliced(const float* __restrict__ X, int64_t n, int d, int K, const double*
     }
     __syncthreads();
     const float* xi = X + i * (int64_t)d;
-    const double n2i = nrm2[i];
+    const double ri = rinv[i];
     for (int64_t j = j0 + w; j < j1; j += kExWarps) {
       if (j == i) continue;
-      const double cs = exact_cos(xi, X + j * (int64_t)d, d, n2i, nrm2[j]);
-      if (lane == 0 && before(cs, (int32_t)j, lv[w][K - 1], li[w][K - 1])) {
-        int p = K - 1;
-        while (p > 0 && before(cs, (int32_t)j, lv[w][p - 1], li[w][p - 1])) {
-          lv[w][p] = lv[w][p - 1];
-          li[w][p] = li[w][p - 1];
-          --p;
+      float ds, dc;
+      dot2_rows(xi, X + j * (int64_t)d, d, ds, dc);
+      if (lane == 0) {
+        const double cs = cos_from(ds, dc, ri, rinv[j]);
+        if (before(cs, (int32_t)j, lv[w][K - 1], li[w][K - 1])) {
+          int p = K - 1;
+          while (p > 0 && before(cs, (int32_t)j, lv[w][p - 1], li[w][p - 1])) {
+            lv[w][p] = lv[w][p - 1];
+            li[w][p] = li[w][p - 1];
+            --p;
+          }
+          lv[w][p] = cs;
+          li[w][p] = (int32_t)j;
         }
-        lv[w][p] = cs;
-        li[w][p] = (int32_t)j;
       }
       __syncwarp();
     }
@@ -368,6 +445,10 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
                         bool want_counts, cudaStream_t s) {
   int32_t *fb_rows, *fb_count;
   unsigned long long* ncand;
+  double* rinv;
+  ANCKA_TRY(ws.alloc(&rinv, (size_t)n));
+  k_inv_norms<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(pr.nrm2, n, rinv);
+  ANCKA_LAUNCHED();
   ANCKA_TRY(ws.alloc(&fb_rows, (size_t)n));
   ANCKA_TRY(ws.zeros(&fb_count, 1));
   ANCKA_TRY(ws.zeros(&ncand, 1));
@@ -376,7 +457,7 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     float* fb_thr = nullptr;
     if (collect_prec == ANCKA_PREC_BF16) ANCKA_TRY(ws.alloc(&fb_thr, (size_t)n));
     k_rerank<<<(unsigned)ceil_div(n, kWarps), kWarps * 32, 0, s>>>(
-        X, n, d, K, pr.err, pr.err_max, acc_coef, pr.nrm2, cand_val, cand_idx, lists, out_idx, out_sim,
+        X, n, d, K, pr.err, pr.err_max, acc_coef, rinv, cand_val, cand_idx, lists, out_idx, out_sim,
         fb_rows, fb_thr, fb_count, ncand);
     ANCKA_LAUNCHED();
     int32_t* ex_rows = fb_rows;
@@ -397,7 +478,7 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
         ANCKA_TRY(ws.zeros(&terr, 1));
         ANCKA_TRY(knn_collect_bf16(ws, pr, n, fb_rows, nf, fb_thr, cnt, buf, kCap, terr, s));
         k_rerank_collected<<<(unsigned)ceil_div(nf, kWarps), kWarps * 32, 0, s>>>(
-            X, d, K, pr.nrm2, fb_rows, fb_count, cnt, buf, kCap, out_idx, out_sim, ex_rows, ex_count);
+            X, d, K, rinv, fb_rows, fb_count, cnt, buf, kCap, out_idx, out_sim, ex_rows, ex_count);
         ANCKA_LAUNCHED();
         int32_t hterr = 0;
         ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -413,11 +494,11 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     int32_t* pi;
     ANCKA_TRY(ws.alloc(&pv, (size_t)kSlicedMaxRows * kSlices * K));
     ANCKA_TRY(ws.alloc(&pi, (size_t)kSlicedMaxRows * kSlices * K));
-    k_exh_sliced<<<1216, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, ex_rows, ex_count, pv, pi);
+    k_exh_sliced<<<1216, kExWarps * 32, 0, s>>>(X, n, d, K, rinv, ex_rows, ex_count, pv, pi);
     ANCKA_LAUNCHED();
     k_exh_merge<<<8, 128, 0, s>>>(ex_rows, ex_count, K, pv, pi, out_idx, out_sim);
     ANCKA_LAUNCHED();
-    k_knn_exhaustive<<<304, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, ex_rows, ex_count, 0, out_idx,
+    k_knn_exhaustive<<<304, kExWarps * 32, 0, s>>>(X, n, d, K, rinv, ex_rows, ex_count, 0, out_idx,
                                                    out_sim);
     ANCKA_LAUNCHED();
     if (want_counts) {
@@ -428,7 +509,7 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     }
   } else {
     const unsigned g = (unsigned)(n < 4096 ? n : 4096);
-    k_knn_exhaustive<<<g, kExWarps * 32, 0, s>>>(X, n, d, K, pr.nrm2, nullptr, nullptr, n, out_idx,
+    k_knn_exhaustive<<<g, kExWarps * 32, 0, s>>>(X, n, d, K, rinv, nullptr, nullptr, n, out_idx,
                                                  out_sim);
     ANCKA_LAUNCHED();
     if (n_exhaustive) *n_exhaustive = n;
