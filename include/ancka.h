@@ -135,6 +135,7 @@ typedef struct {
   float ms_total;
   float ms_contract;           /* the candidate similarity contraction kernel alone */
   float ms_rerank;             /* exact re-rank, certificate and fallback after the contraction */
+  float ms_spmm;               /* the T products Z = P Q of the orthogonal iteration (inside ms_iter) */
 } ancka_info;
 
 /* Fill *p with the defaults above. */
@@ -160,10 +161,32 @@ int64_t ancka_kernel_launches(void);
  *   out_idx  n x K int32: N_K(v_i) ordered by (cosine desc, index asc), i excluded
  *   out_sim  n x K FP32: the cosines, correctly rounded from a compensated
  *            (double-FP32) evaluation
- *   prec     ancka_prec of the candidate contraction (FP32 or BF16)
+ *   prec     ancka_prec of the candidate contraction: FP32 (CUDA cores), BF16
+ *            or FP8-E4M3 (tensor cores, d <= 512).  The result is the same
+ *            exact list for every precision; FP8 rows whose candidates cannot
+ *            be certified are redone from BF16 candidates.
  * Requires 1 <= K <= 64, K < n, 1 <= d <= 4096, n < 2^31. */
 ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
                        int32_t* out_idx, float* out_sim, ancka_info* info, void* stream);
+
+/* Diagnostic, not part of the method: the candidate lists of the tensor-core
+ * contraction before the exact re-rank, with the quantised copy and the error
+ * model the certificate uses, so that the bounds can be checked against exact
+ * arithmetic (Section 3.1 candidates; no counterpart in the paper).
+ *   X         n x d FP32 (device); prec BF16 or FP8; d <= 512
+ *   cand_val  n x 32 FP32 (device): row i's two 16-entry lists, entries
+ *             [0, 16) for keys j with (j mod 256) < 128 and [16, 32) for the
+ *             others; each list holds the 16 best low-precision scores of its
+ *             keys (self excluded), in cosine units
+ *   cand_idx  n x 32 int32 (device): their keys, -1 for an empty slot
+ *   qrows     n x d FP32 (device) or NULL: the quantised unit rows q_i the
+ *             contraction multiplied (FP8: codes divided by the scale)
+ *   err       n FP32 (device) or NULL: e_i >= || q_i - x_i/||x_i|| ||_2
+ *   acc       host, or NULL: the bound acc with
+ *             |score_ij - q_i . q_j| <= acc ||q_i|| ||q_j||
+ * All buffers are caller-owned. */
+ancka_status ancka_knn_candidates(const float* X, int64_t n, int32_t d, int32_t prec, float* cand_val,
+                                  int32_t* cand_idx, float* qrows, float* err, float* acc, void* stream);
 
 /* Algorithm 4 end to end: labels[i] in [0, k) for every node.
  *   topo   topology with device pointers

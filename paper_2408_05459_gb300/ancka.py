@@ -52,7 +52,7 @@ class Info(ctypes.Structure):
                 ("ms_knn", ctypes.c_float), ("ms_build", ctypes.c_float), ("ms_init", ctypes.c_float),
                 ("ms_iter", ctypes.c_float), ("ms_disc", ctypes.c_float), ("ms_mhc", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("ms_contract", ctypes.c_float),
-                ("ms_rerank", ctypes.c_float)]
+                ("ms_rerank", ctypes.c_float), ("ms_spmm", ctypes.c_float)]
 
     def to_dict(self) -> dict:
         n = self.n_phi
@@ -62,7 +62,8 @@ class Info(ctypes.Structure):
                     taken=list(self.taken[:n]), phi_best=self.phi_best, numeric_flags=self.numeric_flags,
                     ms_knn=self.ms_knn, ms_build=self.ms_build, ms_init=self.ms_init, ms_iter=self.ms_iter,
                     ms_disc=self.ms_disc, ms_mhc=self.ms_mhc, ms_total=self.ms_total,
-                    ms_contract=self.ms_contract, ms_rerank=self.ms_rerank)
+                    ms_contract=self.ms_contract, ms_rerank=self.ms_rerank,
+                    ms_spmm=self.ms_spmm)
 
 
 class AnckaError(RuntimeError):
@@ -103,6 +104,8 @@ def load(path: str = LIB_PATH):
     L.ancka_kernel_launches.restype = ctypes.c_int64
     L.ancka_knn.argtypes = [vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(Info), vp]
     L.ancka_knn.restype = ctypes.c_int
+    L.ancka_knn_candidates.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
+    L.ancka_knn_candidates.restype = ctypes.c_int
     L.ancka_cluster.argtypes = [ctypes.POINTER(Topology), vp, i32, ctypes.POINTER(Params), vp,
                                 ctypes.POINTER(Outputs), ctypes.POINTER(Info), vp]
     L.ancka_cluster.restype = ctypes.c_int
@@ -165,6 +168,24 @@ def knn(X, K: int, prec: str = "bf16", with_info: bool = True):
                           ctypes.byref(info) if with_info else None, _stream())
     _check("ancka_knn", st)
     return idx, sim, (info.to_dict() if with_info else None)
+
+
+def knn_candidates(X, prec: str = "bf16"):
+    """Diagnostic: the contraction's candidate lists before the exact re-rank
+    (n x 32 scores and keys, two 16-entry lists per row), the quantised unit
+    rows (n x d), the per-row error bounds (n) and the accumulation bound."""
+    import torch
+    assert X.is_cuda and X.dtype == torch.float32 and X.is_contiguous()
+    n, d = X.shape
+    cv = torch.empty((n, 32), dtype=torch.float32, device=X.device)
+    ci = torch.empty((n, 32), dtype=torch.int32, device=X.device)
+    q = torch.empty((n, d), dtype=torch.float32, device=X.device)
+    err = torch.empty(n, dtype=torch.float32, device=X.device)
+    acc = ctypes.c_float(0.0)
+    st = load().ancka_knn_candidates(_ptr(X), n, d, PREC[prec], _ptr(cv), _ptr(ci), _ptr(q), _ptr(err),
+                                     ctypes.byref(acc), _stream())
+    _check("ancka_knn_candidates", st)
+    return cv, ci, q, err, acc.value
 
 
 def topology_to_device(g: dict, device="cuda"):

@@ -4,6 +4,10 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda_fp8.h>
+
+#include <cmath>
+
 #include "common.cuh"
 
 namespace ancka {
@@ -111,6 +115,7 @@ void fill_times(Timer& t, ancka_info* info) {
     info->ms_iter = acc[3];
     info->ms_disc = acc[4];
     info->ms_mhc = acc[5];
+    info->ms_spmm = acc[6];
   }
 }
 
@@ -149,22 +154,27 @@ ancka_status validate_knn_args(const float* X, int64_t n, int32_t d, int32_t K, 
   ANCKA_REQUIRE(K >= 1 && K <= 64 && K < n, "K = %d must satisfy 1 <= K <= 64 and K < n", K);
   ANCKA_REQUIRE(prec == ANCKA_PREC_FP32 || prec == ANCKA_PREC_BF16 || prec == ANCKA_PREC_FP8,
                 "unknown precision %d", prec);
-  if (prec == ANCKA_PREC_FP8) {
-    set_error("FP8 contraction is not available in this build");
+  const bool tc = prec == ANCKA_PREC_BF16 || prec == ANCKA_PREC_FP8;
+  if (tc && !knn_tc_available()) {
+    set_error("tensor-core contraction is not available in this build");
     return ANCKA_ERR_UNSUPPORTED;
   }
-  if (prec == ANCKA_PREC_BF16 && !knn_tc_available()) {
-    set_error("BF16 tensor-core contraction is not available in this build");
-    return ANCKA_ERR_UNSUPPORTED;
-  }
-  if (prec == ANCKA_PREC_BF16 && K <= kCandC / 2 - 4 && round_up(d, 64) > knn_tc_max_dp()) {
-    set_error("BF16 contraction keeps the query block in shared memory: d must be <= %d", knn_tc_max_dp());
+  // FP8 keeps a BF16 copy for the rows its certificate leaves open
+  if (tc && K <= kCandC / 2 - 4 && round_up(d, 64) > knn_tc_max_dp()) {
+    set_error("tensor-core contraction keeps the query block in shared memory: d must be <= %d", knn_tc_max_dp());
     return ANCKA_ERR_UNSUPPORTED;
   }
   return ANCKA_OK;
 }
 
-int max_candidate_K(int prec) { return prec == ANCKA_PREC_BF16 ? kCandC / 2 - 4 : kCandC / 2; }
+int max_candidate_K(int prec) { return prec == ANCKA_PREC_FP32 ? kCandC / 2 : kCandC / 2 - 4; }
+
+// accumulation bound of the tensor-core contraction: a few units in the last
+// place of FP32 per MMA step (16 BF16 or 32 FP8 products), checked against
+// exact products of the quantised rows in the tests
+float tc_acc_bound(int dp, int k_per_mma, int ulp_log2) {
+  return (float)((dp / k_per_mma + 2) * std::ldexp(1.0, ulp_log2));
+}
 
 // the KNN lists with every step on the device
 ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
@@ -194,9 +204,20 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
         set_error("tensor-core contraction: a pipeline wait expired (role %d)", hterr);
         return ANCKA_ERR_TIMEOUT;
       }
-      // tensor-core FP32 accumulation: a few units in the last place per
-      // 16-wide MMA step (bound validated against exact products in tests)
-      acc = (float)((pr.dp / 16 + 2) * 2.384185791015625e-07);  // 2^-22 per step
+      acc = tc_acc_bound(pr.dp, 16, -22);
+    } else if (prec == ANCKA_PREC_FP8) {
+      int32_t* terr;
+      ANCKA_TRY(ws.zeros(&terr, 1));
+      ANCKA_TRY(knn_candidates_fp8(pr, n, cv, ci, terr, s));
+      if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
+      int32_t hterr = 0;
+      ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaStreamSynchronize(s));
+      if (hterr) {
+        set_error("tensor-core FP8 contraction: a pipeline wait expired (role %d)", hterr);
+        return ANCKA_ERR_TIMEOUT;
+      }
+      acc = tc_acc_bound(pr.dp8, 32, -18);
     } else {
       ANCKA_TRY(knn_candidates_fp32(pr, n, cv, ci, s));
       if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
@@ -206,12 +227,13 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
     }
     // the tensor-core kernel leaves two 16-entry lists per row (one per half
     // of the key columns), the CUDA-core kernel one 32-entry list
-    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, acc, cv, ci, prec == ANCKA_PREC_BF16 ? 2 : 1, prec, idx, sim, ncand,
-                         nfb, nex, counts, s));
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, prec, acc, tc_acc_bound(pr.dp, 16, -22), cv, ci,
+                         prec == ANCKA_PREC_FP32 ? 1 : 2, prec == ANCKA_PREC_FP32 ? prec : ANCKA_PREC_BF16, idx, sim,
+                         ncand, nfb, nex, counts, s));
     if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[2], s));
   } else {
-    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, 0.f, nullptr, nullptr, 1, ANCKA_PREC_FP32, idx, sim, ncand, nfb, nex,
-                         counts, s));
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, ANCKA_PREC_FP32, 0.f, 0.f, nullptr, nullptr, 1, ANCKA_PREC_FP32, idx,
+                         sim, ncand, nfb, nex, counts, s));
   }
   return ANCKA_OK;
 }
@@ -387,6 +409,22 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
 
 using namespace ancka;
 
+// quantised unit rows as the contraction multiplied them (diagnostics)
+__global__ void k_copy_qrows(const __nv_bfloat16* __restrict__ xb, int dp, const uint8_t* __restrict__ x8, int dp8,
+                             const float* __restrict__ inv_s2, int64_t n, int d, float* __restrict__ q) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * d) return;
+  const int64_t row = t / d;
+  const int c = (int)(t % d);
+  if (x8) {
+    __nv_fp8_e4m3 v;
+    v.__x = x8[row * dp8 + c];
+    q[t] = (float)v * sqrtf(*inv_s2);  // 1/S exactly: S^2 is an even power of two
+  } else {
+    q[t] = __bfloat162float(xb[row * dp + c]);
+  }
+}
+
 extern "C" {
 
 void ancka_params_default(ancka_params* p) {
@@ -477,6 +515,42 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
     cudaEventDestroy(b);
   }
   return st;
+}
+
+ancka_status ancka_knn_candidates(const float* X, int64_t n, int32_t d, int32_t prec, float* cand_val,
+                                  int32_t* cand_idx, float* qrows, float* err, float* acc, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_REQUIRE(prec == ANCKA_PREC_BF16 || prec == ANCKA_PREC_FP8, "precision must be BF16 or FP8");
+  ANCKA_TRY(validate_knn_args(X, n, d, 1, prec));
+  ANCKA_REQUIRE(cand_val && cand_idx, "output pointers are NULL");
+  Workspace ws(s);
+  PrepOut pr;
+  ANCKA_TRY(prep_rows(ws, X, n, d, prec, &pr, s));
+  int32_t* terr;
+  ANCKA_TRY(ws.zeros(&terr, 1));
+  if (prec == ANCKA_PREC_BF16) {
+    ANCKA_TRY(knn_candidates_bf16(pr, n, cand_val, cand_idx, terr, s));
+  } else {
+    ANCKA_TRY(knn_candidates_fp8(pr, n, cand_val, cand_idx, terr, s));
+  }
+  if (qrows) {
+    k_copy_qrows<<<(unsigned)ceil_div(n * d, 256), 256, 0, s>>>(pr.xb, pr.dp, prec == ANCKA_PREC_FP8 ? pr.x8 : nullptr,
+                                                                pr.dp8, pr.inv_s2, n, d, qrows);
+    ANCKA_LAUNCHED();
+  }
+  if (err)
+    ANCKA_CUDA(cudaMemcpyAsync(err, prec == ANCKA_PREC_FP8 ? pr.err8 : pr.err, sizeof(float) * n,
+                               cudaMemcpyDeviceToDevice, s));
+  int32_t hterr = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (hterr) {
+    set_error("tensor-core contraction: a pipeline wait expired (role %d)", hterr);
+    return ANCKA_ERR_TIMEOUT;
+  }
+  if (acc) *acc = prec == ANCKA_PREC_FP8 ? tc_acc_bound(pr.dp8, 32, -18) : tc_acc_bound(pr.dp, 16, -22);
+  return ANCKA_OK;
 }
 
 ancka_status ancka_cluster(const ancka_topology* topo, const float* X, int32_t d, const ancka_params* p,

@@ -173,6 +173,14 @@ struct PrepOut {
   double* nrm2;        // n: ||x_i||^2 (compensated)
   int32_t* zero_row;   // n: 1 if x_i == 0
   float* err_max;      // 1: max_i err_i
+  // FP8 mode (besides the BF16 copy above): E4M3 copy of S * unit rows, one
+  // power-of-two scale S for all rows, so q_i . q_j / S^2 approximates the
+  // cosine; err8 bounds || q_i / S - x_i/||x_i|| ||_2
+  int32_t dp8;            // padded feature dimension (multiple of 128)
+  uint8_t* x8;            // n_pad x dp8 E4M3 codes, or null
+  float* err8;            // n
+  float* err8_max;        // 1
+  float* inv_s2;          // 1: 1 / S^2
 };
 ancka_status prep_rows(Workspace& ws, const float* X, int64_t n, int32_t d, int prec, PrepOut* out,
                        cudaStream_t s);
@@ -183,6 +191,13 @@ ancka_status knn_candidates_fp32(const PrepOut& pr, int64_t n, float* cand_val, 
                                  cudaStream_t s);
 ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
                                  int32_t* err, cudaStream_t s);
+// FP8 (E4M3) list pass: scores written in cosine units (times 1/S^2)
+ancka_status knn_candidates_fp8(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx, int32_t* err,
+                                cudaStream_t s);
+int knn_tc_max_dp_fp8();
+// BF16 list pass for the n_a rows listed in rows; lists written at their global rows
+ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
+                                    float* cand_val, int32_t* cand_idx, int32_t* err, cudaStream_t s);
 bool knn_tc_available();
 int knn_tc_max_dp();
 // collect pass: for the n_a query rows listed in `rows`, every key j != row
@@ -192,13 +207,16 @@ ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const
                               const float* thr, int32_t* cnt, int32_t* buf, int cap, int32_t* err, cudaStream_t s);
 
 // rerank.cu: certified exact re-rank + exhaustive fallback
-// lists: 1 (one 32-list per row) or 2 (two 16-lists); collect_prec ==
-// ANCKA_PREC_BF16 sends uncertified rows through the tensor-core collect pass
+// list_prec: precision of the candidate lists (FP32, BF16 or FP8; acc_coef
+// is its accumulation bound); lists: 1 (one 32-list per row) or 2 (two
+// 16-lists).  FP8: rows the FP8 lists cannot certify get BF16 lists
+// (acc_bf16) and a second certificate.  collect_prec == ANCKA_PREC_BF16 sends
+// rows still uncertified through the tensor-core collect pass.
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
-                        const PrepOut& pr, float acc_coef, const float* cand_val,
-                        const int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx,
-                        float* out_sim, int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive,
-                        bool want_counts, cudaStream_t s);
+                        const PrepOut& pr, int list_prec, float acc_coef, float acc_bf16, float* cand_val,
+                        int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx, float* out_sim,
+                        int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive, bool want_counts,
+                        cudaStream_t s);
 
 // graph.cu: walk structures
 struct Csr {

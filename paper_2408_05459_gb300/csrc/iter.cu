@@ -1374,7 +1374,7 @@ struct PhaseTimer {
 
 }  // namespace
 
-// phases: 2 = init, 3 = iteration, 4 = discretize, 5 = mhc
+// phases: 2 = init, 3 = iteration, 4 = discretize, 5 = mhc, 6 = the walk products inside 3
 ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const int32_t* init_labels,
                        int32_t* labels_out, float* Q_out, int32_t* init_out, IterTrace* tr,
                        cudaStream_t s) {
@@ -1480,7 +1480,10 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   for (int t = 1; t <= cfg.T; ++t) {
     {
       PhaseTimer pt(tr, s, 3);
-      ANCKA_TRY(apply_walk(c, Q, ld, Z, 1.f, nullptr, nullptr, 0.f));   // Z = P Q
+      {
+        PhaseTimer pw(tr, s, 6);
+        ANCKA_TRY(apply_walk(c, Q, ld, Z, 1.f, nullptr, nullptr, 0.f));  // Z = P Q
+      }
       ANCKA_TRY(cholqr2(ws, c, Z, Q, wq, gpart, gblk, gticket, Rinv, chol_status));  // result in Z
       float* tt = Q;
       Q = Z;

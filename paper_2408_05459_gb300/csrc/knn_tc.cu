@@ -1,12 +1,14 @@
-// tcgen05 BF16 candidate search for the cosine KNN of Section 3.1.
+// tcgen05 BF16 / FP8-e4m3 candidate search for the cosine KNN of Section 3.1.
 //
 // One CTA per 128 query rows sweeps every 256-row key tile:
-//   warp 0     TMA producer: the CTA's query block A (128 x dp BF16, 128-byte
-//              swizzle) once, then key tiles B (256 rows x 64 features per
-//              stage) through an nstages-deep ring (mbarrier full/empty);
+//   warp 0     TMA producer: the CTA's query block A (128 x dp, 128-byte
+//              swizzle) once, then key tiles B (256 rows x 128 bytes of
+//              features per stage: 64 BF16 or 128 FP8) through an
+//              nstages-deep ring (mbarrier full/empty);
 //   warp 1     MMA issuer: allocates 512 TMEM columns, issues
-//              tcgen05.mma.cta_group::1.kind::f16 (M=128, N=256, K=16) into
-//              two ping-pong FP32 accumulators, commits stage releases and
+//              tcgen05.mma.cta_group::1.kind::f16 (BF16, K=16) or
+//              kind::f8f6f4 (E4M3, K=32) with M=128, N=256 into two
+//              ping-pong FP32 accumulators, commits stage releases and
 //              accumulator-ready signals;
 //   warps 2-9  epilogue: two warps per TMEM lane quarter, each owning half of
 //              every tile's 256 columns; tcgen05.ld (32x32b) of the thread's
@@ -30,21 +32,24 @@ namespace {
 
 constexpr int kTM = 128;                 // query rows per CTA = TMEM lanes
 constexpr int kTN = 256;                 // key rows per tile = accumulator columns
-constexpr int kTK = 64;                  // features per stage: one 128-byte swizzle row
+constexpr int kTKB = 128;                // bytes of features per stage: one 128-byte swizzle row
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kListC = kCandC / 2;     // per-thread list (two per row)
-constexpr int kABytes = kTM * kTK * 2;   // 16 KB per 64-feature block of A
-constexpr int kBBytes = kTN * kTK * 2;   // 32 KB per stage of B
+constexpr int kABytes = kTM * kTKB;      // 16 KB per 128-byte block of A
+constexpr int kBBytes = kTN * kTKB;      // 32 KB per stage of B
+constexpr int kMmaPerStage = 4;          // 32 bytes of K per MMA: 16 BF16 or 32 FP8
 constexpr int kMaxStages = 8;
 constexpr int kMaxSmem = 232448;         // 227 KB opt-in dynamic shared memory
 constexpr uint32_t kTmemCols = 512;      // two 256-column FP32 accumulators
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
-// instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
-                            ((uint32_t)(kTM >> 4) << 24);
+// instruction descriptors: D = F32 (bits 4-5 = 1), both operands K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28; kind::f16 with A = B = BF16
+// (format 1 at bits 7-9 and 10-12); kind::f8f6f4 with A = B = E4M3 (format 0)
+constexpr uint32_t kIdescBF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                                ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t kIdescE4M3 = (1u << 4) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 
 struct __align__(8) Bars {
   uint64_t full[kMaxStages];
@@ -117,7 +122,14 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           tmem_d),
-      "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
+      "l"(da), "l"(db), "r"(kIdescBF16), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem_d),
+      "l"(da), "l"(db), "r"(kIdescE4M3), "r"(accum)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -200,19 +212,24 @@ __device__ __forceinline__ void collect_chunk(const uint32_t (&r)[32], int64_t j
 }
 
 struct CollectArgs {
-  const int32_t* a_rows;  // global row of each compact query row
+  const int32_t* a_rows;  // global row of each compact query row (null: A holds rows 0..n-1)
   int64_t n_a;            // compact query rows
-  const float* thr;       // per compact row threshold
-  int32_t* cnt;           // per compact row counter
-  int32_t* buf;           // n_a x cap keys
+  const float* thr;       // collect mode: per compact row threshold
+  int32_t* cnt;           // collect mode: per compact row counter
+  int32_t* buf;           // collect mode: n_a x cap keys
   int cap;
 };
 
-template <bool kCollect>
+// kCollect: collect mode (keys above a per-row threshold) instead of list
+// mode (two 16-entry lists per row); kE4M3: FP8 operands.  out_scale (list
+// mode, may be null) multiplies the scores written out.
+template <bool kCollect, bool kE4M3>
 __global__ void __launch_bounds__(kThreads, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
          int64_t n_pad, int kb_count, int nstages, int tps, float* __restrict__ cand_val,
-         int32_t* __restrict__ cand_idx, CollectArgs ca, int* __restrict__ err) {
+         int32_t* __restrict__ cand_idx, const float* __restrict__ out_scale, CollectArgs ca,
+         int* __restrict__ err) {
+  constexpr int kTK = kE4M3 ? 128 : 64;  // features per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -311,8 +328,12 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           const uint32_t a0 = smem_u32(sA + kb * kABytes);
           const uint32_t b0 = smem_u32(sB + stage * kBBytes);
 #pragma unroll
-          for (int kk = 0; kk < kTK / 16; ++kk)
-            umma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < kMmaPerStage; ++kk) {
+            if constexpr (kE4M3)
+              umma_e4m3(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+            else
+              umma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+          }
           issued = true;
           umma_commit(&bars->empty[stage]);
           if (++stage == nstages) {
@@ -333,10 +354,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     const int q = warp & 3;    // TMEM lane quarter this warp may access
     const int h = ew >> 2;     // column half of every tile
     const int r = q * 32 + lane;
-    // list mode: query row ib + r; collect mode: compact row ra -> global row
+    // A row ra is query row ra, or compact row ra -> global row a_rows[ra]
     const int64_t ra = ib + r;
-    const bool row_ok = kCollect ? (ra < ca.n_a) : (ra < n);
-    const int64_t i = kCollect ? (row_ok ? (int64_t)ca.a_rows[ra] : -1) : ra;
+    const bool row_ok = ca.a_rows ? (ra < ca.n_a) : (ra < n);
+    const int64_t i = ca.a_rows ? (row_ok ? (int64_t)ca.a_rows[ra] : -1) : ra;
     const float t_row = kCollect && row_ok ? ca.thr[ra] : INFINITY;
     constexpr int C = kListC;
     float lv[C];
@@ -374,9 +395,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       if (lane == 0) mbar_arrive(&bars->tempty[b]);
     }
     if (!kCollect && row_ok) {
+      const float sc = out_scale ? *out_scale : 1.f;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        cand_val[i * kCandC + h * C + c] = lv[c];
+        cand_val[i * kCandC + h * C + c] = lv[c] * sc;
         cand_idx[i * kCandC + h * C + c] = li[c];
       }
     }
@@ -403,24 +425,53 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-ancka_status make_map(CUtensorMap* m, const void* base, int64_t dp, int64_t rows_total, uint32_t box_rows) {
+// tensor map over a row-major (rows_total x dp) matrix of 1- or 2-byte
+// elements: boxes of 128 bytes of features x box_rows rows, 128-byte swizzle
+ancka_status make_map(CUtensorMap* m, const void* base, int64_t dp, int64_t rows_total, uint32_t box_rows,
+                      int elem_bytes) {
   auto enc = encode_fn();
   if (!enc) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return ANCKA_ERR_UNSUPPORTED;
   }
   cuuint64_t gdim[2] = {(cuuint64_t)dp, (cuuint64_t)rows_total};
-  cuuint64_t gstride[1] = {(cuuint64_t)dp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kTK, box_rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)dp * (cuuint64_t)elem_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(kTKB / elem_bytes), box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                   const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
     return ANCKA_ERR_CUDA;
   }
   return ANCKA_OK;
+}
+
+// pipeline depth and dynamic shared memory for kb_count blocks of A
+ancka_status tc_smem(int kb_count, int* nstages, size_t* smem) {
+  const size_t fixed = 1024 + (size_t)kb_count * kABytes + sizeof(Bars);
+  int ns = (int)((kMaxSmem - fixed) / kBBytes);
+  if (ns > kMaxStages) ns = kMaxStages;
+  if (ns < 2) {
+    set_error("tensor-core contraction: not enough shared memory for two stages");
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  // at least ~120 KB so that one CTA owns an SM and its 512 TMEM columns
+  size_t sm = fixed + (size_t)ns * kBBytes;
+  if (sm < 120 * 1024) sm = 120 * 1024;
+  *nstages = ns;
+  *smem = sm;
+  return ANCKA_OK;
+}
+
+__global__ void k_gather_rows(const uint8_t* __restrict__ x, int row_bytes, const int32_t* __restrict__ rows,
+                              int64_t n_a, int64_t n_a_pad, uint8_t* __restrict__ out) {
+  const int64_t r = blockIdx.x;
+  if (r >= n_a_pad) return;
+  const uint4* src = r < n_a ? reinterpret_cast<const uint4*>(x + (int64_t)rows[r] * row_bytes) : nullptr;
+  uint4* dst = reinterpret_cast<uint4*>(out + r * row_bytes);
+  for (int c = threadIdx.x; c < row_bytes / 16; c += blockDim.x) dst[c] = src ? src[c] : make_uint4(0, 0, 0, 0);
 }
 
 }  // namespace
@@ -431,61 +482,91 @@ int knn_tc_max_dp() { return 512; }
 
 ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx, int32_t* err,
                                  cudaStream_t s) {
-  const int kb_count = pr.dp / kTK;
-  if (pr.dp % kTK != 0 || kb_count < 1 || pr.dp > knn_tc_max_dp()) {
+  const int kb_count = pr.dp / 64;
+  if (pr.dp % 64 != 0 || kb_count < 1 || pr.dp > knn_tc_max_dp()) {
     set_error("BF16 contraction supports up to %d features (got %d)", knn_tc_max_dp(), pr.dp);
     return ANCKA_ERR_UNSUPPORTED;
   }
-  const size_t fixed = 1024 + (size_t)kb_count * kABytes + sizeof(Bars);
-  int nstages = (int)((kMaxSmem - fixed) / kBBytes);
-  if (nstages > kMaxStages) nstages = kMaxStages;
-  if (nstages < 2) {
-    set_error("BF16 contraction: not enough shared memory for two stages");
-    return ANCKA_ERR_UNSUPPORTED;
-  }
-  // at least ~120 KB so that one CTA owns an SM and its 512 TMEM columns
-  size_t smem = fixed + (size_t)nstages * kBBytes;
-  if (smem < 120 * 1024) smem = 120 * 1024;
+  int nstages;
+  size_t smem;
+  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
   CUtensorMap ta, tb;
-  ANCKA_TRY(make_map(&ta, pr.xb, pr.dp, pr.n_pad, kTM));
-  ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN));
-  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ANCKA_TRY(make_map(&ta, pr.xb, pr.dp, pr.n_pad, kTM, 2));
+  ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CollectArgs none{};
   const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
-  k_knn_tc<false><<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(ta, tb, n, pr.n_pad, kb_count, nstages,
-                                                                   all_tiles, cand_val, cand_idx, none, err);
+  k_knn_tc<false, false><<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(
+      ta, tb, n, pr.n_pad, kb_count, nstages, all_tiles, cand_val, cand_idx, nullptr, none, err);
   ANCKA_LAUNCHED();
   return ANCKA_OK;
 }
 
-namespace {
-__global__ void k_gather_rows(const __nv_bfloat16* __restrict__ xb, int dp, const int32_t* __restrict__ rows,
-                              int64_t n_a, int64_t n_a_pad, __nv_bfloat16* __restrict__ out) {
-  const int64_t r = blockIdx.x;
-  if (r >= n_a_pad) return;
-  const uint4* src = r < n_a ? reinterpret_cast<const uint4*>(xb + (int64_t)rows[r] * dp) : nullptr;
-  uint4* dst = reinterpret_cast<uint4*>(out + r * dp);
-  for (int c = threadIdx.x; c < dp / 8; c += blockDim.x) dst[c] = src ? src[c] : make_uint4(0, 0, 0, 0);
+ancka_status knn_candidates_fp8(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx, int32_t* err,
+                                cudaStream_t s) {
+  const int kb_count = pr.dp8 / 128;
+  if (!pr.x8 || pr.dp8 % 128 != 0 || kb_count < 1 || pr.dp8 > knn_tc_max_dp_fp8()) {
+    set_error("FP8 contraction supports up to %d features (got %d)", knn_tc_max_dp_fp8(), pr.dp8);
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  int nstages;
+  size_t smem;
+  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
+  CUtensorMap ta, tb;
+  ANCKA_TRY(make_map(&ta, pr.x8, pr.dp8, pr.n_pad, kTM, 1));
+  ANCKA_TRY(make_map(&tb, pr.x8, pr.dp8, pr.n_pad, kTN, 1));
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CollectArgs none{};
+  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
+  k_knn_tc<false, true><<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(
+      ta, tb, n, pr.n_pad, kb_count, nstages, all_tiles, cand_val, cand_idx, pr.inv_s2, none, err);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
 }
-}  // namespace
 
-ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
-                              const float* thr, int32_t* cnt, int32_t* buf, int cap, int32_t* err, cudaStream_t s) {
-  const int kb_count = pr.dp / kTK;
-  const size_t fixed = 1024 + (size_t)kb_count * kABytes + sizeof(Bars);
-  int nstages = (int)((kMaxSmem - fixed) / kBBytes);
-  if (nstages > kMaxStages) nstages = kMaxStages;
-  size_t smem = fixed + (size_t)nstages * kBBytes;
-  if (smem < 120 * 1024) smem = 120 * 1024;
+int knn_tc_max_dp_fp8() { return 1024; }
+
+// BF16 lists for the n_a rows listed in rows (written at their global rows)
+ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
+                                    float* cand_val, int32_t* cand_idx, int32_t* err, cudaStream_t s) {
+  const int kb_count = pr.dp / 64;
+  int nstages;
+  size_t smem;
+  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
   const int64_t n_a_pad = round_up(n_a, kTM);
   __nv_bfloat16* af;
   ANCKA_TRY(ws.alloc(&af, (size_t)n_a_pad * pr.dp));
-  k_gather_rows<<<(unsigned)n_a_pad, 64, 0, s>>>(pr.xb, pr.dp, rows, n_a, n_a_pad, af);
+  k_gather_rows<<<(unsigned)n_a_pad, 64, 0, s>>>(reinterpret_cast<const uint8_t*>(pr.xb), pr.dp * 2, rows, n_a,
+                                                 n_a_pad, reinterpret_cast<uint8_t*>(af));
   ANCKA_LAUNCHED();
   CUtensorMap ta, tb;
-  ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM));
-  ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN));
-  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM, 2));
+  ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CollectArgs ca{rows, n_a, nullptr, nullptr, nullptr, 0};
+  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
+  k_knn_tc<false, false><<<(unsigned)(n_a_pad / kTM), kThreads, smem, s>>>(
+      ta, tb, n, pr.n_pad, kb_count, nstages, all_tiles, cand_val, cand_idx, nullptr, ca, err);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
+                              const float* thr, int32_t* cnt, int32_t* buf, int cap, int32_t* err, cudaStream_t s) {
+  const int kb_count = pr.dp / 64;
+  int nstages;
+  size_t smem;
+  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
+  const int64_t n_a_pad = round_up(n_a, kTM);
+  __nv_bfloat16* af;
+  ANCKA_TRY(ws.alloc(&af, (size_t)n_a_pad * pr.dp));
+  k_gather_rows<<<(unsigned)n_a_pad, 64, 0, s>>>(reinterpret_cast<const uint8_t*>(pr.xb), pr.dp * 2, rows, n_a,
+                                                 n_a_pad, reinterpret_cast<uint8_t*>(af));
+  ANCKA_LAUNCHED();
+  CUtensorMap ta, tb;
+  ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM, 2));
+  ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CollectArgs ca{rows, n_a, thr, cnt, buf, cap};
   // split the key sweep so that about two waves of CTAs run
   int sms = 152, dev = 0;
@@ -496,9 +577,8 @@ ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const
   int splits = (int)std::max<int64_t>(1, std::min<int64_t>(all_tiles, (2 * sms) / std::max<int64_t>(1, qblocks)));
   const int tps = (int)ceil_div(all_tiles, splits);
   splits = (int)ceil_div(all_tiles, tps);
-  k_knn_tc<true><<<dim3((unsigned)qblocks, (unsigned)splits), kThreads, smem, s>>>(ta, tb, n, pr.n_pad, kb_count,
-                                                                                  nstages, tps, nullptr, nullptr, ca,
-                                                                                  err);
+  k_knn_tc<true, false><<<dim3((unsigned)qblocks, (unsigned)splits), kThreads, smem, s>>>(
+      ta, tb, n, pr.n_pad, kb_count, nstages, tps, nullptr, nullptr, nullptr, ca, err);
   ANCKA_LAUNCHED();
   return ANCKA_OK;
 }

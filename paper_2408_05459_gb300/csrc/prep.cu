@@ -6,6 +6,8 @@
 //     err_i >= || copy_i - x_i/||x_i|| ||_2 .
 // The bound feeds the candidate certificate of the re-rank: for unit rows
 // |cos_ij - copy_i . copy_j| <= err_i (1 + err_j) + err_j + (accumulation).
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace ancka {
@@ -19,11 +21,15 @@ constexpr int kPrepWarps = 8;
 // ||u - x/||x|||| <= 2^-22; twice that is used.
 constexpr float kUnitSlack = 4.8e-7f;
 
+// the FP32 sum of dp squares (fmaf, in any order) is within a factor
+// 1 + (dp + 1) 2^-24 of the exact sum; its square root within half that
+__device__ __forceinline__ float norm_slack(int dp) { return 1.f + (float)(dp + 2) * 5.9604645e-8f; }
+
 __global__ void __launch_bounds__(kPrepWarps * 32)
 k_prep_rows(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp, int prec,
             float* __restrict__ xu32, __nv_bfloat16* __restrict__ xb, float* __restrict__ err,
             double* __restrict__ nrm2, int32_t* __restrict__ zero_row,
-            unsigned int* __restrict__ err_max_bits, int64_t n_pad) {
+            unsigned int* __restrict__ err_max_bits, unsigned int* __restrict__ umax_bits, int64_t n_pad) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * kPrepWarps + (threadIdx.x >> 5);
   if (row >= n_pad) return;
@@ -46,9 +52,10 @@ k_prep_rows(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp, int p
   any = __any_sync(0xffffffffu, any);
   double n2 = (double)s + (double)cc;
   float inv = any ? (float)(1.0 / sqrt(n2)) : 0.f;
-  float e2 = 0.f;
+  float e2 = 0.f, um = 0.f;
   for (int c = lane; c < dp; c += 32) {
     float u = c < d ? x[c] * inv : 0.f;
+    um = fmaxf(um, fabsf(u));
     if (prec == ANCKA_PREC_BF16) {
       __nv_bfloat16 b = __float2bfloat16_rn(u);
       xb[row * dp + c] = b;
@@ -59,12 +66,59 @@ k_prep_rows(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp, int p
     }
   }
   e2 = warp_sum(e2);
+  for (int off = 16; off >= 1; off >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, off));
   if (lane == 0) {
-    float e = any ? sqrtf(e2) * (1.f + 1e-6f) + kUnitSlack : 0.f;
+    float e = any ? sqrtf(e2) * norm_slack(dp) + kUnitSlack : 0.f;
     err[row] = e;
     nrm2[row] = n2;
     zero_row[row] = any ? 0 : 1;
     atomicMax(err_max_bits, __float_as_uint(e));  // non-negative floats order as uints
+    if (umax_bits) atomicMax(umax_bits, __float_as_uint(um));
+  }
+}
+
+// the power-of-two scale of the FP8 copy: the largest S with S * max|u| <= 448
+// (E4M3's largest finite value); S = 1 for an all-zero input
+__device__ __forceinline__ float fp8_scale(const unsigned int* umax_bits) {
+  const float um = __uint_as_float(*umax_bits);
+  if (!(um > 0.f)) return 1.f;
+  return ldexpf(1.f, (int)floorf(log2f(448.f / um)));
+}
+
+// E4M3 copy of S * unit rows (round to nearest even, saturating) and the
+// exact distance bound err8_i >= || q_i / S - u_i ||, one warp per row.  The
+// unit row u is formed as in k_prep_rows (same norm, same reciprocal).
+__global__ void __launch_bounds__(kPrepWarps * 32)
+k_prep_fp8(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp8, const double* __restrict__ nrm2,
+           const int32_t* __restrict__ zero_row, const unsigned int* __restrict__ umax_bits,
+           uint8_t* __restrict__ x8, float* __restrict__ err8, unsigned int* __restrict__ err8_max_bits,
+           float* __restrict__ inv_s2, int64_t n_pad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * kPrepWarps + (threadIdx.x >> 5);
+  if (row >= n_pad) return;
+  const float S = fp8_scale(umax_bits);
+  if (row == 0 && lane == 0) *inv_s2 = 1.f / (S * S);  // exact: a power of two
+  if (row >= n) {
+    for (int c = lane; c < dp8; c += 32) x8[row * dp8 + c] = 0;
+    return;
+  }
+  const float* x = X + row * (int64_t)d;
+  const bool zero = zero_row[row] != 0;
+  const float inv = zero ? 0.f : (float)(1.0 / sqrt(nrm2[row]));
+  const float invS = 1.f / S;
+  float e2 = 0.f;
+  for (int c = lane; c < dp8; c += 32) {
+    const float u = c < d ? x[c] * inv : 0.f;
+    const __nv_fp8_e4m3 q(u * S);
+    x8[row * dp8 + c] = q.__x;
+    const float dq = (float)q * invS - u;  // exact: q / S is exact and within a factor 2 of u (or 0)
+    e2 = fmaf(dq, dq, e2);
+  }
+  e2 = warp_sum(e2);
+  if (lane == 0) {
+    const float e = zero ? 0.f : sqrtf(e2) * norm_slack(dp8) + kUnitSlack;
+    err8[row] = e;
+    atomicMax(err8_max_bits, __float_as_uint(e));
   }
 }
 
@@ -75,9 +129,10 @@ ancka_status prep_rows(Workspace& ws, const float* X, int64_t n, int32_t d, int 
   PrepOut o{};
   // BF16 tiles consume 64 features (128 bytes) per pipeline stage; the FP32
   // SIMT tiles consume 8.  Rows are padded to the 128-row tile height.
-  o.dp = (int32_t)(prec == ANCKA_PREC_BF16 ? round_up(d, 64) : round_up(d, 8));
+  const bool tc = prec == ANCKA_PREC_BF16 || prec == ANCKA_PREC_FP8;
+  o.dp = (int32_t)(tc ? round_up(d, 64) : round_up(d, 8));
   o.n_pad = round_up(n, 128);
-  if (prec == ANCKA_PREC_BF16) {
+  if (tc) {
     ANCKA_TRY(ws.alloc(&o.xb, (size_t)o.n_pad * o.dp));
   } else {
     ANCKA_TRY(ws.alloc(&o.xu32, (size_t)o.n_pad * o.dp));
@@ -86,11 +141,23 @@ ancka_status prep_rows(Workspace& ws, const float* X, int64_t n, int32_t d, int 
   ANCKA_TRY(ws.alloc(&o.nrm2, (size_t)n));
   ANCKA_TRY(ws.alloc(&o.zero_row, (size_t)n));
   ANCKA_TRY(ws.zeros(&o.err_max, 1));
+  unsigned int* umax = nullptr;
+  if (prec == ANCKA_PREC_FP8) ANCKA_TRY(ws.zeros(&umax, 1));
   dim3 grid((unsigned)ceil_div(o.n_pad, kPrepWarps));
-  k_prep_rows<<<grid, kPrepWarps * 32, 0, s>>>(X, n, d, o.dp, prec, o.xu32, o.xb, o.err, o.nrm2,
-                                               o.zero_row, reinterpret_cast<unsigned int*>(o.err_max),
-                                               o.n_pad);
+  k_prep_rows<<<grid, kPrepWarps * 32, 0, s>>>(X, n, d, o.dp, tc ? ANCKA_PREC_BF16 : ANCKA_PREC_FP32, o.xu32, o.xb,
+                                               o.err, o.nrm2, o.zero_row,
+                                               reinterpret_cast<unsigned int*>(o.err_max), umax, o.n_pad);
   ANCKA_LAUNCHED();
+  if (prec == ANCKA_PREC_FP8) {
+    o.dp8 = (int32_t)round_up(d, 128);
+    ANCKA_TRY(ws.alloc(&o.x8, (size_t)o.n_pad * o.dp8));
+    ANCKA_TRY(ws.alloc(&o.err8, (size_t)n));
+    ANCKA_TRY(ws.zeros(&o.err8_max, 1));
+    ANCKA_TRY(ws.alloc(&o.inv_s2, 1));
+    k_prep_fp8<<<grid, kPrepWarps * 32, 0, s>>>(X, n, d, o.dp8, o.nrm2, o.zero_row, umax, o.x8, o.err8,
+                                                reinterpret_cast<unsigned int*>(o.err8_max), o.inv_s2, o.n_pad);
+    ANCKA_LAUNCHED();
+  }
   *out = o;
   return ANCKA_OK;
 }

@@ -137,7 +137,8 @@ __global__ void k_inv_norms(const double* __restrict__ nrm2, int64_t n, double* 
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
-k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __restrict__ err,
+k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64_t n_rows, int d, int K,
+         const float* __restrict__ err,
          const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ rinv,
          const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx, int lists,
          int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ fb_rows,
@@ -146,8 +147,9 @@ k_rerank(const float* __restrict__ X, int64_t n, int d, int K, const float* __re
   if (threadIdx.x == 0) block_cand = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (i < n) {
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w < n_rows) {
+    const int64_t i = rows_in ? (int64_t)rows_in[w] : w;  // all rows, or the listed ones
     float v = cand_val[i * kCandC + lane];
     int32_t j = cand_idx[i * kCandC + lane];
     const bool valid = j >= 0;
@@ -439,10 +441,10 @@ __global__ void k_exh_merge(const int32_t* __restrict__ rows, const int32_t* __r
 }  // namespace
 
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
-                        const PrepOut& pr, float acc_coef, const float* cand_val,
-                        const int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx,
-                        float* out_sim, int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive,
-                        bool want_counts, cudaStream_t s) {
+                        const PrepOut& pr, int list_prec, float acc_coef, float acc_bf16, float* cand_val,
+                        int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx, float* out_sim,
+                        int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive, bool want_counts,
+                        cudaStream_t s) {
   int32_t *fb_rows, *fb_count;
   unsigned long long* ncand;
   double* rinv;
@@ -454,19 +456,49 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
   ANCKA_TRY(ws.zeros(&ncand, 1));
   const bool use_candidates = cand_val != nullptr;
   if (use_candidates) {
+    const bool fp8 = list_prec == ANCKA_PREC_FP8;
     float* fb_thr = nullptr;
-    if (collect_prec == ANCKA_PREC_BF16) ANCKA_TRY(ws.alloc(&fb_thr, (size_t)n));
+    if (collect_prec == ANCKA_PREC_BF16 && !fp8) ANCKA_TRY(ws.alloc(&fb_thr, (size_t)n));
     k_rerank<<<(unsigned)ceil_div(n, kWarps), kWarps * 32, 0, s>>>(
-        X, n, d, K, pr.err, pr.err_max, acc_coef, rinv, cand_val, cand_idx, lists, out_idx, out_sim,
-        fb_rows, fb_thr, fb_count, ncand);
+        X, nullptr, n, d, K, fp8 ? pr.err8 : pr.err, fp8 ? pr.err8_max : pr.err_max, acc_coef, rinv, cand_val,
+        cand_idx, lists, out_idx, out_sim, fb_rows, fb_thr, fb_count, ncand);
     ANCKA_LAUNCHED();
-    int32_t* ex_rows = fb_rows;
-    int32_t* ex_count = fb_count;
+    int32_t* cl_rows = fb_rows;   // rows for the collect pass, their count and thresholds
+    int32_t* cl_count = fb_count;
+    float* cl_thr = fb_thr;
+    if (fp8) {
+      // rows the FP8 lists could not certify: BF16 lists for those rows, then
+      // the BF16 certificate; what it cannot settle goes to the collect pass
+      int32_t nf8 = 0;
+      ANCKA_CUDA(cudaMemcpyAsync(&nf8, fb_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaStreamSynchronize(s));
+      ANCKA_TRY(ws.alloc(&cl_rows, (size_t)(nf8 > 0 ? nf8 : 1)));
+      ANCKA_TRY(ws.zeros(&cl_count, 1));
+      ANCKA_TRY(ws.alloc(&cl_thr, (size_t)(nf8 > 0 ? nf8 : 1)));
+      if (nf8 > 0) {
+        int32_t* terr;
+        ANCKA_TRY(ws.zeros(&terr, 1));
+        ANCKA_TRY(knn_list_gathered_bf16(ws, pr, n, fb_rows, nf8, cand_val, cand_idx, terr, s));
+        k_rerank<<<(unsigned)ceil_div(nf8, kWarps), kWarps * 32, 0, s>>>(
+            X, fb_rows, nf8, d, K, pr.err, pr.err_max, acc_bf16, rinv, cand_val, cand_idx, 2, out_idx, out_sim,
+            cl_rows, cl_thr, cl_count, ncand);
+        ANCKA_LAUNCHED();
+        int32_t hterr = 0;
+        ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        ANCKA_CUDA(cudaStreamSynchronize(s));
+        if (hterr) {
+          set_error("tensor-core BF16 list pass: a pipeline wait expired (role %d)", hterr);
+          return ANCKA_ERR_TIMEOUT;
+        }
+      }
+    }
+    int32_t* ex_rows = cl_rows;
+    int32_t* ex_count = cl_count;
     if (collect_prec == ANCKA_PREC_BF16) {
       // flagged rows: collect every key above the row's certified threshold
       // with the tensor-core contraction, then re-rank those exactly
       int32_t nf = 0;
-      ANCKA_CUDA(cudaMemcpyAsync(&nf, fb_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ANCKA_CUDA(cudaMemcpyAsync(&nf, cl_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       ANCKA_CUDA(cudaStreamSynchronize(s));
       ANCKA_TRY(ws.zeros(&ex_count, 1));
       ANCKA_TRY(ws.alloc(&ex_rows, (size_t)(nf > 0 ? nf : 1)));
@@ -476,9 +508,9 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
         ANCKA_TRY(ws.zeros(&cnt, (size_t)nf));
         ANCKA_TRY(ws.alloc(&buf, (size_t)nf * kCap));
         ANCKA_TRY(ws.zeros(&terr, 1));
-        ANCKA_TRY(knn_collect_bf16(ws, pr, n, fb_rows, nf, fb_thr, cnt, buf, kCap, terr, s));
+        ANCKA_TRY(knn_collect_bf16(ws, pr, n, cl_rows, nf, cl_thr, cnt, buf, kCap, terr, s));
         k_rerank_collected<<<(unsigned)ceil_div(nf, kWarps), kWarps * 32, 0, s>>>(
-            X, d, K, rinv, fb_rows, fb_count, cnt, buf, kCap, out_idx, out_sim, ex_rows, ex_count);
+            X, d, K, rinv, cl_rows, cl_count, cnt, buf, kCap, out_idx, out_sim, ex_rows, ex_count);
         ANCKA_LAUNCHED();
         int32_t hterr = 0;
         ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

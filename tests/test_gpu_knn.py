@@ -9,7 +9,7 @@ from tests.parity_util import compare_knn
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32", "bf16"]
+PRECS = ["fp32", "bf16", "fp8"]
 
 
 @pytest.fixture(scope="module")
@@ -35,9 +35,13 @@ def test_knn_random_shapes(ak, prec, n, d, K):
     idx, sim, info = _run(ak, X, K, prec)
     c = compare_knn(X, K, np.arange(n), idx, sim)
     assert c["exact_rows"] + c["near_tie_rows"] == n
-    # within the certified range (K <= 12 for BF16, 16 for FP32) few rows fall back
-    if K <= (12 if prec == "bf16" else 16):
+    # within the certified range (K <= 12 for BF16, 16 for FP32) few rows fall
+    # back; FP8's wider margin leaves most rows to its BF16 second pass, whose
+    # certificate then settles nearly all of them
+    if prec != "fp8" and K <= (12 if prec == "bf16" else 16):
         assert info["knn_fallback_rows"] <= n // 20
+    if prec == "fp8" and K <= 12:
+        assert info["knn_exhaustive_rows"] <= n // 20
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -77,7 +81,9 @@ def test_knn_hypergraph_workload_sampled(ak):
         idx, sim, info = _run(ak, X, 10, prec)
         c = compare_knn(X, 10, rows, idx, sim)
         assert c["exact_rows"] + c["near_tie_rows"] == rows.size
-        assert info["knn_fallback_rows"] < X.shape[0] // 100
+        if prec != "fp8":
+            assert info["knn_fallback_rows"] < X.shape[0] // 100
+        assert info["knn_exhaustive_rows"] < X.shape[0] // 100
 
 
 def test_knn_invalid_arguments(ak):
@@ -107,3 +113,75 @@ def test_knn_collect_pass_dense_rows(ak):
     assert info["knn_exhaustive_rows"] <= max(1, info["knn_fallback_rows"] // 10)
     c = compare_knn(X, 10, np.arange(12000), idx, sim)
     assert c["exact_rows"] + c["near_tie_rows"] == 12000
+
+
+@pytest.mark.parametrize("ordered", [False, True])
+def test_knn_clustered_rows_parity(ak, ordered):
+    """n = 20000 Gaussian mixture; ordered=True sorts the rows by cluster so
+    that each row's neighbours sit in a narrow key range (one 128-key half
+    of a tile holds most of them)."""
+    rng = np.random.default_rng(21)
+    n, d, K = 20000, 96, 10
+    labels = rng.integers(0, 8, n)
+    if ordered:
+        labels = np.sort(labels)
+    X = synth.gaussian_mixture(rng, labels, 8, d, 1.2)
+    idx, sim, info = _run(ak, X, K, "bf16")
+    rows = np.random.default_rng(22).choice(n, 1200, replace=False)
+    c = compare_knn(X, K, rows, idx, sim)
+    assert c["exact_rows"] + c["near_tie_rows"] == rows.size
+    assert info["knn_fallback_rows"] <= n // 20
+
+
+def test_knn_fp8_certified_groups(ak):
+    """Groups of K + 1 near-duplicate rows (cosine ~0.99 inside a group,
+    ~0.25 across): the FP8 margin is far below the gap after the K-th
+    neighbour, so the FP8 lists certify nearly every row themselves."""
+    rng = np.random.default_rng(31)
+    g, K, d = 300, 10, 64
+    centres = rng.standard_normal((g, d))
+    X = (np.repeat(centres, K + 1, axis=0) + 0.05 * rng.standard_normal((g * (K + 1), d))).astype(np.float32)
+    X = X[rng.permutation(X.shape[0])]
+    idx, sim, info = _run(ak, X, K, "fp8")
+    c = compare_knn(X, K, np.arange(X.shape[0]), idx, sim)
+    assert c["exact_rows"] + c["near_tie_rows"] == X.shape[0]
+    assert info["knn_fallback_rows"] <= X.shape[0] // 20
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,d", [(3000, 200), (2600, 130)])
+def test_candidate_error_model(ak, prec, n, d):
+    """The certificate's error model against exact arithmetic on the
+    quantised rows: e_i >= ||q_i - u_i||, |score - q_i.q_j| <= acc |q_i||q_j|
+    for every kept candidate, and every key a list left out scores at most the
+    list's minimum (up to the same bound)."""
+    rng = np.random.default_rng(n + d)
+    labels = rng.integers(0, 6, n)
+    X = synth.gaussian_mixture(rng, labels, 6, d, 1.0)
+    cv, ci, q, err, acc = ak.knn_candidates(torch.as_tensor(X, device="cuda"), prec)
+    torch.cuda.synchronize()
+    cv, ci, q, err = [t.cpu().numpy() for t in (cv, ci, q, err)]
+    q = q.astype(np.float64)
+    U = O.unit_rows(X)
+    assert np.all(np.linalg.norm(q - U, axis=1) <= err.astype(np.float64))
+    G = q @ q.T
+    nq = np.linalg.norm(q, axis=1)
+    half_of = (np.arange(n) % 256) // 128
+    worst = 0.0
+    for i in range(n):
+        for h in range(2):
+            js = ci[i, 16 * h:16 * h + 16]
+            vs = cv[i, 16 * h:16 * h + 16].astype(np.float64)
+            assert np.all(js != i) and np.all(half_of[js[js >= 0]] == h)
+            ok = js >= 0
+            bound = acc * nq[i] * nq[js[ok]]
+            worst = max(worst, float((np.abs(vs[ok] - G[i, js[ok]]) / bound).max()))
+            others = half_of == h
+            others[i] = False
+            others[js[ok]] = False
+            if ok.all() and others.any():
+                assert np.all(G[i, others] <= vs.min() + acc * nq[i] * nq[others]), f"row {i} list {h}"
+            else:
+                assert not others.any(), f"row {i} list {h}: list not full but keys left out"
+    print(f"{prec}: max |score - q.q| / (acc |q||q|) = {worst:.3g} (acc = {acc:.3g})")
+    assert worst <= 1.0
