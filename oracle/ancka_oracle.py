@@ -50,6 +50,28 @@ R13 Q^(0) = [n^{-1/2} 1 | h(Y^(0))] has rank k, not k+1: 1 = sum_c
     non-empty cluster and the column of every empty cluster c become the sign
     vector s_i / sqrt(n), s_i = +1 or -1 from the top bit of
     splitmix64(64 i + c) (Steele, Lea, Flood 2014; Vigna's constants).
+
+Learned warm start (an addition to the paper's method: an MLP predicts the
+initial block instead of InitBCM; no counterpart in the paper):
+W1  features A = [U | P_N U], U the unit rows of X (a zero row stays zero),
+    P_N the topology walk of Eqs. (rw-hg), (rw-ag), (rw-mg) (no KNN part).
+W2  MLP: W = GELU(A W1 + b1) W2 + b2 with GELU(z) = z Phi(z) (Phi the standard
+    normal CDF, erf form).  The two large operands of the first layer (A and
+    W1, and A^T and dZ1 in its weight gradient) are BF16 with FP32
+    accumulation; ``bf16=True`` rounds exactly those operands (round to
+    nearest even), everything else is FP64.
+W3  loss L = k - tr(G^-1 M^T M) + lam ||G/n - I||_F^2 with G = W^T W and
+    M = Q_t^T W for the target's k orthonormal columns Q_t; the first term is
+    k - ||Q_t^T orth(W)||_F^2 for any orthonormal basis orth(W) of span(W)
+    (CholeskyQR's included), so L depends on W only through its span and
+    scale; dL/dW = -2 (Q_t M G^-1 - W S) + (4 lam / n) W (G/n - I) with
+    S = G^-1 M^T M G^-1.
+W4  Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected), one full-graph
+    step per training graph in a fixed order, epochs repeated.
+W5  the initial weights are inputs (drawn by the seeded input generators).
+W6  the warm block is Q^(0) = QR([n^-1/2 1 | W]) with diag(R) > 0 and
+    Y^(0) = Discretize(Q^(0)[:, 1:]); it replaces InitBCM's start only when
+    Phi(Y^(0)) is not higher than InitBCM's (otherwise InitBCM is the fallback).
 """
 from __future__ import annotations
 
@@ -424,11 +446,13 @@ def build_walk(topo_dict, X, K, beta, knn=None):
     return WalkOperator(topo, P_K, b), idx
 
 
-def ancka(topo_dict, X, params=None, knn=None, init_labels=None):
+def ancka(topo_dict, X, params=None, knn=None, init_labels=None, warm=None, warm_bf16=True):
     """Algorithm 4 (ANCKA) in FP64 with the fixed schedule of reading R9.
 
-    Returns a dict with the labels, the final Q (n x (k+1)), the InitBCM
-    labels, the phi trace and the Discretize inner-iteration counts.
+    ``warm``: MLP weights (W1, b1, W2, b2) for the learned warm start of
+    readings W1-W6.  Returns a dict with the labels, the final Q
+    (n x (k+1)), the InitBCM labels, the phi trace and the Discretize
+    inner-iteration counts.
     """
     p = dict(DEFAULTS)
     if params:
@@ -443,6 +467,14 @@ def ancka(topo_dict, X, params=None, knn=None, init_labels=None):
     Y_best = y0.copy()
     phi_best = cal_mhc(P, y0, k, alpha, gamma)       # reading R8
     Q = initial_block(y0, k)
+    warm_used = False
+    if warm is not None:                              # reading W6
+        Wm, _ = warm_forward(warm_features(P.topo, X), warm, warm_bf16)
+        Q_w = warm_initial_block(Wm)
+        y_w = discretize(Q_w[:, 1:], p["disc_max_iter"])
+        phi_w = cal_mhc(P, y_w, k, alpha, gamma)
+        if phi_w <= phi_best:
+            Q, y0, Y_best, phi_best, warm_used = Q_w, y_w, y_w.copy(), phi_w, True
     phis = [phi_best]
     disc_iters = []
     taken = []
@@ -468,7 +500,113 @@ def ancka(topo_dict, X, params=None, knn=None, init_labels=None):
                     break
     return dict(labels=Y_best.astype(np.int64), Q=Q, init_labels=y0, centres=Vc,
                 phi=np.array(phis), phi_best=phi_best, disc_iters=disc_iters,
-                taken=taken, iters=t_run, knn_idx=idx)
+                taken=taken, iters=t_run, knn_idx=idx, warm_used=warm_used)
+
+
+# ----------------------------------------------------------------------------
+# learned warm start (readings W1-W6)
+# ----------------------------------------------------------------------------
+def round_bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(F64)
+
+
+def warm_features(topo: Topology, X):
+    """Reading W1: A = [U | P_N U]."""
+    U = unit_rows(X)
+    return np.hstack([U, topo.apply(U)])
+
+
+def gelu(z):
+    from scipy.special import erf
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def warm_forward(A, prm, bf16=False):
+    """Reading W2: returns W and the cache (Z1, H) for the backward pass."""
+    Ab = round_bf16(A) if bf16 else np.asarray(A, F64)
+    W1 = round_bf16(prm["W1"]) if bf16 else prm["W1"]
+    Z1 = Ab @ W1 + prm["b1"]
+    H = gelu(Z1)
+    W = H @ prm["W2"] + prm["b2"]
+    return W, (Z1, H)
+
+
+def warm_loss(W, Qt, lam):
+    """Reading W3."""
+    n, k = W.shape
+    G = W.T @ W
+    M = Qt.T @ W
+    f = np.trace(np.linalg.solve(G, M.T @ M))
+    return float(k - f + lam * np.sum((G / n - np.eye(k)) ** 2))
+
+
+def warm_loss_grad(W, Qt, lam):
+    """Reading W3: dL/dW in closed form."""
+    n, k = W.shape
+    G = W.T @ W
+    M = Qt.T @ W
+    Gi = np.linalg.inv(G)
+    S = Gi @ M.T @ M @ Gi
+    return -2.0 * (Qt @ M @ Gi - W @ S) + (4.0 * lam / n) * W @ (G / n - np.eye(k))
+
+
+def warm_backward(A, prm, cache, dW, bf16=False):
+    """Gradients of the loss w.r.t. W1, b1, W2, b2 given dL/dW."""
+    Z1, H = cache
+    g = {"W2": H.T @ dW, "b2": dW.sum(axis=0)}
+    dH = dW @ prm["W2"].T
+    dZ1 = dH * gelu_grad(Z1)
+    g["b1"] = dZ1.sum(axis=0)
+    if bf16:
+        g["W1"] = round_bf16(A).T @ round_bf16(dZ1)
+    else:
+        g["W1"] = np.asarray(A, F64).T @ dZ1
+    return g
+
+
+def adam_step(prm, grads, state, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """Reading W4: one bias-corrected Adam update of every tensor in prm."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    out = {}
+    for name, p in prm.items():
+        m = state.setdefault("m_" + name, np.zeros_like(p))
+        v = state.setdefault("v_" + name, np.zeros_like(p))
+        m[...] = b1 * m + (1.0 - b1) * grads[name]
+        v[...] = b2 * v + (1.0 - b2) * grads[name] ** 2
+        mh = m / (1.0 - b1 ** t)
+        vh = v / (1.0 - b2 ** t)
+        out[name] = p - lr * mh / (np.sqrt(vh) + eps)
+    return out
+
+
+def warm_train(data, prm, epochs, lr=1e-3, lam=1e-3, bf16=False):
+    """Reading W4: data = [(A_g, Qt_g)], one step per graph per epoch."""
+    prm = {k_: np.array(v, F64) for k_, v in prm.items()}
+    state, losses = {}, []
+    for _ in range(epochs):
+        for A, Qt in data:
+            W, cache = warm_forward(A, prm, bf16)
+            losses.append(warm_loss(W, Qt, lam))
+            grads = warm_backward(A, prm, cache, warm_loss_grad(W, Qt, lam), bf16)
+            prm = adam_step(prm, grads, state, lr)
+    return prm, losses
+
+
+def warm_initial_block(W):
+    """Reading W6: Q^(0) = QR([n^-1/2 1 | W]) with diag(R) > 0."""
+    n = W.shape[0]
+    Q, _ = qr_pos(np.hstack([np.full((n, 1), 1.0 / np.sqrt(n)), W]))
+    return Q
 
 
 # ----------------------------------------------------------------------------

@@ -320,3 +320,13 @@ def config_large_dcsbm(seed: int = 0, n: int = 2_400_000, m_edges: int = 60_000_
                        k: int = 47, d: int = 100) -> dict:
     """Large DC-SBM graph: n=2.4e6, 6e7 edges, k=47 Zipf-sized clusters, d=100."""
     return dcsbm_graph(n, k, m_edges, d, 1.5, seed)
+
+
+def warm_init(seed: int, d_in: int, hidden: int, k: int) -> dict:
+    """Seeded initial weights of the warm-start MLP (d_in -> hidden -> k):
+    W1 ~ N(0, 2/d_in), W2 ~ N(0, 1/hidden), zero biases; float32."""
+    rng = np.random.default_rng(seed)
+    return dict(W1=(rng.standard_normal((d_in, hidden)) * np.sqrt(2.0 / d_in)).astype(np.float32),
+                b1=np.zeros(hidden, np.float32),
+                W2=(rng.standard_normal((hidden, k)) * np.sqrt(1.0 / hidden)).astype(np.float32),
+                b2=np.zeros(k, np.float32))

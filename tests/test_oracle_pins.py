@@ -393,3 +393,24 @@ def test_initial_block_full_rank_with_empty_cluster():
     Q1 = O.initial_block(full, 3)
     assert np.linalg.matrix_rank(Q1) == 4
     assert np.allclose(Q1[:, 1:3], O.h_norm(full, 3)[:, :2])
+
+
+def test_paper_mode_stop_rules(monkeypatch):
+    """Alg. 4 checks Eq. tcond-1 / tcond-2 after keep-best at each t with
+    t mod tau = 0: a threshold every ||Q(t) - Q(t-1)|| meets stops at t = tau;
+    with eps_Q = 0, three strictly rising phi values (phi(Y0) counted) stop
+    the loop at their third check, and a flat phi never does (t runs to T)."""
+    g = synth.cliques_closed_form(4, 30, 0)
+    p = dict(k=4, K=10, T=40, tau=5, early_stop=True, eps_Q=10.0)
+    assert O.ancka(g, g["X"], p)["iters"] == 5
+    seq = iter([0.10, 0.20, 0.30, 0.40, 0.50, 0.60, 0.70, 0.80, 0.90])
+    monkeypatch.setattr(O, "cal_mhc", lambda *a, **kw: next(seq))
+    r = O.ancka(g, g["X"], dict(p, eps_Q=0.0))
+    assert r["iters"] == 10 and list(r["phi"]) == [0.10, 0.20, 0.30]
+    seq2 = iter([0.30, 0.20, 0.25, 0.10, 0.15, 0.40, 0.50, 0.60, 0.70])
+    monkeypatch.setattr(O, "cal_mhc", lambda *a, **kw: next(seq2))
+    # 0.30 0.20 0.25 0.10 0.15 0.40: the first strictly rising triple ends at t = 25
+    assert O.ancka(g, g["X"], dict(p, eps_Q=0.0))["iters"] == 25
+    monkeypatch.setattr(O, "cal_mhc", lambda *a, **kw: 0.5)
+    r = O.ancka(g, g["X"], dict(p, eps_Q=0.0))
+    assert r["iters"] == 40 and len(r["phi"]) == 9
