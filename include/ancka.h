@@ -86,6 +86,22 @@ typedef struct {
   const int32_t* he_nodes;  /* hypergraph: he_ptr[m] */
 } ancka_topology;
 
+/* Learned warm-start MLP (an addition to the paper's method; no counterpart
+ * in the paper): W = GELU(A W1 + b1) W2 + b2 with A = [U | P_N U], U the unit
+ * rows of X and P_N the topology walk of Eqs. rw-hg / rw-ag / rw-mg.  The
+ * first layer runs on the tensor cores with BF16 operands and FP32
+ * accumulation.  All pointers are device FP32, row-major, caller-owned. */
+typedef struct {
+  int32_t d_in;    /* 2 d (d = attribute columns) */
+  int32_t hidden;  /* 256 (the only width this build supports) */
+  int32_t k;       /* outputs: the number of clusters */
+  int32_t pad_;
+  float* W1;       /* d_in x hidden */
+  float* b1;       /* hidden */
+  float* W2;       /* hidden x k */
+  float* b2;       /* k */
+} ancka_warm_model;
+
 /* Parameters of Algorithm 4 (defaults from the method's settings, Section 8.1). */
 typedef struct {
   int32_t k;             /* clusters, 1 <= k <= 64 (default 5) */
@@ -98,9 +114,14 @@ typedef struct {
   int32_t tau;           /* Discretize / CalMHC interval (5) */
   int32_t disc_max_iter; /* Discretize inner iterations (20) */
   int32_t knn_prec;      /* ancka_prec (ANCKA_PREC_BF16) */
-  int32_t init;          /* 0 = InitBCM, 1 = labels in init_labels (device, n int32) */
+  int32_t init;          /* 0 = InitBCM, 1 = labels in init_labels (device, n int32),
+                            2 = learned warm start (warm), InitBCM as the fallback */
   int32_t pad_;
   const int32_t* init_labels;
+  int32_t early_stop;    /* 1: stop by Eq. tcond-1 or Eq. tcond-2 at the Discretize
+                            points (the paper's mode, T = T_a up to 1000); 0: run T (0) */
+  float eps_Q;           /* Eq. tcond-1 threshold on ||Q(t) - Q(t-1)||_F (0.005) */
+  const ancka_warm_model* warm;  /* init = 2: the MLP (device weights) */
 } ancka_params;
 
 /* Optional device outputs (any field may be NULL). */
@@ -136,6 +157,8 @@ typedef struct {
   float ms_contract;           /* the candidate similarity contraction kernel alone */
   float ms_rerank;             /* exact re-rank, certificate and fallback after the contraction */
   float ms_spmm;               /* the T products Z = P Q of the orthogonal iteration (inside ms_iter) */
+  int32_t warm_used;           /* init = 2: 1 if the warm start replaced InitBCM's (lower or equal Phi) */
+  int32_t pad2_;
 } ancka_info;
 
 /* Fill *p with the defaults above. */
@@ -233,6 +256,40 @@ ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq
  * calls that overlap on the GPU race.  Arguments as for ancka_discretize. */
 ancka_status ancka_discretize_noalloc(const float* Qk, int64_t n, int32_t k, int32_t ldq,
                                       int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
+
+/* Learned warm start: one training graph (device pointers).  The target is
+ * ANCKA's own final block: Qt = columns 2..k+1 of Q^(T) (n x k, orthonormal
+ * columns, row stride k), e.g. from ancka_cluster's outputs. */
+typedef struct {
+  const ancka_topology* topo;
+  const float* X;   /* n x d attributes */
+  const float* Qt;  /* n x k target block */
+  int32_t d;
+  int32_t pad_;
+} ancka_warm_graph;
+
+/* Trains the warm-start MLP in place: epochs x n_graphs full-graph steps (graph
+ * order fixed) of Adam (lr; beta 0.9 / 0.999, eps 1e-8) on the loss
+ *   L = k - tr(G^-1 M^T M) + lam ||G/n - I||_F^2,  G = W^T W, M = Qt^T W,
+ * i.e. k - ||Qt^T orth(W)||_F^2 plus a scale penalty; it depends on W only
+ * through span(W) and its scale.  model: initial weights in, trained weights
+ * out (device FP32; d_in = 2d, hidden = 256, k as in the graphs).  losses:
+ * host array of epochs * n_graphs values (the loss before each step), or
+ * NULL.  Every graph needs the same d and k.  ANCKA_ERR_NUMERIC if some
+ * W^T W is singular. */
+ancka_status ancka_warm_train(const ancka_warm_graph* graphs, int32_t n_graphs, int32_t epochs, float lr, float lam,
+                              ancka_warm_model* model, float* losses, void* stream);
+
+/* W = MLP([U | P_N U]) (n x k, device, row stride k) for a topology and its
+ * attributes. */
+ancka_status ancka_warm_predict(const ancka_topology* topo, const float* X, int32_t d, const ancka_warm_model* model,
+                                float* W, void* stream);
+
+/* Diagnostic: the gradients of the training loss for one graph at the given
+ * weights, without updating them (dW1 d_in x 256, db1 256, dW2 256 x k, db2 k,
+ * device), and the loss (host, may be NULL). */
+ancka_status ancka_warm_gradients(const ancka_warm_graph* graph, float lam, const ancka_warm_model* model,
+                                  float* dW1, float* db1, float* dW2, float* db2, double* loss, void* stream);
 
 #ifdef __cplusplus
 }

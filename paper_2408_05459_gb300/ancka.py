@@ -29,12 +29,24 @@ class Topology(ctypes.Structure):
                 ("he_ptr", ctypes.c_void_p), ("he_nodes", ctypes.c_void_p)]
 
 
+class WarmModel(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_int32), ("hidden", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("W2", ctypes.c_void_p), ("b2", ctypes.c_void_p)]
+
+
+class WarmGraph(ctypes.Structure):
+    _fields_ = [("topo", ctypes.POINTER(Topology)), ("X", ctypes.c_void_p), ("Qt", ctypes.c_void_p),
+                ("d", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("K", ctypes.c_int32), ("alpha", ctypes.c_float),
                 ("beta", ctypes.c_float), ("T", ctypes.c_int32), ("gamma", ctypes.c_int32),
                 ("T_i", ctypes.c_int32), ("tau", ctypes.c_int32), ("disc_max_iter", ctypes.c_int32),
                 ("knn_prec", ctypes.c_int32), ("init", ctypes.c_int32), ("pad_", ctypes.c_int32),
-                ("init_labels", ctypes.c_void_p)]
+                ("init_labels", ctypes.c_void_p), ("early_stop", ctypes.c_int32), ("eps_Q", ctypes.c_float),
+                ("warm", ctypes.POINTER(WarmModel))]
 
 
 class Outputs(ctypes.Structure):
@@ -52,7 +64,8 @@ class Info(ctypes.Structure):
                 ("ms_knn", ctypes.c_float), ("ms_build", ctypes.c_float), ("ms_init", ctypes.c_float),
                 ("ms_iter", ctypes.c_float), ("ms_disc", ctypes.c_float), ("ms_mhc", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("ms_contract", ctypes.c_float),
-                ("ms_rerank", ctypes.c_float), ("ms_spmm", ctypes.c_float)]
+                ("ms_rerank", ctypes.c_float), ("ms_spmm", ctypes.c_float),
+                ("warm_used", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
         n = self.n_phi
@@ -63,7 +76,7 @@ class Info(ctypes.Structure):
                     ms_knn=self.ms_knn, ms_build=self.ms_build, ms_init=self.ms_init, ms_iter=self.ms_iter,
                     ms_disc=self.ms_disc, ms_mhc=self.ms_mhc, ms_total=self.ms_total,
                     ms_contract=self.ms_contract, ms_rerank=self.ms_rerank,
-                    ms_spmm=self.ms_spmm)
+                    ms_spmm=self.ms_spmm, warm_used=self.warm_used)
 
 
 class AnckaError(RuntimeError):
@@ -106,6 +119,14 @@ def load(path: str = LIB_PATH):
     L.ancka_knn.restype = ctypes.c_int
     L.ancka_knn_candidates.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
     L.ancka_knn_candidates.restype = ctypes.c_int
+    L.ancka_warm_predict.argtypes = [ctypes.POINTER(Topology), vp, i32, ctypes.POINTER(WarmModel), vp, vp]
+    L.ancka_warm_predict.restype = ctypes.c_int
+    L.ancka_warm_train.argtypes = [ctypes.POINTER(WarmGraph), i32, i32, ctypes.c_float, ctypes.c_float,
+                                   ctypes.POINTER(WarmModel), ctypes.POINTER(ctypes.c_float), vp]
+    L.ancka_warm_train.restype = ctypes.c_int
+    L.ancka_warm_gradients.argtypes = [ctypes.POINTER(WarmGraph), ctypes.c_float, ctypes.POINTER(WarmModel),
+                                       vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.ancka_warm_gradients.restype = ctypes.c_int
     L.ancka_cluster.argtypes = [ctypes.POINTER(Topology), vp, i32, ctypes.POINTER(Params), vp,
                                 ctypes.POINTER(Outputs), ctypes.POINTER(Info), vp]
     L.ancka_cluster.restype = ctypes.c_int
@@ -229,15 +250,85 @@ def _topology_struct(t: dict) -> Topology:
     return s
 
 
+def warm_model(weights: dict) -> tuple:
+    """ctypes model over device tensors W1 (d_in x 256), b1, W2 (256 x k), b2
+    (float32, contiguous; kept referenced by the caller)."""
+    W1, b1, W2, b2 = (weights[k_] for k_ in ("W1", "b1", "W2", "b2"))
+    for t in (W1, b1, W2, b2):
+        assert t.is_cuda and t.is_contiguous() and t.dtype.is_floating_point and t.element_size() == 4
+    m = WarmModel(d_in=W1.shape[0], hidden=W1.shape[1], k=W2.shape[1], W1=W1.data_ptr(), b1=b1.data_ptr(),
+                  W2=W2.data_ptr(), b2=b2.data_ptr())
+    return m
+
+
+def warm_predict(topo_dev: dict, X, weights: dict):
+    """W = MLP([U | P_N U]) (n x k) of the learned warm start."""
+    import torch
+    n, d = X.shape
+    m = warm_model(weights)
+    W = torch.empty((n, m.k), dtype=torch.float32, device=X.device)
+    ts = _topology_struct(topo_dev)
+    st = load().ancka_warm_predict(ctypes.byref(ts), _ptr(X), d, ctypes.byref(m), _ptr(W), _stream())
+    _check("ancka_warm_predict", st)
+    return W
+
+
+def _warm_graphs(items):
+    keep, arr = [], (WarmGraph * len(items))()
+    for q, (topo_dev, X, Qt) in enumerate(items):
+        assert Qt.is_cuda and Qt.is_contiguous() and Qt.dtype == X.dtype
+        ts = _topology_struct(topo_dev)
+        keep.append(ts)
+        arr[q].topo = ctypes.pointer(ts)
+        arr[q].X = X.data_ptr()
+        arr[q].Qt = Qt.data_ptr()
+        arr[q].d = X.shape[1]
+    return arr, keep
+
+
+def warm_train(items, weights: dict, epochs: int, lr: float = 1e-3, lam: float = 1e-3):
+    """Trains the warm-start MLP in place on [(topo_dev, X, Qt)]; returns the
+    loss before every step (epochs x graphs, graph order fixed)."""
+    arr, keep = _warm_graphs(items)
+    m = warm_model(weights)
+    losses = (ctypes.c_float * (epochs * len(items)))()
+    st = load().ancka_warm_train(arr, len(items), epochs, lr, lam, ctypes.byref(m), losses, _stream())
+    _check("ancka_warm_train", st)
+    return np.array(losses[:], np.float64)
+
+
+def warm_gradients(topo_dev: dict, X, Qt, weights: dict, lam: float = 1e-3):
+    """Gradients of the warm-start loss for one graph (no update) and the loss."""
+    import torch
+    arr, keep = _warm_graphs([(topo_dev, X, Qt)])
+    m = warm_model(weights)
+    dev = X.device
+    g = dict(W1=torch.empty((m.d_in, 256), dtype=torch.float32, device=dev),
+             b1=torch.empty(256, dtype=torch.float32, device=dev),
+             W2=torch.empty((256, m.k), dtype=torch.float32, device=dev),
+             b2=torch.empty(m.k, dtype=torch.float32, device=dev))
+    loss = ctypes.c_double(0.0)
+    st = load().ancka_warm_gradients(arr, lam, ctypes.byref(m), _ptr(g["W1"]), _ptr(g["b1"]), _ptr(g["W2"]),
+                                     _ptr(g["b2"]), ctypes.byref(loss), _stream())
+    _check("ancka_warm_gradients", st)
+    return g, loss.value
+
+
 def cluster(topo_dev: dict, X, params: Params | None = None, knn_lists=None, want_Q=False,
-            want_init=False, want_knn=False, with_info=True, init_labels=None):
-    """Algorithm 4 on device buffers; returns (labels, extras dict, info dict)."""
+            want_init=False, want_knn=False, with_info=True, init_labels=None, warm=None):
+    """Algorithm 4 on device buffers; returns (labels, extras dict, info dict).
+    warm: device weights of the warm-start MLP (init = 2, InitBCM fallback)."""
     import torch
     n, d = X.shape
     p = params or default_params()
     if init_labels is not None:
         p.init = 1
         p.init_labels = init_labels.data_ptr()
+    wm = None
+    if warm is not None:
+        wm = warm_model(warm)
+        p.init = 2
+        p.warm = ctypes.pointer(wm)
     labels = torch.empty(n, dtype=torch.int32, device=X.device)
     extras = {}
     o = Outputs()

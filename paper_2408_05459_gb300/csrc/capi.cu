@@ -7,6 +7,7 @@
 #include <cuda_fp8.h>
 
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
@@ -262,8 +263,42 @@ ancka_status validate_params(const ancka_params* p, int64_t n) {
   ANCKA_REQUIRE(p->T >= 1 && p->tau >= 1, "T and tau must be >= 1");
   ANCKA_REQUIRE(p->gamma >= 0 && p->T_i >= 0, "gamma and T_i must be >= 0");
   ANCKA_REQUIRE(p->disc_max_iter >= 1 && p->disc_max_iter <= 1000, "disc_max_iter out of range");
-  ANCKA_REQUIRE(p->T / p->tau + 2 <= ANCKA_MAX_TRACE, "T / tau too large for the trace");
-  ANCKA_REQUIRE(p->init == 0 || (p->init == 1 && p->init_labels), "init must be 0 or 1 with init_labels");
+  ANCKA_REQUIRE(p->T <= 100000, "T must be <= 100000");
+  ANCKA_REQUIRE(p->init == 0 || (p->init == 1 && p->init_labels) || (p->init == 2 && p->warm),
+                "init must be 0, 1 with init_labels, or 2 with a warm model");
+  ANCKA_REQUIRE(p->early_stop == 0 || (p->early_stop == 1 && p->eps_Q >= 0.f), "early_stop must be 0 or 1, eps_Q >= 0");
+  return ANCKA_OK;
+}
+
+ancka_status validate_warm(const ancka_warm_model* m, int32_t d, int32_t k) {
+  ANCKA_REQUIRE(m != nullptr, "warm model is NULL");
+  ANCKA_REQUIRE(m->W1 && m->b1 && m->W2 && m->b2, "warm model has NULL weights");
+  ANCKA_REQUIRE(m->hidden == 256, "warm model: hidden must be 256 (got %d)", m->hidden);
+  ANCKA_REQUIRE(m->d_in == 2 * d, "warm model: d_in = %d must be 2 d = %d", m->d_in, 2 * d);
+  ANCKA_REQUIRE(m->k == k && k >= 1 && k <= 64, "warm model: k = %d must equal the clusters %d (<= 64)", m->k, k);
+  return ANCKA_OK;
+}
+
+// W = MLP([U | P_N U]) for the walk's topology (n x k, row stride ldw)
+ancka_status warm_predict_impl(Workspace& ws, const Walk& w, const float* X, int32_t d, const ancka_warm_model* m,
+                               float* W, int ldw, cudaStream_t s) {
+  const int64_t n = w.n;
+  const int kp = warm_kp(d);
+  __nv_bfloat16 *A, *W1t;
+  int32_t* err;
+  ANCKA_TRY(ws.alloc(&A, (size_t)round_up(n, 128) * kp));
+  ANCKA_TRY(ws.alloc(&W1t, (size_t)256 * kp));
+  ANCKA_TRY(ws.zeros(&err, 1));
+  ANCKA_TRY(warm_features(ws, w, X, d, A, nullptr, s));
+  ANCKA_TRY(warm_refresh_w1t(m->W1, m->d_in, kp, W1t, s));
+  ANCKA_TRY(warm_forward(ws, A, n, kp, W1t, m->b1, m->W2, m->b2, m->k, W, ldw, nullptr, nullptr, err, s));
+  int32_t he = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&he, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (he) {
+    set_error("warm-start GEMM: a pipeline wait expired (role %d)", he);
+    return ANCKA_ERR_TIMEOUT;
+  }
   return ANCKA_OK;
 }
 
@@ -356,12 +391,20 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       if (st == ANCKA_OK) st = ws.zeros(&tr.flags_dev, 1);
       if (st == ANCKA_OK) st = ws.zeros(&tr.phi_best_dev, 1);
     }
+    float* warmW = nullptr;
+    const int ldwarm = p->k;
+    if (st == ANCKA_OK && p->init == 2) {
+      Phase ph(tp, s, 2);
+      st = validate_warm(p->warm, d, p->k);
+      if (st == ANCKA_OK) st = ws.alloc(&warmW, (size_t)n * ldwarm);
+      if (st == ANCKA_OK) st = warm_predict_impl(ws, w, X, d, p->warm, warmW, ldwarm, s);
+    }
     if (st == ANCKA_OK) {
       tr.events = tp ? &timer.ev : nullptr;
       tr.phases = tp ? &timer.ph : nullptr;
-      IterCfg cfg{p->k, p->T, p->gamma, p->T_i, p->tau, p->disc_max_iter, p->alpha};
-      st = run_ancka(ws, w, cfg, p->init == 1 ? p->init_labels : nullptr, labels, out ? out->Q : nullptr,
-                     out ? out->init_labels : nullptr, &tr, s);
+      IterCfg cfg{p->k, p->T, p->gamma, p->T_i, p->tau, p->disc_max_iter, p->alpha, p->early_stop, p->eps_Q};
+      st = run_ancka(ws, w, cfg, p->init == 1 ? p->init_labels : nullptr, warmW, ldwarm, labels,
+                     out ? out->Q : nullptr, out ? out->init_labels : nullptr, &tr, s);
     }
     if (info) cudaEventRecord(t1, s);
     if (info && (st == ANCKA_OK || st == ANCKA_ERR_NUMERIC)) {
@@ -374,7 +417,8 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       cudaError_t e = cudaStreamSynchronize(s);
       if (e != cudaSuccess && st == ANCKA_OK) st = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
       info->n_phi = tr.n_phi;
-      info->iters_run = p->T;
+      info->iters_run = tr.iters_run;
+      info->warm_used = tr.warm_used;
       info->knn_candidates = ncand;
       info->knn_fallback_rows = nfb;
       info->knn_exhaustive_rows = nex;
@@ -442,6 +486,9 @@ void ancka_params_default(ancka_params* p) {
   p->knn_prec = ANCKA_PREC_BF16;
   p->init = 0;
   p->init_labels = nullptr;
+  p->early_stop = 0;
+  p->eps_Q = 0.005f;
+  p->warm = nullptr;
 }
 
 const char* ancka_status_str(ancka_status s) {
@@ -653,6 +700,185 @@ ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq
     }
   }
   return st;
+}
+
+
+ancka_status ancka_warm_predict(const ancka_topology* topo, const float* X, int32_t d, const ancka_warm_model* model,
+                                float* W, void* stream) {
+  using namespace ancka;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_TRY(validate_topology(topo));
+  ANCKA_REQUIRE(X && W && d >= 1 && d <= 4096, "bad X / W / d");
+  ANCKA_REQUIRE(model != nullptr, "warm model is NULL");
+  ANCKA_TRY(validate_warm(model, d, model->k));
+  Workspace ws(s);
+  Walk w;
+  ANCKA_TRY(build_topology(ws, *topo, &w, s));
+  return warm_predict_impl(ws, w, X, d, model, W, model->k, s);
+}
+
+namespace {
+struct WarmBuffers {
+  float *mW1, *vW1, *mb1, *vb1, *mW2, *vW2, *mb2, *vb2;
+  __nv_bfloat16* W1t;
+  double* loss;
+  int32_t *status, *err;
+};
+
+ancka_status warm_buffers(ancka::Workspace& ws, int d_in, int kp, int k, int steps, WarmBuffers* b) {
+  using namespace ancka;
+  ANCKA_TRY(ws.zeros(&b->mW1, (size_t)d_in * 256));
+  ANCKA_TRY(ws.zeros(&b->vW1, (size_t)d_in * 256));
+  ANCKA_TRY(ws.zeros(&b->mb1, 256));
+  ANCKA_TRY(ws.zeros(&b->vb1, 256));
+  ANCKA_TRY(ws.zeros(&b->mW2, (size_t)256 * k));
+  ANCKA_TRY(ws.zeros(&b->vW2, (size_t)256 * k));
+  ANCKA_TRY(ws.zeros(&b->mb2, (size_t)k));
+  ANCKA_TRY(ws.zeros(&b->vb2, (size_t)k));
+  ANCKA_TRY(ws.alloc(&b->W1t, (size_t)256 * kp));
+  ANCKA_TRY(ws.zeros(&b->loss, (size_t)(steps > 0 ? steps : 1)));
+  ANCKA_TRY(ws.zeros(&b->status, 1));
+  ANCKA_TRY(ws.zeros(&b->err, 1));
+  return ANCKA_OK;
+}
+
+struct WarmGraphDev {
+  int64_t n;
+  __nv_bfloat16 *A, *At;
+  const float* Qt;
+};
+
+ancka_status warm_graph_setup(ancka::Workspace& ws, const ancka_warm_graph& g, int d, int k, WarmGraphDev* o,
+                              cudaStream_t s) {
+  using namespace ancka;
+  ANCKA_REQUIRE(g.topo && g.X && g.Qt, "warm graph with NULL topology, X or Qt");
+  ANCKA_REQUIRE(g.d == d, "every warm graph must have d = %d", d);
+  ANCKA_TRY(validate_topology(g.topo));
+  ANCKA_REQUIRE(g.topo->n >= k + 1, "warm graph smaller than k + 1 nodes");
+  Walk w;
+  ANCKA_TRY(build_topology(ws, *g.topo, &w, s));
+  const int kp = warm_kp(d);
+  o->n = w.n;
+  ANCKA_TRY(ws.alloc(&o->A, (size_t)round_up(w.n, 128) * kp));
+  ANCKA_TRY(ws.alloc(&o->At, (size_t)round_up(kp, 128) * round_up(w.n, 64)));
+  ANCKA_TRY(warm_features(ws, w, g.X, d, o->A, o->At, s));
+  o->Qt = g.Qt;
+  return ANCKA_OK;
+}
+
+ancka_status warm_step_args(const WarmGraphDev& g, const ancka_warm_model* m, int kp, const WarmBuffers& b, float lr,
+                            float lam, int t, double* loss_dev, const ancka::WarmGrads* grads,
+                            ancka::WarmStepArgs* a) {
+  a->n = g.n;
+  a->k = m->k;
+  a->d_in = m->d_in;
+  a->kp = kp;
+  a->A = g.A;
+  a->At = g.At;
+  a->Qt = g.Qt;
+  a->ldq = m->k;
+  a->W1 = m->W1;
+  a->b1 = m->b1;
+  a->W2 = m->W2;
+  a->b2 = m->b2;
+  a->W1t = b.W1t;
+  a->mW1 = b.mW1;
+  a->vW1 = b.vW1;
+  a->mb1 = b.mb1;
+  a->vb1 = b.vb1;
+  a->mW2 = b.mW2;
+  a->vW2 = b.vW2;
+  a->mb2 = b.mb2;
+  a->vb2 = b.vb2;
+  a->lr = lr;
+  a->lam = lam;
+  a->t = t;
+  a->loss_dev = loss_dev;
+  a->status = b.status;
+  a->err = b.err;
+  a->grads = grads;
+  return ANCKA_OK;
+}
+
+ancka_status warm_check(const WarmBuffers& b, cudaStream_t s) {
+  using namespace ancka;
+  int32_t h[2] = {0, 0};
+  ANCKA_CUDA(cudaMemcpyAsync(&h[0], b.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaMemcpyAsync(&h[1], b.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  if (h[0]) {
+    set_error("warm-start GEMM: a pipeline wait expired (role %d)", h[0]);
+    return ANCKA_ERR_TIMEOUT;
+  }
+  if (h[1]) {
+    set_error("warm start: W^T W is singular");
+    return ANCKA_ERR_NUMERIC;
+  }
+  return ANCKA_OK;
+}
+}  // namespace
+
+ancka_status ancka_warm_train(const ancka_warm_graph* graphs, int32_t n_graphs, int32_t epochs, float lr, float lam,
+                              ancka_warm_model* model, float* losses, void* stream) {
+  using namespace ancka;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_REQUIRE(graphs && n_graphs >= 1 && epochs >= 1 && epochs <= 100000, "bad graphs / epochs");
+  ANCKA_REQUIRE(lr >= 0.f && lam >= 0.f, "lr and lam must be >= 0");
+  ANCKA_REQUIRE(model != nullptr, "warm model is NULL");
+  const int d = graphs[0].d;
+  ANCKA_TRY(validate_warm(model, d, model->k));
+  const int kp = warm_kp(d);
+  Workspace ws(s);
+  std::vector<WarmGraphDev> gd((size_t)n_graphs);
+  for (int g = 0; g < n_graphs; ++g) ANCKA_TRY(warm_graph_setup(ws, graphs[g], d, model->k, &gd[(size_t)g], s));
+  const int steps = epochs * n_graphs;
+  WarmBuffers b;
+  ANCKA_TRY(warm_buffers(ws, model->d_in, kp, model->k, steps, &b));
+  ANCKA_TRY(warm_refresh_w1t(model->W1, model->d_in, kp, b.W1t, s));
+  for (int e = 0; e < epochs; ++e)
+    for (int g = 0; g < n_graphs; ++g) {
+      const int t = e * n_graphs + g;
+      WarmStepArgs a;
+      warm_step_args(gd[(size_t)g], model, kp, b, lr, lam, t + 1, b.loss + t, nullptr, &a);
+      ANCKA_TRY(warm_train_step(ws, a, s));
+    }
+  ANCKA_TRY(warm_check(b, s));
+  if (losses) {
+    std::vector<double> h((size_t)steps);
+    ANCKA_CUDA(cudaMemcpyAsync(h.data(), b.loss, sizeof(double) * steps, cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    for (int t = 0; t < steps; ++t) losses[t] = (float)h[(size_t)t];
+  }
+  return ANCKA_OK;
+}
+
+ancka_status ancka_warm_gradients(const ancka_warm_graph* graph, float lam, const ancka_warm_model* model,
+                                  float* dW1, float* db1, float* dW2, float* db2, double* loss, void* stream) {
+  using namespace ancka;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_REQUIRE(graph && model && dW1 && db1 && dW2 && db2, "NULL argument");
+  ANCKA_TRY(validate_warm(model, graph->d, model->k));
+  const int kp = warm_kp(graph->d);
+  Workspace ws(s);
+  WarmGraphDev g;
+  ANCKA_TRY(warm_graph_setup(ws, *graph, graph->d, model->k, &g, s));
+  WarmBuffers b;
+  ANCKA_TRY(warm_buffers(ws, model->d_in, kp, model->k, 1, &b));
+  ANCKA_TRY(warm_refresh_w1t(model->W1, model->d_in, kp, b.W1t, s));
+  // lr = 0: the step leaves the weights unchanged (its Adam moments are scratch)
+  const WarmGrads gr{dW1, db1, dW2, db2};
+  WarmStepArgs a;
+  warm_step_args(g, model, kp, b, 0.f, lam, 1, b.loss, &gr, &a);
+  ANCKA_TRY(warm_train_step(ws, a, s));
+  ANCKA_TRY(warm_check(b, s));
+  if (loss) {
+    ANCKA_CUDA(cudaMemcpyAsync(loss, b.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+  }
+  return ANCKA_OK;
 }
 
 }  // extern "C"

@@ -246,6 +246,8 @@ ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* 
 struct IterCfg {
   int32_t k, T, gamma, T_i, tau, disc_max_iter;
   float alpha;
+  int32_t early_stop;  // Eq. tcond-1 / tcond-2 checks (paper mode)
+  float eps_Q;         // Eq. tcond-1 threshold
 };
 struct IterTrace {
   double* phi_dev;         // device [ANCKA_MAX_TRACE]
@@ -254,12 +256,56 @@ struct IterTrace {
   int32_t* flags_dev;      // device [1]
   double* phi_best_dev;    // device [1]
   int n_phi;
+  int iters_run;           // orthogonal iterations executed
+  int warm_used;           // 1 if the learned warm start replaced InitBCM's
   std::vector<cudaEvent_t>* events;  // (phase, start, stop) triples
   std::vector<int>* phases;
 };
+// warm_W: n x k block predicted by the warm-start MLP (row stride ldw), or null
 ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& c, const int32_t* init_labels,
-                       int32_t* labels_out, float* Q_out, int32_t* init_out, IterTrace* tr,
-                       cudaStream_t s);
+                       const float* warm_W, int ldw, int32_t* labels_out, float* Q_out, int32_t* init_out,
+                       IterTrace* tr, cudaStream_t s);
+// out = P_N U (topology walk only) for an n x ld block (ld a multiple of 4)
+ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld, float* out, cudaStream_t s);
+
+// warm.cu: learned warm start (MLP d_in -> 256 -> k)
+int warm_kp(int d);  // padded feature width of [U | P_N U]: round_up(2d, 64)
+ancka_status warm_features(Workspace& ws, const Walk& w, const float* X, int d, __nv_bfloat16* A,
+                           __nv_bfloat16* At, cudaStream_t s);
+ancka_status warm_forward(Workspace& ws, const __nv_bfloat16* A, int64_t n, int kp, const __nv_bfloat16* W1t,
+                          const float* b1, const float* W2, const float* b2, int k, float* W, int ldw, float* Z1,
+                          float* H, int32_t* err, cudaStream_t s);
+ancka_status warm_refresh_w1t(const float* W1, int d_in, int kp, __nv_bfloat16* W1t, cudaStream_t s);
+struct WarmGrads {
+  float* W1;  // d_in x 256
+  float* b1;  // 256
+  float* W2;  // 256 x k
+  float* b2;  // k
+};
+struct WarmStepArgs {
+  int64_t n;
+  int k, d_in, kp;
+  const __nv_bfloat16* A;   // n x kp
+  const __nv_bfloat16* At;  // kp x round_up(n, 64)
+  const float* Qt;          // n x k target (row stride ldq)
+  int ldq;
+  float *W1, *b1, *W2, *b2;  // FP32 master weights (updated)
+  __nv_bfloat16* W1t;        // 256 x kp BF16 copy of W1^T (refreshed)
+  float *mW1, *vW1, *mb1, *vb1, *mW2, *vW2, *mb2, *vb2;  // Adam moments
+  float lr, lam;
+  int t;                     // Adam step (1-based)
+  double* loss_dev;          // loss before the update
+  int32_t* status;           // singular W^T W
+  int32_t* err;              // tensor-core wait expired
+  const WarmGrads* grads;    // optional: raw gradients out
+};
+ancka_status warm_train_step(Workspace& ws, const WarmStepArgs& a, cudaStream_t s);
+
+// gemm_tc.cu: tcgen05 BF16 GEMMs of the warm-start MLP (N = 256 columns)
+ancka_status gemm_bias_gelu(const __nv_bfloat16* A, int64_t m, int64_t k_pad, const __nv_bfloat16* Wt,
+                            const float* bias, float* Z, float* H, int ldz, int32_t* err, cudaStream_t s);
+ancka_status gemm_at_b(Workspace& ws, const __nv_bfloat16* At, int64_t m, int64_t k_pad, const __nv_bfloat16* Bt,
+                       float* C, int32_t* err, cudaStream_t s);
 ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, int32_t ldq,
                         int32_t max_iter, int32_t* labels, int32_t* iters_dev, int32_t* flags_dev,
                         int32_t** err_dev, cudaStream_t s);

@@ -1201,6 +1201,69 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
 }
 
 // Pi^T <- (1 - alpha) P_N^T Pi^T + alpha Z_0^T  (one InitBCM hop)
+}  // namespace
+
+// out = P_N U for an n x ld block U (Eqs. rw-hg, rw-ag, rw-mg: the topology
+// walk alone, no KNN part), in column chunks of at most 64 (the SpMM's
+// widest row); ld a multiple of 4, U and out 16-byte aligned.
+ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld, float* out, cudaStream_t s) {
+  const bool hyper = w.kind == ANCKA_HYPERGRAPH;
+  LongRows lt, le;
+  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, w.n, w.topo.nnz, &lt, s));
+  float* E = nullptr;
+  if (hyper) {
+    ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, &le, s));
+    ANCKA_TRY(ws.alloc(&E, (size_t)w.m * ld));
+  }
+  int32_t h[2] = {0, 0};
+  ANCKA_CUDA(cudaMemcpyAsync(&h[0], lt.count, 4, cudaMemcpyDeviceToHost, s));
+  if (hyper) ANCKA_CUDA(cudaMemcpyAsync(&h[1], le.count, 4, cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  lt.count_host = h[0];
+  le.count_host = h[1];
+  for (int c0 = 0; c0 < ld; c0 += 64) {
+    const int cw = ld - c0 < 64 ? ld - c0 : 64;
+    SpmmArgs a;
+    a.nrows = w.n;
+    a.nv4 = cw / 4;
+    a.out = out + c0;
+    a.ldo = ld;
+    a.ptrA = w.topo.ptr;
+    a.colA = w.topo.col;
+    a.ldA = ld;
+    a.long_rows = lt.rows;
+    a.n_long = lt.count;
+    a.n_long_host = lt.count_host;
+    a.long_min = lt.min_entries;
+    if (hyper) {
+      SpmmArgs e;  // E = D_E^-1 H U, then P_N U = D_V^-1 H^T E
+      e.nrows = w.m;
+      e.nv4 = cw / 4;
+      e.ptrA = w.edges.ptr;
+      e.colA = w.edges.col;
+      e.rsA = w.inv_size;
+      e.srcA = U + c0;
+      e.ldA = ld;
+      e.out = E + c0;
+      e.ldo = ld;
+      e.long_rows = le.rows;
+      e.n_long = le.count;
+      e.n_long_host = le.count_host;
+      e.long_min = le.min_entries;
+      ANCKA_TRY(spmm(e, s));
+      a.rsA = w.inv_deg;
+      a.srcA = E + c0;
+    } else {
+      a.valA = w.topo.val;
+      a.srcA = U + c0;
+    }
+    ANCKA_TRY(spmm(a, s));
+  }
+  return ANCKA_OK;
+}
+
+namespace {
+
 ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_t* seedcol) {
   const Walk& w = c.w;
   SpmmArgs a;
@@ -1283,6 +1346,37 @@ ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma
   k_copy_if<<<grid_for(c.n, 256), 256, 0, s>>>(sc.take, labels, best_labels, c.n);
   ANCKA_LAUNCHED();
   return ANCKA_OK;
+}
+
+// [n^-1/2 1 | W | 0-padding] (reading W6)
+__global__ void k_warm_block(const float* __restrict__ W, int ldw, int64_t n, int k, int ld, float c0,
+                             float* __restrict__ Q) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int64_t i = t / ld;
+  const int c = (int)(t % ld);
+  Q[t] = c == 0 ? c0 : (c <= k ? W[i * ldw + c - 1] : 0.f);
+}
+
+// per-block partial sums of (A - B)^2 over the first w columns
+__global__ void k_diff_norm2(const float* __restrict__ A, const float* __restrict__ B, int64_t n, int w, int ld,
+                             float* __restrict__ partial) {
+  __shared__ float red[32];
+  float acc = 0.f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * w; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / w;
+    const int c = (int)(t % w);
+    const float d = A[i * ld + c] - B[i * ld + c];
+    acc = fmaf(d, d, acc);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    partial[blockIdx.x] = t;
+  }
 }
 
 ancka_status make_disc_state(Workspace& ws, int64_t n, int k, DiscState* st) {
@@ -1376,8 +1470,8 @@ struct PhaseTimer {
 
 // phases: 2 = init, 3 = iteration, 4 = discretize, 5 = mhc, 6 = the walk products inside 3
 ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const int32_t* init_labels,
-                       int32_t* labels_out, float* Q_out, int32_t* init_out, IterTrace* tr,
-                       cudaStream_t s) {
+                       const float* warm_W, int ldw, int32_t* labels_out, float* Q_out, int32_t* init_out,
+                       IterTrace* tr, cudaStream_t s) {
   const int64_t n = w.n;
   const int k = cfg.k;
   const int wq = k + 1;
@@ -1459,7 +1553,6 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
       k_argmax_rows<<<grid_for(n, 256), 256, 0, s>>>(cur, ldk, n, k, y0);
       ANCKA_LAUNCHED();
     }
-    if (init_out) ANCKA_CUDA(cudaMemcpyAsync(init_out, y0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     // Q^(0) = [n^-1/2 1 | h(Y^(0))]
     ANCKA_CUDA(cudaMemsetAsync(sc.cnt, 0, sizeof(int32_t) * k, s));
     k_count_labels<<<grid_for(n, 1024) < 304 ? grid_for(n, 1024) : 304, 256, 0, s>>>(y0, n, k, sc.cnt);
@@ -1470,46 +1563,131 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
                                                         (float)(1.0 / sqrt((double)n)), 1.f, Qa);
     ANCKA_LAUNCHED();
   }
+  tr->warm_used = 0;
   {  // phi(Y^(0)) (reading R8)
     PhaseTimer pt(tr, s, 5);
     ANCKA_TRY(cal_mhc(c, sc, y0, cfg.gamma, tr->phi_dev + 0, tr->phi_best_dev, nullptr, ybest, true));
   }
+  if (warm_W) {
+    // learned warm start: Q_w = QR([n^-1/2 1 | W]) and Y_w = Discretize(Q_w[:, 1:]);
+    // it replaces InitBCM's start only if Phi(Y_w) <= Phi(Y^(0)) (reading W6)
+    PhaseTimer pt(tr, s, 2);
+    float* Qs;
+    double* phw;
+    int32_t *yw, *ywb, *wstatus;
+    ANCKA_TRY(ws.alloc(&Qs, (size_t)n * ld));
+    ANCKA_TRY(ws.alloc(&phw, 2));
+    ANCKA_TRY(ws.alloc(&yw, (size_t)n));
+    ANCKA_TRY(ws.alloc(&ywb, (size_t)n));
+    ANCKA_TRY(ws.zeros(&wstatus, 1));
+    k_warm_block<<<grid_for(n * ld, 256), 256, 0, s>>>(warm_W, ldw, n, k, ld, (float)(1.0 / sqrt((double)n)), Qb);
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(cholqr2(ws, c, Qb, Qs, wq, gpart, gblk, gticket, Rinv, wstatus));  // result in Qb
+    k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qb, ld, 1, n, k, Qt, ldk);
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, cfg.disc_max_iter, yw, nullptr, tr->flags_dev, s));
+    ANCKA_TRY(cal_mhc(c, sc, yw, cfg.gamma, phw, phw + 1, nullptr, ywb, true));
+    double h[2] = {0.0, 0.0};
+    int32_t hs = 0, de = 0;
+    ANCKA_CUDA(cudaMemcpyAsync(&h[0], phw, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&h[1], tr->phi_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&hs, wstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&de, st.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    if (de) {
+      set_error("Discretize: a grid barrier wait expired");
+      return ANCKA_ERR_TIMEOUT;
+    }
+    if (hs == 0 && h[0] <= h[1]) {
+      ANCKA_CUDA(cudaMemcpyAsync(Qa, Qb, sizeof(float) * n * ld, cudaMemcpyDeviceToDevice, s));
+      ANCKA_CUDA(cudaMemcpyAsync(y0, yw, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+      ANCKA_CUDA(cudaMemcpyAsync(ybest, yw, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+      ANCKA_CUDA(cudaMemcpyAsync(tr->phi_dev, phw, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ANCKA_CUDA(cudaMemcpyAsync(tr->phi_best_dev, phw, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      tr->warm_used = 1;
+    }
+  }
+  if (init_out) ANCKA_CUDA(cudaMemcpyAsync(init_out, y0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  // paper mode (Eq. tcond-1 / tcond-2): Q(t-1) kept at the check points
+  float* Qprev = nullptr;
+  float* dq_part = nullptr;
+  constexpr int kDqBlocks = 256;
+  double phi_hist[3] = {0.0, 0.0, 0.0};
+  int n_hist = 0;
+  double *phi_spare = nullptr;
+  int32_t *di_spare = nullptr, *tk_spare = nullptr;
+  ANCKA_TRY(ws.alloc(&phi_spare, 1));
+  ANCKA_TRY(ws.alloc(&di_spare, 1));
+  ANCKA_TRY(ws.alloc(&tk_spare, 1));
+  if (cfg.early_stop) {
+    ANCKA_TRY(ws.alloc(&Qprev, (size_t)n * ld));
+    ANCKA_TRY(ws.alloc(&dq_part, kDqBlocks));
+    ANCKA_CUDA(cudaMemcpyAsync(&phi_hist[0], tr->phi_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    n_hist = 1;
+  }
   int slot = 1;
   float* Q = Qa;
   float* Z = Qb;
+  int t_run = 0;
   for (int t = 1; t <= cfg.T; ++t) {
+    const bool check = t % cfg.tau == 0 || t == cfg.T;
     {
       PhaseTimer pt(tr, s, 3);
       {
         PhaseTimer pw(tr, s, 6);
         ANCKA_TRY(apply_walk(c, Q, ld, Z, 1.f, nullptr, nullptr, 0.f));  // Z = P Q
       }
+      if (Qprev && check)  // Q(t-1); CholeskyQR2 below uses Q as scratch
+        ANCKA_CUDA(cudaMemcpyAsync(Qprev, Q, sizeof(float) * n * ld, cudaMemcpyDeviceToDevice, s));
       ANCKA_TRY(cholqr2(ws, c, Z, Q, wq, gpart, gblk, gticket, Rinv, chol_status));  // result in Z
       float* tt = Q;
       Q = Z;
       Z = tt;
     }
-    if (t % cfg.tau == 0 || t == cfg.T) {
-      if (slot >= ANCKA_MAX_TRACE) {
-        set_error("too many Discretize calls for the trace (T / tau >= %d)", ANCKA_MAX_TRACE);
-        return ANCKA_ERR_INVALID_ARG;
-      }
+    t_run = t;
+    if (check) {
+      // trace slots beyond ANCKA_MAX_TRACE are not recorded
+      const bool rec = slot < ANCKA_MAX_TRACE;
+      double* phi_slot = rec ? tr->phi_dev + slot : phi_spare;
       {
         PhaseTimer pt(tr, s, 4);
         k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Q, ld, 1, n, k, Qt, ldk);
         ANCKA_LAUNCHED();
-        ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, cfg.disc_max_iter, yt, tr->disc_iters_dev + slot,
+        ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, cfg.disc_max_iter, yt, rec ? tr->disc_iters_dev + slot : di_spare,
                                  tr->flags_dev, s));
       }
       {
         PhaseTimer pt(tr, s, 5);
-        ANCKA_TRY(cal_mhc(c, sc, yt, cfg.gamma, tr->phi_dev + slot, tr->phi_best_dev, tr->taken_dev + slot,
+        ANCKA_TRY(cal_mhc(c, sc, yt, cfg.gamma, phi_slot, tr->phi_best_dev, rec ? tr->taken_dev + slot : tk_spare,
                           ybest, false));
       }
       ++slot;
+      if (cfg.early_stop) {
+        k_diff_norm2<<<kDqBlocks, 256, 0, s>>>(Q, Qprev, n, wq, ld, dq_part);
+        ANCKA_LAUNCHED();
+        float hp[kDqBlocks];
+        double ph = 0.0;
+        ANCKA_CUDA(cudaMemcpyAsync(hp, dq_part, sizeof(hp), cudaMemcpyDeviceToHost, s));
+        ANCKA_CUDA(cudaMemcpyAsync(&ph, phi_slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ANCKA_CUDA(cudaStreamSynchronize(s));
+        double dq = 0.0;
+        for (int b = 0; b < kDqBlocks; ++b) dq += hp[b];
+        dq = std::sqrt(dq);
+        if (n_hist == 3) {
+          phi_hist[0] = phi_hist[1];
+          phi_hist[1] = phi_hist[2];
+          n_hist = 2;
+        }
+        phi_hist[n_hist++] = ph;
+        const bool conv = dq < (double)cfg.eps_Q;                                                    // Eq. tcond-1
+        const bool rising = n_hist == 3 && phi_hist[0] < phi_hist[1] && phi_hist[1] < phi_hist[2];  // Eq. tcond-2
+        if (conv || rising) break;
+      }
     }
   }
-  tr->n_phi = slot;
+  tr->n_phi = slot < ANCKA_MAX_TRACE ? slot : ANCKA_MAX_TRACE;
+  tr->iters_run = t_run;
   ANCKA_CUDA(cudaMemcpyAsync(labels_out, ybest, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
   if (Q_out) ANCKA_CUDA(cudaMemcpy2DAsync(Q_out, sizeof(float) * wq, Q, sizeof(float) * ld, sizeof(float) * wq, n,
                                          cudaMemcpyDeviceToDevice, s));

@@ -20,11 +20,9 @@
 // leave the SM.  Every mbarrier wait is bounded: on expiry the kernel records
 // an error code, stops all roles, drains its own copies and MMAs (bounded),
 // frees TMEM and returns.
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 
-#include "common.cuh"
+#include "tc_common.cuh"
 
 namespace ancka {
 
@@ -32,7 +30,6 @@ namespace {
 
 constexpr int kTM = 128;                 // query rows per CTA = TMEM lanes
 constexpr int kTN = 256;                 // key rows per tile = accumulator columns
-constexpr int kTKB = 128;                // bytes of features per stage: one 128-byte swizzle row
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kListC = kCandC / 2;     // per-thread list (two per row)
@@ -42,7 +39,6 @@ constexpr int kMmaPerStage = 4;          // 32 bytes of K per MMA: 16 BF16 or 32
 constexpr int kMaxStages = 8;
 constexpr int kMaxSmem = 232448;         // 227 KB opt-in dynamic shared memory
 constexpr uint32_t kTmemCols = 512;      // two 256-column FP32 accumulators
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // instruction descriptors: D = F32 (bits 4-5 = 1), both operands K-major,
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28; kind::f16 with A = B = BF16
@@ -62,62 +58,6 @@ struct __align__(8) Bars {
   int abort;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; false on expiry (which raises the CTA-wide abort) or when
-// another role has already aborted
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* err, int code) {
-  if (mbar_try(b, parity)) return true;
-  const long long t0 = clock64();
-  while (true) {
-    if (mbar_try(b, parity)) return true;
-    if (abort && *abort) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      if (abort) *abort = 1;
-      if (err) atomicExch(err, code);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
-// layout (8-row x 128-byte atoms, 1024 bytes apart)
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
@@ -132,32 +72,6 @@ __device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t
       "l"(da), "l"(db), "r"(kIdescE4M3), "r"(accum)
       : "memory");
 }
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Issue a load of 32 consecutive FP32 accumulator columns of this thread's
-// TMEM lane; the registers are valid only after tmem_wait() + pin().
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// make every later use of r depend on this point (after the wait)
-__device__ __forceinline__ void pin(uint32_t (&r)[32]) {
-#pragma unroll
-  for (int q = 0; q < 32; ++q) asm volatile("" : "+r"(r[q]));
-}
-
 // Fold one 32-key chunk (scores in r, keys j0..j0+31) into the row's list.
 template <int C>
 __device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], int64_t j0, int64_t n, int64_t i,
@@ -409,43 +323,6 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    cudaGetLastError();
-  }
-  return fn;
-}
-
-// tensor map over a row-major (rows_total x dp) matrix of 1- or 2-byte
-// elements: boxes of 128 bytes of features x box_rows rows, 128-byte swizzle
-ancka_status make_map(CUtensorMap* m, const void* base, int64_t dp, int64_t rows_total, uint32_t box_rows,
-                      int elem_bytes) {
-  auto enc = encode_fn();
-  if (!enc) {
-    set_error("cuTensorMapEncodeTiled is not available from the driver");
-    return ANCKA_ERR_UNSUPPORTED;
-  }
-  cuuint64_t gdim[2] = {(cuuint64_t)dp, (cuuint64_t)rows_total};
-  cuuint64_t gstride[1] = {(cuuint64_t)dp * (cuuint64_t)elem_bytes};
-  cuuint32_t box[2] = {(cuuint32_t)(kTKB / elem_bytes), box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                   const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return ANCKA_ERR_CUDA;
-  }
-  return ANCKA_OK;
 }
 
 // pipeline depth and dynamic shared memory for kb_count blocks of A
