@@ -48,6 +48,14 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--knn-probe", default=None, metavar="N,D",
                     help="only run the BF16 KNN twice on a seeded N x D Gaussian matrix (profiling aid)")
+    ap.add_argument("--warm-report", action="store_true",
+                    help="learned warm start: train on multiplex graphs, evaluate plain vs learned start on the "
+                         "DC-SBM generator in the paper's early-termination mode (one JSON line)")
+    ap.add_argument("--warm-train-n", type=int, default=200_000)
+    ap.add_argument("--warm-graphs", type=int, default=16)
+    ap.add_argument("--warm-epochs", type=int, default=30)
+    ap.add_argument("--warm-eval-n", type=int, default=2_400_000)
+    ap.add_argument("--warm-eval-seeds", type=int, default=3)
     return ap.parse_args()
 
 
@@ -195,8 +203,87 @@ def knn_probe(args):
                       "knn_fallback_rows": info["knn_fallback_rows"]}), flush=True)
 
 
+def adjusted_rand(a, b):
+    """Adjusted Rand index of two labelings (Hubert and Arabie), for reports."""
+    a = np.unique(np.asarray(a), return_inverse=True)[1]
+    b = np.unique(np.asarray(b), return_inverse=True)[1]
+    C = np.zeros((a.max() + 1, b.max() + 1))
+    np.add.at(C, (a, b), 1.0)
+    c2 = lambda x: x * (x - 1) / 2.0
+    s_ij, s_a, s_b, tot = c2(C).sum(), c2(C.sum(1)).sum(), c2(C.sum(0)).sum(), c2(float(a.size))
+    exp = s_a * s_b / tot if tot > 0 else 0.0
+    mx = 0.5 * (s_a + s_b)
+    return 1.0 if mx == exp else float((s_ij - exp) / (mx - exp))
+
+
+def warm_report(args):
+    """Learned warm start (BASELINE config 5): an MLP 2d -> 256 -> k trained on
+    ANCKA's own blocks of multiplex graphs (the config-3 generator at n =
+    warm_train_n, d = 256, k = 20, seeds 100...), then plain (InitBCM) vs
+    learned start on the DC-SBM generator re-run with k = 20 and d = 256 (seeds
+    200...), both in the paper's early-termination mode (eps_Q = 0.005, at most
+    100 hops, tau = 5, T_i = 1 as for the large graphs)."""
+    import torch
+    from paper_2408_05459_gb300 import ancka, synth
+    ancka.load()
+    k, d = 20, 256
+    t0 = time.perf_counter()
+    items = []
+    for s in range(args.warm_graphs):
+        g = synth.multiplex_sbm(args.warm_train_n, k, 20.0, (8.0, 4.0, 2.0), d, 2.0, 100 + s)
+        td = ancka.topology_to_device(g)
+        X = torch.as_tensor(g["X"], device="cuda")
+        p = ancka.default_params(k=k, K=10, T=8, knn_prec="bf16")
+        _, ex, _ = ancka.cluster(td, X, p, want_Q=True, with_info=False)
+        items.append((td, X, ex["Q"][:, 1:].contiguous()))
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    w = {k_: torch.as_tensor(v, device="cuda") for k_, v in synth.warm_init(0, 2 * d, 256, k).items()}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = ancka.warm_train(items, w, args.warm_epochs, 1e-3, 1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1) / 1e3
+    del items
+    runs = []
+    for s in range(args.warm_eval_seeds):
+        g = synth.dcsbm_graph(args.warm_eval_n, k, 25 * args.warm_eval_n, d, 1.5, 200 + s)
+        td = ancka.topology_to_device(g)
+        X = torch.as_tensor(g["X"], device="cuda")
+        row = {"seed": 200 + s}
+        labs = {}
+        for mode in ("plain", "learned"):
+            p = ancka.default_params(k=k, K=10, T=100, tau=5, T_i=1, beta=0.4, knn_prec="bf16", early_stop=1,
+                                     eps_Q=0.005)
+            ancka.cluster(td, X, p, warm=w if mode == "learned" else None, with_info=False)  # warm-up
+            lab, _, info = ancka.cluster(td, X, p, warm=w if mode == "learned" else None)
+            torch.cuda.synchronize()
+            labs[mode] = lab.cpu().numpy()
+            row[mode] = {"hops": info["iters_run"], "time_to_labels_s": round(info["ms_total"] / 1e3, 4),
+                         "ms_knn": round(info["ms_knn"], 1), "ms_iter": round(info["ms_iter"], 1),
+                         "phi_best": round(info["phi_best"], 6),
+                         "ari_vs_planted": round(adjusted_rand(labs[mode], g["labels"]), 4)}
+            if mode == "learned":
+                row[mode]["warm_used"] = int(info["warm_used"])
+        row["ari_learned_vs_plain"] = round(adjusted_rand(labs["learned"], labs["plain"]), 4)
+        runs.append(row)
+        del td, X, g
+        torch.cuda.empty_cache()
+    fb = sum(1 for r in runs if not r["learned"]["warm_used"]) / max(1, len(runs))
+    print(json.dumps({"report": "learned_warm_start", "train": {
+        "graphs": args.warm_graphs, "n": args.warm_train_n, "d": d, "k": k, "epochs": args.warm_epochs,
+        "loss_first": round(float(losses[0]), 5), "loss_last": round(float(losses[-1]), 5),
+        "train_s": round(t_train, 3), "data_s": round(t_data, 1)},
+        "eval": {"generator": "DC-SBM (config 4) with k=20, d=256", "n": args.warm_eval_n,
+                 "mode": "early termination (Eq. tcond-1/2), eps_Q=0.005, at most 100 hops", "runs": runs,
+                 "plain_start_fallback_rate": fb}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.warm_report:
+        return warm_report(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

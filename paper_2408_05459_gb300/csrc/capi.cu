@@ -842,7 +842,8 @@ ancka_status ancka_warm_train(const ancka_warm_graph* graphs, int32_t n_graphs, 
       const int t = e * n_graphs + g;
       WarmStepArgs a;
       warm_step_args(gd[(size_t)g], model, kp, b, lr, lam, t + 1, b.loss + t, nullptr, &a);
-      ANCKA_TRY(warm_train_step(ws, a, s));
+      Workspace step_ws(s);  // the step's temporaries, released (stream-ordered) after it
+      ANCKA_TRY(warm_train_step(step_ws, a, s));
     }
   ANCKA_TRY(warm_check(b, s));
   if (losses) {

@@ -51,6 +51,7 @@ struct SpmmArgs {
   const int32_t* n_long = nullptr;     // their count (device)
   int64_t n_long_host = -1;            // the same count on the host (-1: not known)
   int64_t long_min = 0;                // rows with more entries than this are long
+  int64_t mean_entries = 0;            // mean entries per row (picks the slices per row)
 };
 
 __device__ __forceinline__ void fma4(float4& acc, float w, const float4& x) {
@@ -68,41 +69,77 @@ __device__ __forceinline__ int64_t row_entries(const SpmmArgs& a, int64_t i) {
   return (a.ptrA[i + 1] - a.ptrA[i]) + (a.ptrB ? a.ptrB[i + 1] - a.ptrB[i] : 0);
 }
 
-template <int G>
+// One row per G * S lanes: G lanes over the row's float4 chunks, S slices
+// over its entries (slice sl takes entries sl, sl + S, ..., four per step
+// with their loads in flight); the slices are summed by a fixed xor
+// butterfly, so every lane of the group holds the same sum.  Rows with more
+// than long_min entries are left to k_spmm_long.
+template <int G, int S>
 __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
+  constexpr int L = G * S;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = t / G;
-  const int g = (int)(t % G);
-  if (i >= a.nrows || g >= a.nv4) return;
-  if (row_entries(a, i) > a.long_min) return;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  {
-    // four entries per step: independent index/row loads in flight, the FMAs
-    // applied in entry order (same result as one entry per step)
-    int64_t p = a.ptrA[i];
+  const int64_t i = t / L;
+  const int u = (int)(t % L);
+  const int g = u % G, sl = u / G;
+  const bool row_ok = i < a.nrows && row_entries(a, i) <= a.long_min;
+  const bool act = row_ok && g < a.nv4;
+  float4 accA = make_float4(0.f, 0.f, 0.f, 0.f), accB = accA;
+  if (act) {
+    int64_t p = a.ptrA[i] + sl;
     const int64_t e = a.ptrA[i + 1];
-    for (; p + 4 <= e; p += 4) {
+    for (; p + 3 * S < e; p += 4 * S) {
       int32_t j[4];
       float w[4];
       float4 x[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) j[u] = a.colA[p + u];
+      for (int q = 0; q < 4; ++q) j[q] = a.colA[p + q * S];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        w[u] = a.valA ? a.valA[p + u] : 1.f;
-        if (a.csA) w[u] *= a.csA[j[u]];
-        x[u] = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j[u] * a.ldA + 4 * g);
+      for (int q = 0; q < 4; ++q) {
+        w[q] = a.valA ? a.valA[p + q * S] : 1.f;
+        if (a.csA) w[q] *= a.csA[j[q]];
+        x[q] = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j[q] * a.ldA + 4 * g);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) fma4(acc, w[u], x[u]);
+      for (int q = 0; q < 4; ++q) fma4(accA, w[q], x[q]);
     }
-    for (; p < e; ++p) {
+    for (; p < e; p += S) {
       const int32_t j = a.colA[p];
       float w = a.valA ? a.valA[p] : 1.f;
       if (a.csA) w *= a.csA[j];
-      fma4(acc, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
+      fma4(accA, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
+    }
+    if (a.ptrB) {
+      int64_t pb = a.ptrB[i] + sl;
+      const int64_t eb = a.ptrB[i + 1];
+      for (; pb + 3 * S < eb; pb += 4 * S) {
+        int32_t j[4];
+        float4 x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) j[q] = a.colB[pb + q * S];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j[q] * a.ldB + 4 * g);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fma4(accB, a.valB[pb + q * S], x[q]);
+      }
+      for (; pb < eb; pb += S)
+        fma4(accB, a.valB[pb], *reinterpret_cast<const float4*>(a.srcB + (int64_t)a.colB[pb] * a.ldB + 4 * g));
     }
   }
+  if constexpr (S > 1) {  // every lane of the warp takes part
+#pragma unroll
+    for (int off = G; off < L; off <<= 1) {
+      accA.x += __shfl_xor_sync(0xffffffffu, accA.x, off);
+      accA.y += __shfl_xor_sync(0xffffffffu, accA.y, off);
+      accA.z += __shfl_xor_sync(0xffffffffu, accA.z, off);
+      accA.w += __shfl_xor_sync(0xffffffffu, accA.w, off);
+      accB.x += __shfl_xor_sync(0xffffffffu, accB.x, off);
+      accB.y += __shfl_xor_sync(0xffffffffu, accB.y, off);
+      accB.z += __shfl_xor_sync(0xffffffffu, accB.z, off);
+      accB.w += __shfl_xor_sync(0xffffffffu, accB.w, off);
+    }
+  }
+  if (!act || sl != 0) return;
+  float4 acc = accA;
   if (a.rsA) {
     const float r = a.rsA[i];
     acc.x *= r;
@@ -110,26 +147,10 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
     acc.z *= r;
     acc.w *= r;
   }
-  if (a.ptrB) {
-    int64_t p = a.ptrB[i];
-    const int64_t e = a.ptrB[i + 1];
-    for (; p + 4 <= e; p += 4) {
-      int32_t j[4];
-      float4 x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) j[u] = a.colB[p + u];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j[u] * a.ldB + 4 * g);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) fma4(acc, a.valB[p + u], x[u]);
-    }
-    for (; p < e; ++p)
-      fma4(acc, a.valB[p], *reinterpret_cast<const float4*>(a.srcB + (int64_t)a.colB[p] * a.ldB + 4 * g));
-  }
-  acc.x *= a.coef;
-  acc.y *= a.coef;
-  acc.z *= a.coef;
-  acc.w *= a.coef;
+  acc.x = (acc.x + accB.x) * a.coef;
+  acc.y = (acc.y + accB.y) * a.coef;
+  acc.z = (acc.z + accB.z) * a.coef;
+  acc.w = (acc.w + accB.w) * a.coef;
   if (a.oh_col) {
     const int c = a.oh_col[i];
     if (c >= 4 * g && c < 4 * g + 4) {
@@ -223,6 +244,7 @@ struct LongRows {
   int32_t* count = nullptr;
   int64_t count_host = -1;
   int64_t min_entries = 0;
+  int64_t mean = 0;
 };
 
 // long rows of (ptrA [, ptrB]) (nnz entries in all), listed once per call
@@ -230,6 +252,7 @@ struct LongRows {
 ancka_status find_long_rows(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, int64_t nrows, int64_t nnz,
                             LongRows* out, cudaStream_t s) {
   const int64_t mean = nrows > 0 ? ceil_div(nnz, nrows) : 0;
+  out->mean = mean;
   out->min_entries = 4 * mean > kLongRowMin ? 4 * mean : kLongRowMin;
   ANCKA_TRY(ws.alloc(&out->rows, (size_t)(nrows > 0 ? nrows : 1)));
   ANCKA_TRY(ws.zeros(&out->count, 1));
@@ -239,10 +262,31 @@ ancka_status find_long_rows(Workspace& ws, const int64_t* ptrA, const int64_t* p
   return ANCKA_OK;
 }
 
+template <int G, int S>
+void launch_spmm(const SpmmArgs& a, cudaStream_t s) {
+  k_spmm<G, S><<<grid_for(a.nrows * G * S, 256), 256, 0, s>>>(a);
+}
+
+template <int G>
+void launch_spmm_slices(const SpmmArgs& a, int S, cudaStream_t s) {
+  if constexpr (G <= 4) {
+    if (S >= 8) return launch_spmm<G, 8>(a, s);
+  }
+  if constexpr (G <= 8) {
+    if (S >= 4) return launch_spmm<G, 4>(a, s);
+  }
+  if constexpr (G <= 16) {
+    if (S >= 2) return launch_spmm<G, 2>(a, s);
+  }
+  launch_spmm<G, 1>(a, s);
+}
+
 ancka_status spmm(const SpmmArgs& a, cudaStream_t s) {
   const int nv4 = a.nv4;
   const int G = nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16;
-  const unsigned grid = grid_for(a.nrows * G, 256);
+  // slices per row: about four entries per slice, at most 32 lanes per row
+  int S = 1;
+  while (S < 8 && 4 * S * 2 <= a.mean_entries && G * S * 2 <= 32) S <<= 1;
   if (!a.long_rows || a.n_long_host < 0) {
     set_error("internal: SpMM without a long-row list");
     return ANCKA_ERR_INTERNAL;
@@ -250,11 +294,11 @@ ancka_status spmm(const SpmmArgs& a, cudaStream_t s) {
   // the long-row kernel walks the device-side list; skipped when it is empty
   const unsigned lgrid = (unsigned)(a.n_long_host < 1216 ? a.n_long_host : 1216);
   switch (G) {
-    case 1: k_spmm<1><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<1><<<lgrid, 256, 0, s>>>(a); break;
-    case 2: k_spmm<2><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<2><<<lgrid, 256, 0, s>>>(a); break;
-    case 4: k_spmm<4><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<4><<<lgrid, 256, 0, s>>>(a); break;
-    case 8: k_spmm<8><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<8><<<lgrid, 256, 0, s>>>(a); break;
-    default: k_spmm<16><<<grid, 256, 0, s>>>(a); if (lgrid) k_spmm_long<16><<<lgrid, 256, 0, s>>>(a); break;
+    case 1: launch_spmm_slices<1>(a, S, s); if (lgrid) k_spmm_long<1><<<lgrid, 256, 0, s>>>(a); break;
+    case 2: launch_spmm_slices<2>(a, S, s); if (lgrid) k_spmm_long<2><<<lgrid, 256, 0, s>>>(a); break;
+    case 4: launch_spmm_slices<4>(a, S, s); if (lgrid) k_spmm_long<4><<<lgrid, 256, 0, s>>>(a); break;
+    case 8: launch_spmm_slices<8>(a, S, s); if (lgrid) k_spmm_long<8><<<lgrid, 256, 0, s>>>(a); break;
+    default: launch_spmm_slices<16>(a, S, s); if (lgrid) k_spmm_long<16><<<lgrid, 256, 0, s>>>(a); break;
   }
   ANCKA_LAUNCHED();
   if (lgrid) count_launch();
@@ -1179,6 +1223,7 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
     e.n_long = c.lr_edges.count;
     e.n_long_host = c.lr_edges.count_host;
     e.long_min = c.lr_edges.min_entries;
+    e.mean_entries = c.lr_edges.mean;
     ANCKA_TRY(spmm(e, c.s));
     a.ptrA = w.topo.ptr;
     a.colA = w.topo.col;
@@ -1197,6 +1242,7 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
   a.n_long = c.lr_walk.count;
   a.n_long_host = c.lr_walk.count_host;
   a.long_min = c.lr_walk.min_entries;
+  a.mean_entries = c.lr_walk.mean;
   return spmm(a, c.s);
 }
 
@@ -1235,6 +1281,7 @@ ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld
     a.n_long = lt.count;
     a.n_long_host = lt.count_host;
     a.long_min = lt.min_entries;
+    a.mean_entries = lt.mean;
     if (hyper) {
       SpmmArgs e;  // E = D_E^-1 H U, then P_N U = D_V^-1 H^T E
       e.nrows = w.m;
@@ -1250,6 +1297,7 @@ ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld
       e.n_long = le.count;
       e.n_long_host = le.count_host;
       e.long_min = le.min_entries;
+      e.mean_entries = le.mean;
       ANCKA_TRY(spmm(e, s));
       a.rsA = w.inv_deg;
       a.srcA = E + c0;
@@ -1289,6 +1337,7 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
     e.n_long = c.lr_edges.count;
     e.n_long_host = c.lr_edges.count_host;
     e.long_min = c.lr_edges.min_entries;
+    e.mean_entries = c.lr_edges.mean;
     ANCKA_TRY(spmm(e, c.s));
     a.ptrA = w.topo.ptr;  // sum_{e ni i} y_e / |e|
     a.colA = w.topo.col;
@@ -1306,6 +1355,7 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
   a.n_long = c.lr_topo.count;
   a.n_long_host = c.lr_topo.count_host;
   a.long_min = c.lr_topo.min_entries;
+  a.mean_entries = c.lr_topo.mean;
   return spmm(a, c.s);
 }
 

@@ -44,7 +44,12 @@ def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, symmetric: bool = T
     src, dst = src[keep], dst[keep]
     if symmetric:
         src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
-    key = np.unique(src * n + dst)
+    key = np.sort(src * n + dst)     # sorted unique keys (same result as np.unique, faster here)
+    if key.size:
+        first = np.empty(key.size, bool)
+        first[0] = True
+        np.not_equal(key[1:], key[:-1], out=first[1:])
+        key = key[first]
     rows = key // n
     cols = (key % n).astype(np.int32)
     counts = np.bincount(rows, minlength=n)
