@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--knn-probe", default=None, metavar="N,D",
                     help="only run the BF16 KNN twice on a seeded N x D Gaussian matrix (profiling aid)")
+    ap.add_argument("--spmm-probe", type=int, default=None, metavar="N",
+                    help="Algorithm 4 on the DC-SBM generator (k=47, d=100, 25 N edges) at N nodes: the walk "
+                         "products' time against their compulsory bytes (one JSON line; profiling aid)")
     ap.add_argument("--warm-report", action="store_true",
                     help="learned warm start: train on multiplex graphs, evaluate plain vs learned start on the "
                          "DC-SBM generator in the paper's early-termination mode (one JSON line)")
@@ -280,8 +283,43 @@ def warm_report(args):
                  "plain_start_fallback_rate": fb}}), flush=True)
 
 
+def spmm_probe(args):
+    """SpMM in the HBM regime: the DC-SBM generator at N nodes (config-4
+    settings: k = 47, d = 100, beta = 0.4, T_i = 1, T = 10), where the block Q
+    (N x 48 FP32) exceeds L2.  Compulsory bytes per hop: the merged topology
+    CSR (int64 row pointers, int32 columns, FP32 values, row scale), the KNN
+    CSR, one read of Q and one write of Z."""
+    import torch
+    from paper_2408_05459_gb300 import ancka, synth
+    ancka.load()
+    n, k, d = args.spmm_probe, 47, 100
+    g = synth.dcsbm_graph(n, k, 25 * n, d, 1.5, 0)
+    td = ancka.topology_to_device(g)
+    X = torch.as_tensor(g["X"], device="cuda")
+    p = ancka.default_params(k=k, K=10, T=10, T_i=1, beta=0.4, knn_prec="bf16")
+    ancka.cluster(td, X, p, with_info=False)
+    _, ex, info = ancka.cluster(td, X, p, want_knn=True)
+    torch.cuda.synchronize()
+    kidx = ex["knn_idx"].cpu().numpy().astype(np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), kidx.shape[1])
+    mutual = np.isin(kidx.reshape(-1) * n + rows, rows * n + kidx.reshape(-1))
+    nnz_k = n * kidx.shape[1] + int((~mutual).sum())
+    nnz_t = int(g["layers"][0][0][-1])
+    ld = 48
+    hop = (n + 1) * 8 + nnz_t * 8 + n * 4 + (n + 1) * 8 + nnz_k * 8 + 2 * n * ld * 4
+    print(json.dumps({"probe": "spmm", "workload": f"DC-SBM n={n}, k={k}, d={d}, nnz(P_N)={nnz_t}, nnz(P_K)={nnz_k}",
+                      "ms_spmm_total": round(info["ms_spmm"], 3), "hops": 10,
+                      "us_per_hop": round(info["ms_spmm"] * 100, 1), "compulsory_bytes_per_hop": int(hop),
+                      "effective_gbs": round(hop * 10 / (info["ms_spmm"] * 1e-3) / 1e9, 1),
+                      "phases_ms": {k_: round(info[k_], 2) for k_ in ("ms_knn", "ms_build", "ms_init", "ms_iter",
+                                                                      "ms_spmm", "ms_disc", "ms_mhc", "ms_total")}}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.spmm_probe:
+        return spmm_probe(args)
     if args.warm_report:
         return warm_report(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -9,6 +9,8 @@
 // Cholesky, the Discretize SVD) and for cross-CTA sums.
 #include <cub/cub.cuh>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ancka {
@@ -52,6 +54,12 @@ struct SpmmArgs {
   int64_t n_long_host = -1;            // the same count on the host (-1: not known)
   int64_t long_min = 0;                // rows with more entries than this are long
   int64_t mean_entries = 0;            // mean entries per row (picks the slices per row)
+  int oh_off = 0;                      // column of the block where this launch's columns start
+  int64_t srcA_rows = 0;               // rows of srcA / srcB (0: not known)
+  int64_t srcB_rows = 0;
+  const int2* long_items = nullptr;    // (long row q, part) work items of at most kLongChunk entries
+  const int32_t* long_off = nullptr;   // items of long row q: [long_off[q], long_off[q + 1])
+  int64_t n_items_host = 0;
 };
 
 __device__ __forceinline__ void fma4(float4& acc, float w, const float4& x) {
@@ -61,9 +69,12 @@ __device__ __forceinline__ void fma4(float4& acc, float w, const float4& x) {
   acc.w = fmaf(w, x.w, acc.w);
 }
 
-// A row is long when it has more than max(kLongRowMin, 4 x the mean row
-// length) entries; long rows go to k_spmm_long.
-constexpr int64_t kLongRowMin = 256;
+// A row is long when it has more than max(256, 4 x the mean row length)
+// entries, or max(128, 2 x mean) when the gathered block exceeds 64 MB (there
+// the row-length tail dominates; on small blocks the extra launches do);
+// long rows are cut into work items of at most kLongChunk entries (topology
+// entries, then KNN entries) for k_spmm_long.
+constexpr int kLongChunk = 1024;
 
 __device__ __forceinline__ int64_t row_entries(const SpmmArgs& a, int64_t i) {
   return (a.ptrA[i + 1] - a.ptrA[i]) + (a.ptrB ? a.ptrB[i + 1] - a.ptrB[i] : 0);
@@ -92,10 +103,10 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
       float w[4];
       float4 x[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) j[q] = a.colA[p + q * S];
+      for (int q = 0; q < 4; ++q) j[q] = *(a.colA + p + q * S);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        w[q] = a.valA ? a.valA[p + q * S] : 1.f;
+        w[q] = a.valA ? *(a.valA + p + q * S) : 1.f;
         if (a.csA) w[q] *= a.csA[j[q]];
         x[q] = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j[q] * a.ldA + 4 * g);
       }
@@ -103,8 +114,8 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
       for (int q = 0; q < 4; ++q) fma4(accA, w[q], x[q]);
     }
     for (; p < e; p += S) {
-      const int32_t j = a.colA[p];
-      float w = a.valA ? a.valA[p] : 1.f;
+      const int32_t j = *(a.colA + p);
+      float w = a.valA ? *(a.valA + p) : 1.f;
       if (a.csA) w *= a.csA[j];
       fma4(accA, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
     }
@@ -115,14 +126,14 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
         int32_t j[4];
         float4 x[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) j[q] = a.colB[pb + q * S];
+        for (int q = 0; q < 4; ++q) j[q] = *(a.colB + pb + q * S);
 #pragma unroll
         for (int q = 0; q < 4; ++q) x[q] = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j[q] * a.ldB + 4 * g);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) fma4(accB, a.valB[pb + q * S], x[q]);
+        for (int q = 0; q < 4; ++q) fma4(accB, *(a.valB + pb + q * S), x[q]);
       }
       for (; pb < eb; pb += S)
-        fma4(accB, a.valB[pb], *reinterpret_cast<const float4*>(a.srcB + (int64_t)a.colB[pb] * a.ldB + 4 * g));
+        fma4(accB, *(a.valB + pb), *reinterpret_cast<const float4*>(a.srcB + (int64_t)*(a.colB + pb) * a.ldB + 4 * g));
     }
   }
   if constexpr (S > 1) {  // every lane of the warp takes part
@@ -153,9 +164,10 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
   acc.w = (acc.w + accB.w) * a.coef;
   if (a.oh_col) {
     const int c = a.oh_col[i];
-    if (c >= 4 * g && c < 4 * g + 4) {
+    const int cl = c - a.oh_off;  // this launch's column
+    if (cl >= 4 * g && cl < 4 * g + 4) {
       const float add = a.oh_coef * (a.oh_scale ? a.oh_scale[c] : 1.f);
-      const int q = c - 4 * g;
+      const int q = cl - 4 * g;
       if (q == 0) acc.x += add;
       else if (q == 1) acc.y += add;
       else if (q == 2) acc.z += add;
@@ -165,29 +177,67 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
   *reinterpret_cast<float4*>(a.out + i * a.ldo + 4 * g) = acc;
 }
 
-// Long rows (hubs of skewed degree
-// distributions): one CTA per row, 256/G teams of G lanes split the entries,
-// partial sums combined by a fixed-order tree in shared memory.
+// Long rows (hubs of skewed degree distributions): CTAs take work items
+// (row, part) grid-stride; 256/G teams of G lanes split the item's entries
+// (four in flight per team), a fixed-order tree in shared memory combines
+// the teams, and the item's partial sums (topology part, KNN part) go to
+// part[item].  k_spmm_long_finish then adds a row's items in order.
 template <int G>
-__global__ void __launch_bounds__(256) k_spmm_long(SpmmArgs a) {
+__global__ void __launch_bounds__(256) k_spmm_long(SpmmArgs a, float4* __restrict__ part) {
   constexpr int kTeams = 256 / G;
   __shared__ float4 redA[kTeams][G];
   __shared__ float4 redB[kTeams][G];
   const int team = threadIdx.x / G, g = threadIdx.x % G;
-  const int64_t nl = a.n_long ? *a.n_long : 0;
-  for (int64_t q = blockIdx.x; q < nl; q += gridDim.x) {
-    const int64_t i = a.long_rows[q];
+  for (int64_t it = blockIdx.x; it < a.n_items_host; it += gridDim.x) {
+    const int2 item = a.long_items[it];
+    const int64_t i = a.long_rows[item.x];
+    const int64_t a0 = a.ptrA[i], lenA = a.ptrA[i + 1] - a0;
+    const int64_t b0 = a.ptrB ? a.ptrB[i] : 0, lenB = a.ptrB ? a.ptrB[i + 1] - b0 : 0;
+    const int64_t e0 = (int64_t)item.y * kLongChunk;
+    const int64_t e1 = (e0 + kLongChunk < lenA + lenB) ? e0 + kLongChunk : lenA + lenB;
     float4 accA = make_float4(0.f, 0.f, 0.f, 0.f), accB = accA;
     if (g < a.nv4) {
-      for (int64_t p = a.ptrA[i] + team, e = a.ptrA[i + 1]; p < e; p += kTeams) {
-        const int32_t j = a.colA[p];
-        float w = a.valA ? a.valA[p] : 1.f;
-        if (a.csA) w *= a.csA[j];
-        fma4(accA, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
+      {  // topology entries [e0, min(e1, lenA))
+        const int64_t end = a0 + (e1 < lenA ? e1 : lenA);
+        int64_t p = a0 + e0 + team;
+        for (; p + 3 * kTeams < end; p += 4 * kTeams) {
+          int32_t j[4];
+          float w[4];
+          float4 x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) j[u] = a.colA[p + u * kTeams];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            w[u] = a.valA ? a.valA[p + u * kTeams] : 1.f;
+            if (a.csA) w[u] *= a.csA[j[u]];
+            x[u] = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j[u] * a.ldA + 4 * g);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) fma4(accA, w[u], x[u]);
+        }
+        for (; p < end; p += kTeams) {
+          const int32_t j = a.colA[p];
+          float w = a.valA ? a.valA[p] : 1.f;
+          if (a.csA) w *= a.csA[j];
+          fma4(accA, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
+        }
       }
-      if (a.ptrB)
-        for (int64_t p = a.ptrB[i] + team, e = a.ptrB[i + 1]; p < e; p += kTeams)
+      if (e1 > lenA) {  // KNN entries [max(e0, lenA), e1) - lenA
+        const int64_t end = b0 + (e1 - lenA);
+        int64_t p = b0 + (e0 > lenA ? e0 - lenA : 0) + team;
+        for (; p + 3 * kTeams < end; p += 4 * kTeams) {
+          int32_t j[4];
+          float4 x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) j[u] = a.colB[p + u * kTeams];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j[u] * a.ldB + 4 * g);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) fma4(accB, a.valB[p + u * kTeams], x[u]);
+        }
+        for (; p < end; p += kTeams)
           fma4(accB, a.valB[p], *reinterpret_cast<const float4*>(a.srcB + (int64_t)a.colB[p] * a.ldB + 4 * g));
+      }
     }
     redA[team][g] = accA;
     redB[team][g] = accB;
@@ -202,33 +252,48 @@ __global__ void __launch_bounds__(256) k_spmm_long(SpmmArgs a) {
       }
       __syncthreads();
     }
-    if (team == 0 && g < a.nv4) {
-      float4 acc = redA[0][g];
-      if (a.rsA) {
-        const float r = a.rsA[i];
-        acc.x *= r;
-        acc.y *= r;
-        acc.z *= r;
-        acc.w *= r;
-      }
-      const float4 b = redB[0][g];
-      acc = make_float4((acc.x + b.x) * a.coef, (acc.y + b.y) * a.coef, (acc.z + b.z) * a.coef,
-                        (acc.w + b.w) * a.coef);
-      if (a.oh_col) {
-        const int c = a.oh_col[i];
-        if (c >= 4 * g && c < 4 * g + 4) {
-          const float add = a.oh_coef * (a.oh_scale ? a.oh_scale[c] : 1.f);
-          const int q = c - 4 * g;
-          if (q == 0) acc.x += add;
-          else if (q == 1) acc.y += add;
-          else if (q == 2) acc.z += add;
-          else acc.w += add;
-        }
-      }
-      *reinterpret_cast<float4*>(a.out + i * a.ldo + 4 * g) = acc;
+    if (team == 0) {
+      part[(it * 2 + 0) * G + g] = redA[0][g];
+      part[(it * 2 + 1) * G + g] = redB[0][g];
     }
     __syncthreads();
   }
+}
+
+template <int G>
+__global__ void k_spmm_long_finish(SpmmArgs a, const float4* __restrict__ part) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t q = t / G;
+  const int g = (int)(t % G);
+  if (q >= a.n_long_host || g >= a.nv4) return;
+  const int64_t i = a.long_rows[q];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), b = acc;
+  for (int64_t it = a.long_off[q]; it < a.long_off[q + 1]; ++it) {
+    const float4 x = part[(it * 2 + 0) * G + g], y = part[(it * 2 + 1) * G + g];
+    acc = make_float4(acc.x + x.x, acc.y + x.y, acc.z + x.z, acc.w + x.w);
+    b = make_float4(b.x + y.x, b.y + y.y, b.z + y.z, b.w + y.w);
+  }
+  if (a.rsA) {
+    const float r = a.rsA[i];
+    acc.x *= r;
+    acc.y *= r;
+    acc.z *= r;
+    acc.w *= r;
+  }
+  acc = make_float4((acc.x + b.x) * a.coef, (acc.y + b.y) * a.coef, (acc.z + b.z) * a.coef, (acc.w + b.w) * a.coef);
+  if (a.oh_col) {
+    const int c = a.oh_col[i];
+    const int cl = c - a.oh_off;
+    if (cl >= 4 * g && cl < 4 * g + 4) {
+      const float add = a.oh_coef * (a.oh_scale ? a.oh_scale[c] : 1.f);
+      const int qq = cl - 4 * g;
+      if (qq == 0) acc.x += add;
+      else if (qq == 1) acc.y += add;
+      else if (qq == 2) acc.z += add;
+      else acc.w += add;
+    }
+  }
+  *reinterpret_cast<float4*>(a.out + i * a.ldo + 4 * g) = acc;
 }
 
 __global__ void k_find_long(const int64_t* __restrict__ ptrA, const int64_t* __restrict__ ptrB, int64_t nrows,
@@ -245,15 +310,65 @@ struct LongRows {
   int64_t count_host = -1;
   int64_t min_entries = 0;
   int64_t mean = 0;
+  int2* items = nullptr;      // (q, part) work items
+  int32_t* off = nullptr;     // count_host + 1 item offsets
+  int64_t items_host = 0;
 };
 
+__global__ void k_long_item_counts(const int64_t* __restrict__ ptrA, const int64_t* __restrict__ ptrB,
+                                   const int32_t* __restrict__ rows, int64_t n_long, int32_t* __restrict__ cnt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q > n_long) return;
+  if (q == n_long) {
+    cnt[q] = 0;
+    return;
+  }
+  const int64_t i = rows[q];
+  const int64_t len = (ptrA[i + 1] - ptrA[i]) + (ptrB ? ptrB[i + 1] - ptrB[i] : 0);
+  cnt[q] = (int32_t)((len + kLongChunk - 1) / kLongChunk);
+}
+
+__global__ void k_long_item_fill(const int32_t* __restrict__ off, int64_t n_long, int2* __restrict__ items) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_long) return;
+  for (int32_t it = off[q]; it < off[q + 1]; ++it) items[it] = make_int2((int)q, it - off[q]);
+}
+
+// work items of the long rows (after count_host is known): one sync
+ancka_status build_long_items(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, LongRows* lr, cudaStream_t s) {
+  const int64_t nl = lr->count_host;
+  int32_t* cnt;
+  ANCKA_TRY(ws.alloc(&cnt, (size_t)nl + 1));
+  ANCKA_TRY(ws.alloc(&lr->off, (size_t)nl + 1));
+  k_long_item_counts<<<grid_for(nl + 1, 256), 256, 0, s>>>(ptrA, ptrB, lr->rows, nl, cnt);
+  ANCKA_LAUNCHED();
+  size_t tmp = 0;
+  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, cnt, lr->off, (int)(nl + 1), s));
+  void* t;
+  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp > 0 ? tmp : 1));
+  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, cnt, lr->off, (int)(nl + 1), s));
+  int32_t total = 0;
+  ANCKA_CUDA(cudaMemcpyAsync(&total, lr->off + nl, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  lr->items_host = total;
+  ANCKA_TRY(ws.alloc(&lr->items, (size_t)(total > 0 ? total : 1)));
+  if (nl > 0) {
+    k_long_item_fill<<<grid_for(nl, 256), 256, 0, s>>>(lr->off, nl, lr->items);
+    ANCKA_LAUNCHED();
+  }
+  return ANCKA_OK;
+}
+
 // long rows of (ptrA [, ptrB]) (nnz entries in all), listed once per call
-// (list order does not affect the result)
+// (list order does not affect the result); block_bytes: size of the block
+// the SpMM gathers from
 ancka_status find_long_rows(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, int64_t nrows, int64_t nnz,
-                            LongRows* out, cudaStream_t s) {
+                            double block_bytes, LongRows* out, cudaStream_t s) {
   const int64_t mean = nrows > 0 ? ceil_div(nnz, nrows) : 0;
   out->mean = mean;
-  out->min_entries = 4 * mean > kLongRowMin ? 4 * mean : kLongRowMin;
+  const bool big = block_bytes > 64.0 * (1 << 20);
+  const int64_t lo = big ? 128 : 256, f = big ? 2 : 4;
+  out->min_entries = f * mean > lo ? f * mean : lo;
   ANCKA_TRY(ws.alloc(&out->rows, (size_t)(nrows > 0 ? nrows : 1)));
   ANCKA_TRY(ws.zeros(&out->count, 1));
   k_find_long<<<(unsigned)ceil_div(nrows > 0 ? nrows : 1, 256), 256, 0, s>>>(ptrA, ptrB, nrows, out->min_entries,
@@ -281,27 +396,65 @@ void launch_spmm_slices(const SpmmArgs& a, int S, cudaStream_t s) {
   launch_spmm<G, 1>(a, s);
 }
 
-ancka_status spmm(const SpmmArgs& a, cudaStream_t s) {
-  const int nv4 = a.nv4;
-  const int G = nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16;
-  // slices per row: about four entries per slice, at most 32 lanes per row
-  int S = 1;
-  while (S < 8 && 4 * S * 2 <= a.mean_entries && G * S * 2 <= 32) S <<= 1;
-  if (!a.long_rows || a.n_long_host < 0) {
+ancka_status spmm(const SpmmArgs& a0, cudaStream_t s) {
+  if (!a0.long_rows || a0.n_long_host < 0) {
     set_error("internal: SpMM without a long-row list");
     return ANCKA_ERR_INTERNAL;
   }
-  // the long-row kernel walks the device-side list; skipped when it is empty
-  const unsigned lgrid = (unsigned)(a.n_long_host < 1216 ? a.n_long_host : 1216);
-  switch (G) {
-    case 1: launch_spmm_slices<1>(a, S, s); if (lgrid) k_spmm_long<1><<<lgrid, 256, 0, s>>>(a); break;
-    case 2: launch_spmm_slices<2>(a, S, s); if (lgrid) k_spmm_long<2><<<lgrid, 256, 0, s>>>(a); break;
-    case 4: launch_spmm_slices<4>(a, S, s); if (lgrid) k_spmm_long<4><<<lgrid, 256, 0, s>>>(a); break;
-    case 8: launch_spmm_slices<8>(a, S, s); if (lgrid) k_spmm_long<8><<<lgrid, 256, 0, s>>>(a); break;
-    default: launch_spmm_slices<16>(a, S, s); if (lgrid) k_spmm_long<16><<<lgrid, 256, 0, s>>>(a); break;
+  const int ld = 4 * a0.nv4;
+  // long rows: work items into partial sums, then the per-row finish
+  const bool longs = a0.n_long_host > 0 && a0.n_items_host > 0;
+  if (a0.n_long_host > 0 && !a0.long_items) {
+    set_error("internal: SpMM with long rows but no work items");
+    return ANCKA_ERR_INTERNAL;
   }
-  ANCKA_LAUNCHED();
-  if (lgrid) count_launch();
+  float4* part = nullptr;
+  if (longs)
+    ANCKA_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&part), sizeof(float4) * 2 * 16 * a0.n_items_host, s));
+  const unsigned lgrid = (unsigned)(a0.n_items_host < 1216 ? a0.n_items_host : 1216);
+  for (int c0 = 0; c0 < ld; c0 += 64) {  // a launch covers at most 64 columns
+    SpmmArgs a = a0;
+    const int w = ld - c0 < 64 ? ld - c0 : 64;
+    a.nv4 = w / 4;
+    a.oh_off = c0;
+    a.out = a0.out + c0;
+    a.srcA = a0.srcA + c0;
+    if (a0.srcB) a.srcB = a0.srcB + c0;
+    const int nv4 = a.nv4;
+    const int G = nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16;
+    // slices per row: about four entries per slice, at most 32 lanes per row
+    int S = 1;
+    while (S < 8 && 4 * S * 2 <= a.mean_entries && G * S * 2 <= 32) S <<= 1;
+    const unsigned fgrid = grid_for(a0.n_long_host * G, 256);
+    switch (G) {
+      case 1:
+        launch_spmm_slices<1>(a, S, s);
+        if (longs) { k_spmm_long<1><<<lgrid, 256, 0, s>>>(a, part); k_spmm_long_finish<1><<<fgrid, 256, 0, s>>>(a, part); }
+        break;
+      case 2:
+        launch_spmm_slices<2>(a, S, s);
+        if (longs) { k_spmm_long<2><<<lgrid, 256, 0, s>>>(a, part); k_spmm_long_finish<2><<<fgrid, 256, 0, s>>>(a, part); }
+        break;
+      case 4:
+        launch_spmm_slices<4>(a, S, s);
+        if (longs) { k_spmm_long<4><<<lgrid, 256, 0, s>>>(a, part); k_spmm_long_finish<4><<<fgrid, 256, 0, s>>>(a, part); }
+        break;
+      case 8:
+        launch_spmm_slices<8>(a, S, s);
+        if (longs) { k_spmm_long<8><<<lgrid, 256, 0, s>>>(a, part); k_spmm_long_finish<8><<<fgrid, 256, 0, s>>>(a, part); }
+        break;
+      default:
+        launch_spmm_slices<16>(a, S, s);
+        if (longs) { k_spmm_long<16><<<lgrid, 256, 0, s>>>(a, part); k_spmm_long_finish<16><<<fgrid, 256, 0, s>>>(a, part); }
+        break;
+    }
+    ANCKA_LAUNCHED();
+    if (longs) {
+      count_launch();
+      count_launch();
+    }
+  }
+  if (part) ANCKA_CUDA(cudaFreeAsync(part, s));
   return ANCKA_OK;
 }
 
@@ -1214,6 +1367,7 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
     e.colA = w.edges.col;
     e.rsA = w.inv_size;
     e.srcA = Q;
+    e.srcA_rows = c.n;
     e.ldA = ld;
     e.out = c.E;
     e.ldo = ld;
@@ -1222,6 +1376,12 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
     e.long_rows = c.lr_edges.rows;
     e.n_long = c.lr_edges.count;
     e.n_long_host = c.lr_edges.count_host;
+
+    e.long_items = c.lr_edges.items;
+
+    e.long_off = c.lr_edges.off;
+
+    e.n_items_host = c.lr_edges.items_host;
     e.long_min = c.lr_edges.min_entries;
     e.mean_entries = c.lr_edges.mean;
     ANCKA_TRY(spmm(e, c.s));
@@ -1229,6 +1389,7 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
     a.colA = w.topo.col;
     a.rsA = w.rs_topo;
     a.srcA = c.E;
+    a.srcA_rows = w.m;
     a.ldA = ld;
   } else {
     a.ptrA = w.topo.ptr;
@@ -1236,11 +1397,19 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
     a.valA = w.topo.val;
     a.rsA = w.rs_topo;
     a.srcA = Q;
+    a.srcA_rows = c.n;
     a.ldA = ld;
   }
+  a.srcB_rows = c.n;
   a.long_rows = c.lr_walk.rows;
   a.n_long = c.lr_walk.count;
   a.n_long_host = c.lr_walk.count_host;
+
+  a.long_items = c.lr_walk.items;
+
+  a.long_off = c.lr_walk.off;
+
+  a.n_items_host = c.lr_walk.items_host;
   a.long_min = c.lr_walk.min_entries;
   a.mean_entries = c.lr_walk.mean;
   return spmm(a, c.s);
@@ -1255,10 +1424,12 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
 ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld, float* out, cudaStream_t s) {
   const bool hyper = w.kind == ANCKA_HYPERGRAPH;
   LongRows lt, le;
-  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, w.n, w.topo.nnz, &lt, s));
+  const double ub = (double)(hyper ? w.m : w.n) * (ld < 64 ? ld : 64) * 4.0;
+  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, w.n, w.topo.nnz, ub, &lt, s));
   float* E = nullptr;
   if (hyper) {
-    ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, &le, s));
+    ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, (double)w.n * (ld < 64 ? ld : 64) * 4.0,
+                             &le, s));
     ANCKA_TRY(ws.alloc(&E, (size_t)w.m * ld));
   }
   int32_t h[2] = {0, 0};
@@ -1267,6 +1438,8 @@ ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld
   ANCKA_CUDA(cudaStreamSynchronize(s));
   lt.count_host = h[0];
   le.count_host = h[1];
+  ANCKA_TRY(build_long_items(ws, w.topo.ptr, nullptr, &lt, s));
+  if (hyper) ANCKA_TRY(build_long_items(ws, w.edges.ptr, nullptr, &le, s));
   for (int c0 = 0; c0 < ld; c0 += 64) {
     const int cw = ld - c0 < 64 ? ld - c0 : 64;
     SpmmArgs a;
@@ -1280,6 +1453,12 @@ ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld
     a.long_rows = lt.rows;
     a.n_long = lt.count;
     a.n_long_host = lt.count_host;
+
+    a.long_items = lt.items;
+
+    a.long_off = lt.off;
+
+    a.n_items_host = lt.items_host;
     a.long_min = lt.min_entries;
     a.mean_entries = lt.mean;
     if (hyper) {
@@ -1290,20 +1469,29 @@ ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld
       e.colA = w.edges.col;
       e.rsA = w.inv_size;
       e.srcA = U + c0;
+      e.srcA_rows = w.n;
       e.ldA = ld;
       e.out = E + c0;
       e.ldo = ld;
       e.long_rows = le.rows;
       e.n_long = le.count;
       e.n_long_host = le.count_host;
+
+      e.long_items = le.items;
+
+      e.long_off = le.off;
+
+      e.n_items_host = le.items_host;
       e.long_min = le.min_entries;
       e.mean_entries = le.mean;
       ANCKA_TRY(spmm(e, s));
       a.rsA = w.inv_deg;
       a.srcA = E + c0;
+      a.srcA_rows = w.m;
     } else {
       a.valA = w.topo.val;
       a.srcA = U + c0;
+      a.srcA_rows = w.n;
     }
     ANCKA_TRY(spmm(a, s));
   }
@@ -1328,6 +1516,7 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
     e.colA = w.edges.col;
     e.csA = w.inv_deg;
     e.srcA = Pi;
+    e.srcA_rows = c.n;
     e.ldA = c.ldk;
     e.out = c.E;
     e.ldo = c.ldk;
@@ -1336,6 +1525,12 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
     e.long_rows = c.lr_edges.rows;
     e.n_long = c.lr_edges.count;
     e.n_long_host = c.lr_edges.count_host;
+
+    e.long_items = c.lr_edges.items;
+
+    e.long_off = c.lr_edges.off;
+
+    e.n_items_host = c.lr_edges.items_host;
     e.long_min = c.lr_edges.min_entries;
     e.mean_entries = c.lr_edges.mean;
     ANCKA_TRY(spmm(e, c.s));
@@ -1343,17 +1538,25 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
     a.colA = w.topo.col;
     a.csA = w.inv_size;
     a.srcA = c.E;
+    a.srcA_rows = w.m;
     a.ldA = c.ldk;
   } else {
     a.ptrA = w.topo.ptr;
     a.colA = w.topo.col;
     a.valA = w.topo.valT;
     a.srcA = Pi;
+    a.srcA_rows = c.n;
     a.ldA = c.ldk;
   }
   a.long_rows = c.lr_topo.rows;
   a.n_long = c.lr_topo.count;
   a.n_long_host = c.lr_topo.count_host;
+
+  a.long_items = c.lr_topo.items;
+
+  a.long_off = c.lr_topo.off;
+
+  a.n_items_host = c.lr_topo.items_host;
   a.long_min = c.lr_topo.min_entries;
   a.mean_entries = c.lr_topo.mean;
   return spmm(a, c.s);
@@ -1534,10 +1737,13 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   ANCKA_TRY(ws.alloc(&Rinv, (size_t)wq * wq));
   if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(ws.alloc(&E, (size_t)(w.m > 0 ? w.m : 1) * (ld > ldk ? ld : ldk)));
   Ctx c{w, n, k, ld, ldk, cfg.alpha, E, s, {}, {}, {}};
-  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, w.knn.ptr, n, w.topo.nnz + w.knn.nnz, &c.lr_walk, s));
-  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, n, w.topo.nnz, &c.lr_topo, s));
+  const double qbytes = (double)n * ld * 4.0, ebytes = (double)w.m * ld * 4.0;
+  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, w.knn.ptr, n, w.topo.nnz + w.knn.nnz,
+                           w.kind == ANCKA_HYPERGRAPH ? ebytes : qbytes, &c.lr_walk, s));
+  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, n, w.topo.nnz, w.kind == ANCKA_HYPERGRAPH ? ebytes : qbytes,
+                           &c.lr_topo, s));
   if (w.kind == ANCKA_HYPERGRAPH)
-    ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, &c.lr_edges, s));
+    ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, qbytes, &c.lr_edges, s));
   {
     int32_t h[3] = {0, 0, 0};
     ANCKA_CUDA(cudaMemcpyAsync(&h[0], c.lr_walk.count, 4, cudaMemcpyDeviceToHost, s));
@@ -1548,6 +1754,9 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     c.lr_topo.count_host = h[1];
     c.lr_edges.count_host = h[2];
   }
+  ANCKA_TRY(build_long_items(ws, w.topo.ptr, w.knn.ptr, &c.lr_walk, s));
+  ANCKA_TRY(build_long_items(ws, w.topo.ptr, nullptr, &c.lr_topo, s));
+  if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(build_long_items(ws, w.edges.ptr, nullptr, &c.lr_edges, s));
   Scratch sc;
   ANCKA_TRY(ws.alloc(&sc.cnt, 64));
   ANCKA_TRY(ws.alloc(&sc.inv, 64));

@@ -160,3 +160,21 @@ def test_invalid_arguments(ak):
     with pytest.raises(ak.AnckaError) as e:
         _gpu_cluster(ak, bad, "fp32")
     assert e.value.status == 1
+
+
+def test_wide_block_k64(ak):
+    """k = 64: the block has 65 columns (row stride 68), wider than one SpMM
+    launch covers (64 columns), so the walk products run in two column
+    chunks.  Checked: identical InitBCM labels, the subspace of Q and
+    phi(Y0).  The labels themselves are not compared: with k clusters only k
+    eigenvalues of P are near 1 and the constant vector lies in their span,
+    so columns 2..k+1 carry k-1 informative directions plus a bulk one, and
+    Discretize's labels at k = 64 sit near ties (the oracle reaches ARI 0.92
+    against the planted clusters)."""
+    g = synth.sbm_graph(3200, 64, 0.5, 0.0002, 96, 0.2, 8)
+    labels, ex, info = _gpu_cluster(ak, g, "fp32", k=64, T=6, tau=3)
+    p = _params(ak, k=64, T=6, tau=3)
+    o = O.ancka(g, g["X"], _oracle_params(p), knn=ex["knn_idx"])
+    assert np.array_equal(ex["init_labels"], o["init_labels"])
+    assert O.max_principal_angle(ex["Q"], o["Q"]) <= ANGLE_MAX
+    assert abs(info["phi"][0] - o["phi"][0]) <= 1e-4   # later phi follow the near-tie labels
