@@ -590,18 +590,18 @@ __device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int
   double* X = csm + 2 * ww;
   {
     // Tn threads per entry, each summing a strided subset of the CTA
-    // partials with four loads in flight; subsets combined in fixed order
+    // partials with eight loads in flight; subsets combined in fixed order
     const int Tn = max(1, min((int)blockDim.x / np, 16));
     for (int e = threadIdx.x; e < np * Tn; e += blockDim.x) {
       const int entry = e / Tn, sub = e % Tn;
       float h = 0.f, l = 0.f;
       int bb = sub;
-      for (; bb + 3 * Tn < nblk; bb += 4 * Tn) {
-        float2 v[4];
+      for (; bb + 7 * Tn < nblk; bb += 8 * Tn) {
+        float2 v[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldcg(partial + (int64_t)(bb + u * Tn) * np + entry);
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(partial + (int64_t)(bb + u * Tn) * np + entry);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ff_add(h, l, v[u].x, v[u].y);
+        for (int u = 0; u < 8; ++u) ff_add(h, l, v[u].x, v[u].y);
       }
       for (; bb < nblk; bb += Tn) {
         const float2 v = __ldcg(partial + (int64_t)bb * np + entry);
@@ -1765,7 +1765,7 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   sc.tblk = (int)(ceil_div(n, 4096) < 304 ? ceil_div(n, 4096) : 304);
   ANCKA_TRY(ws.alloc(&sc.tpart, (size_t)sc.tblk));
   ANCKA_TRY(ws.alloc(&sc.take, 1));
-  const int gblk = (int)(ceil_div(n, 512) < 304 ? ceil_div(n, 512) : 304);
+  const int gblk = (int)(ceil_div(n, 512) < 152 ? ceil_div(n, 512) : 152);
   float2* gpart;
   unsigned int* gticket;
   ANCKA_TRY(ws.alloc(&gpart, (size_t)gblk * wq * (wq + 1) / 2));
