@@ -196,7 +196,7 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
     if (prec == ANCKA_PREC_BF16) {
       int32_t* terr;
       ANCKA_TRY(ws.zeros(&terr, 1));
-      ANCKA_TRY(knn_candidates_bf16(pr, n, cv, ci, terr, s));
+      ANCKA_TRY(knn_candidates_bf16(ws, pr, n, cv, ci, terr, s));
       if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
       int32_t hterr = 0;
       ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -209,7 +209,7 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
     } else if (prec == ANCKA_PREC_FP8) {
       int32_t* terr;
       ANCKA_TRY(ws.zeros(&terr, 1));
-      ANCKA_TRY(knn_candidates_fp8(pr, n, cv, ci, terr, s));
+      ANCKA_TRY(knn_candidates_fp8(ws, pr, n, cv, ci, terr, s));
       if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
       int32_t hterr = 0;
       ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -577,9 +577,9 @@ ancka_status ancka_knn_candidates(const float* X, int64_t n, int32_t d, int32_t 
   int32_t* terr;
   ANCKA_TRY(ws.zeros(&terr, 1));
   if (prec == ANCKA_PREC_BF16) {
-    ANCKA_TRY(knn_candidates_bf16(pr, n, cand_val, cand_idx, terr, s));
+    ANCKA_TRY(knn_candidates_bf16(ws, pr, n, cand_val, cand_idx, terr, s));
   } else {
-    ANCKA_TRY(knn_candidates_fp8(pr, n, cand_val, cand_idx, terr, s));
+    ANCKA_TRY(knn_candidates_fp8(ws, pr, n, cand_val, cand_idx, terr, s));
   }
   if (qrows) {
     k_copy_qrows<<<(unsigned)ceil_div(n * d, 256), 256, 0, s>>>(pr.xb, pr.dp, prec == ANCKA_PREC_FP8 ? pr.x8 : nullptr,

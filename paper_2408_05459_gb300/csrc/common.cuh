@@ -189,11 +189,11 @@ ancka_status prep_rows(Workspace& ws, const float* X, int64_t n, int32_t d, int 
 constexpr int kCandC = 32;  // candidates kept per row
 ancka_status knn_candidates_fp32(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
                                  cudaStream_t s);
-ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
+ancka_status knn_candidates_bf16(Workspace& ws, const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
                                  int32_t* err, cudaStream_t s);
 // FP8 (E4M3) list pass: scores written in cosine units (times 1/S^2)
-ancka_status knn_candidates_fp8(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx, int32_t* err,
-                                cudaStream_t s);
+ancka_status knn_candidates_fp8(Workspace& ws, const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
+                                int32_t* err, cudaStream_t s);
 int knn_tc_max_dp_fp8();
 // BF16 list pass for the n_a rows listed in rows; lists written at their global rows
 ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,

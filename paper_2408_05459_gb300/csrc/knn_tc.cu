@@ -1,21 +1,25 @@
 // tcgen05 BF16 / FP8-e4m3 candidate search for the cosine KNN of Section 3.1.
 //
-// One CTA per 128 query rows sweeps every 256-row key tile:
-//   warp 0     TMA producer: the CTA's query block A (128 x dp, 128-byte
-//              swizzle) once, then key tiles B (256 rows x 128 bytes of
-//              features per stage: 64 BF16 or 128 FP8) through an
-//              nstages-deep ring (mbarrier full/empty);
+// Persistent CTAs (one per SM) share the (128-row query block, 256-row key
+// tile) pairs in equal contiguous runs (stream-K), so no wave tail is left
+// idle.  In each CTA:
+//   warp 0     TMA producer: the current query block A (128 x dp, 128-byte
+//              swizzle) when the run enters it, then key tiles B (256 rows x
+//              128 bytes of features per stage: 64 BF16 or 128 FP8) through
+//              an nstages-deep ring (mbarrier full/empty);
 //   warp 1     MMA issuer: allocates 512 TMEM columns, issues
 //              tcgen05.mma.cta_group::1.kind::f16 (BF16, K=16) or
 //              kind::f8f6f4 (E4M3, K=32) with M=128, N=256 into two
-//              ping-pong FP32 accumulators, commits stage releases and
-//              accumulator-ready signals;
+//              ping-pong FP32 accumulators, commits stage releases,
+//              accumulator-ready signals and the release of A at the end of
+//              each query block;
 //   warps 2-9  epilogue: two warps per TMEM lane quarter, each owning half of
 //              every tile's 256 columns; tcgen05.ld (32x32b) of the thread's
 //              accumulator row (TMEM lane = query row), threshold test and
 //              insert into a register-resident list of its 16 best scores.
 //              Row i thus leaves two 16-entry lists (one per column half),
-//              kCandC = 32 candidates in total.
+//              kCandC = 32 candidates in total; a query block split between
+//              two CTAs leaves partial lists that k_merge_lists combines.
 // The MMA of tile t+1 overlaps the epilogue of tile t.  n x n scores never
 // leave the SM.  Every mbarrier wait is bounded: on expiry the kernel records
 // an error code, stops all roles, drains its own copies and MMAs (bounded),
@@ -51,6 +55,7 @@ struct __align__(8) Bars {
   uint64_t full[kMaxStages];
   uint64_t empty[kMaxStages];
   uint64_t a_full;
+  uint64_t a_empty;
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
@@ -134,15 +139,24 @@ struct CollectArgs {
   int cap;
 };
 
+// Work split (stream-K): the (query block, key tile) pairs, numbered
+// qb * n_tiles + t, are cut into gridDim.x equal contiguous ranges, one per
+// persistent CTA.  A CTA's range is a sequence of segments, one per query
+// block it touches; only its first and its last segment can miss part of a
+// block's key tiles.  Such a partial segment leaves its lists in slot 0
+// (first segment) or 1 (last) of the CTA's partial area, and k_merge_lists
+// combines the pieces of every split block.
+__device__ __forceinline__ int64_t range_begin(int64_t c, int64_t work, int64_t ctas) { return c * work / ctas; }
+
 // kCollect: collect mode (keys above a per-row threshold) instead of list
 // mode (two 16-entry lists per row); kE4M3: FP8 operands.  out_scale (list
 // mode, may be null) multiplies the scores written out.
 template <bool kCollect, bool kE4M3>
 __global__ void __launch_bounds__(kThreads, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-         int64_t n_pad, int kb_count, int nstages, int tps, float* __restrict__ cand_val,
-         int32_t* __restrict__ cand_idx, const float* __restrict__ out_scale, CollectArgs ca,
-         int* __restrict__ err) {
+         int64_t n_pad, int64_t qblocks, int kb_count, int nstages, float* __restrict__ cand_val,
+         int32_t* __restrict__ cand_idx, const float* __restrict__ out_scale, float* __restrict__ part_val,
+         int32_t* __restrict__ part_idx, CollectArgs ca, int* __restrict__ err) {
   constexpr int kTK = kE4M3 ? 128 : 64;  // features per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -150,12 +164,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   uint8_t* sB = sA + kb_count * kABytes;
   Bars* bars = reinterpret_cast<Bars*>(sB + nstages * kBBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ib = (int64_t)blockIdx.x * kTM;
-  // this CTA's key tiles: [t_begin, t_begin + ntiles) (collect mode splits
-  // the sweep over blockIdx.y; list mode sweeps all keys)
-  const int all_tiles = (int)ceil_div(n_pad, kTN);
-  const int t_begin = (int)blockIdx.y * tps;
-  const int ntiles = max(0, min(all_tiles, t_begin + tps) - t_begin);
+  const int n_tiles = (int)ceil_div(n_pad, kTN);
+  const int64_t work = qblocks * n_tiles;
+  const int64_t w_begin = range_begin(blockIdx.x, work, gridDim.x);
+  const int64_t w_end = range_begin((int64_t)blockIdx.x + 1, work, gridDim.x);
   volatile int* abort = &bars->abort;
 
   if (threadIdx.x == 0) {
@@ -164,6 +176,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       mbar_init(&bars->empty[s], 1);
     }
     mbar_init(&bars->a_full, 1);
+    mbar_init(&bars->a_empty, 1);
     mbar_init(&bars->tfull[0], 1);
     mbar_init(&bars->tfull[1], 1);
     mbar_init(&bars->tempty[0], kEpiWarps);
@@ -189,74 +202,99 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       bool pending[kMaxStages];
       uint32_t pend_par[kMaxStages];
       for (int s = 0; s < kMaxStages; ++s) pending[s] = false;
-      mbar_expect_tx(&bars->a_full, (uint32_t)(kb_count * kABytes));
-      for (int kb = 0; kb < kb_count; ++kb)
-        tma_load_2d(smem_u32(sA + kb * kABytes), &tmA, kb * kTK, (int)ib, &bars->a_full);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int t = 0; t < ntiles && ok; ++t) {
-        for (int kb = 0; kb < kb_count; ++kb) {
-          if (!mbar_wait(&bars->empty[stage], phase ^ 1, abort, err, 1)) {
-            ok = false;
-            break;
-          }
-          pending[stage] = false;
-          mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
-          tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, (t_begin + t) * kTN, &bars->full[stage]);
-          pending[stage] = true;
-          pend_par[stage] = phase;
-          if (++stage == nstages) {
-            stage = 0;
-            phase ^= 1;
+      int seg = 0;
+      for (int64_t w = w_begin; w < w_end && ok; ++seg) {
+        const int64_t qb = w / n_tiles;
+        const int t0 = (int)(w - qb * n_tiles);
+        const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
+        w += t1 - t0;
+        // the previous block of A stays in use until its last MMA completes
+        if (seg > 0 && !mbar_wait(&bars->a_empty, (uint32_t)((seg - 1) & 1), abort, err, 6)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&bars->a_full, (uint32_t)(kb_count * kABytes));
+        for (int kb = 0; kb < kb_count; ++kb)
+          tma_load_2d(smem_u32(sA + kb * kABytes), &tmA, kb * kTK, (int)(qb * kTM), &bars->a_full);
+        for (int t = t0; t < t1 && ok; ++t) {
+          for (int kb = 0; kb < kb_count; ++kb) {
+            if (!mbar_wait(&bars->empty[stage], phase ^ 1, abort, err, 1)) {
+              ok = false;
+              break;
+            }
+            pending[stage] = false;
+            mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
+            tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, t * kTN, &bars->full[stage]);
+            pending[stage] = true;
+            pend_par[stage] = phase;
+            if (++stage == nstages) {
+              stage = 0;
+              phase ^= 1;
+            }
           }
         }
       }
       if (!ok) {  // drain this warp's copies still in flight (bounded)
-        mbar_wait(&bars->a_full, 0, nullptr, nullptr, 0);
+        if (seg > 0) mbar_wait(&bars->a_full, (uint32_t)((seg - 1) & 1), nullptr, nullptr, 0);
         for (int s = 0; s < nstages; ++s)
           if (pending[s]) mbar_wait(&bars->full[s], pend_par[s], nullptr, nullptr, 0);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      bool ok = mbar_wait(&bars->a_full, 0, abort, err, 2);
+      bool ok = true;
       int stage = 0;
       uint32_t phase = 0;
       bool issued = false;
-      for (int t = 0; t < ntiles && ok; ++t) {
-        const int b = t & 1;
-        const uint32_t use = (uint32_t)(t >> 1);
-        if (!mbar_wait(&bars->tempty[b], (use & 1) ^ 1, abort, err, 3)) {
+      int64_t g = 0;  // accumulator tiles so far (ping-pong over two)
+      int seg = 0;
+      for (int64_t w = w_begin; w < w_end && ok; ++seg) {
+        const int64_t qb = w / n_tiles;
+        const int t0 = (int)(w - qb * n_tiles);
+        const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
+        w += t1 - t0;
+        if (!mbar_wait(&bars->a_full, (uint32_t)(seg & 1), abort, err, 2)) {
           ok = false;
           break;
         }
-        tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(b * kTN);
-        for (int kb = 0; kb < kb_count; ++kb) {
-          if (!mbar_wait(&bars->full[stage], phase, abort, err, 4)) {
+        for (int t = t0; t < t1; ++t, ++g) {
+          const int b = (int)(g & 1);
+          const uint32_t use = (uint32_t)(g >> 1);
+          if (!mbar_wait(&bars->tempty[b], (use & 1) ^ 1, abort, err, 3)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(sA + kb * kABytes);
-          const uint32_t b0 = smem_u32(sB + stage * kBBytes);
+          const uint32_t d = tmem + (uint32_t)(b * kTN);
+          for (int kb = 0; kb < kb_count; ++kb) {
+            if (!mbar_wait(&bars->full[stage], phase, abort, err, 4)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + kb * kABytes);
+            const uint32_t b0 = smem_u32(sB + stage * kBBytes);
 #pragma unroll
-          for (int kk = 0; kk < kMmaPerStage; ++kk) {
-            if constexpr (kE4M3)
-              umma_e4m3(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
-            else
-              umma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+            for (int kk = 0; kk < kMmaPerStage; ++kk) {
+              if constexpr (kE4M3)
+                umma_e4m3(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+              else
+                umma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+            }
+            issued = true;
+            umma_commit(&bars->empty[stage]);
+            if (++stage == nstages) {
+              stage = 0;
+              phase ^= 1;
+            }
           }
-          issued = true;
-          umma_commit(&bars->empty[stage]);
-          if (++stage == nstages) {
-            stage = 0;
-            phase ^= 1;
-          }
+          if (!ok) break;
+          umma_commit(&bars->tfull[b]);
         }
-        if (!ok) break;
-        umma_commit(&bars->tfull[b]);
+        if (ok) umma_commit(&bars->a_empty);  // A may be replaced once these MMAs complete
       }
       if (!ok && issued) {  // wait for this thread's MMAs before TMEM is freed (bounded)
         umma_commit(&bars->drain);
@@ -268,12 +306,105 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     const int q = warp & 3;    // TMEM lane quarter this warp may access
     const int h = ew >> 2;     // column half of every tile
     const int r = q * 32 + lane;
-    // A row ra is query row ra, or compact row ra -> global row a_rows[ra]
-    const int64_t ra = ib + r;
-    const bool row_ok = ca.a_rows ? (ra < ca.n_a) : (ra < n);
-    const int64_t i = ca.a_rows ? (row_ok ? (int64_t)ca.a_rows[ra] : -1) : ra;
-    const float t_row = kCollect && row_ok ? ca.thr[ra] : INFINITY;
     constexpr int C = kListC;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    const float sc = (!kCollect && out_scale) ? *out_scale : 1.f;
+    int64_t g = 0;
+    int seg = 0;
+    bool ok = true;
+    for (int64_t w = w_begin; w < w_end && ok; ++seg) {
+      const int64_t qb = w / n_tiles;
+      const int t0 = (int)(w - qb * n_tiles);
+      const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
+      w += t1 - t0;
+      // A row ra is query row ra, or compact row ra -> global row a_rows[ra]
+      const int64_t ra = qb * kTM + r;
+      const bool row_ok = ca.a_rows ? (ra < ca.n_a) : (ra < n);
+      const int64_t i = ca.a_rows ? (row_ok ? (int64_t)ca.a_rows[ra] : -1) : ra;
+      const float t_row = kCollect && row_ok ? ca.thr[ra] : INFINITY;
+      float lv[C];
+      int32_t li[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        lv[c] = -INFINITY;
+        li[c] = -1;
+      }
+      float thr = -INFINITY;
+      int mp = 0;
+      for (int t = t0; t < t1; ++t, ++g) {
+        const int b = (int)(g & 1);
+        const uint32_t use = (uint32_t)(g >> 1);
+        const bool got = mbar_wait(&bars->tfull[b], use & 1, abort, err, 5);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int64_t jb = (int64_t)t * kTN + h * (kTN / 2);
+        const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * (kTN / 2));
+#pragma unroll 1
+        for (int c = 0; c < kTN / 64; ++c) {
+          uint32_t rv[32];
+          tmem_ld32_issue(tb + (uint32_t)(c * 32), rv);
+          tmem_wait();
+          pin(rv);
+          if constexpr (kCollect) {
+            collect_chunk(rv, jb + c * 32, n, i, t_row, ra, ca.cnt, ca.buf, ca.cap);
+          } else {
+            fold_chunk<C>(rv, jb + c * 32, n, i, lv, li, thr, mp);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->tempty[b]);
+      }
+      if (!kCollect && ok) {
+        float* ov;
+        int32_t* oi;
+        if (t0 == 0 && t1 == n_tiles) {  // whole block: final lists
+          if (!row_ok) continue;
+          ov = cand_val + i * kCandC;
+          oi = cand_idx + i * kCandC;
+        } else {
+          const int64_t slot = ((int64_t)blockIdx.x * 2 + (seg == 0 ? 0 : 1)) * kTM + r;
+          ov = part_val + slot * kCandC;
+          oi = part_idx + slot * kCandC;
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          ov[h * C + c] = lv[c] * sc;
+          oi[h * C + c] = li[c];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Lists of the query blocks split between CTAs: per row and column half, the
+// 16 best of the pieces' lists (each piece holds the best of its own key
+// tiles, so the result is the best of the whole half).  One CTA of kTM
+// threads per query block; blocks that one CTA covered return at once.
+__global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, int64_t ctas,
+                                                     const float* __restrict__ part_val,
+                                                     const int32_t* __restrict__ part_idx,
+                                                     const int32_t* __restrict__ a_rows, int64_t n_rows,
+                                                     float* __restrict__ cand_val, int32_t* __restrict__ cand_idx) {
+  const int64_t qb = blockIdx.x;
+  const int64_t x0 = qb * n_tiles, x1 = x0 + n_tiles;
+  const int64_t c0 = ((x0 + 1) * ctas + work - 1) / work - 1;  // the CTA whose range holds x0
+  if (range_begin(c0 + 1, work, ctas) >= x1) return;
+  const int r = threadIdx.x;
+  const int64_t ra = qb * kTM + r;
+  if (ra >= n_rows) return;
+  const int64_t i = a_rows ? (int64_t)a_rows[ra] : ra;
+  constexpr int C = kListC;
+  for (int h = 0; h < 2; ++h) {
     float lv[C];
     int32_t li[C];
 #pragma unroll
@@ -283,45 +414,21 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     }
     float thr = -INFINITY;
     int mp = 0;
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    for (int t = 0; t < ntiles; ++t) {
-      const int b = t & 1;
-      const uint32_t use = (uint32_t)(t >> 1);
-      bool ok = mbar_wait(&bars->tfull[b], use & 1, abort, err, 5);
-      if (!__all_sync(0xffffffffu, ok)) break;
-      tc_fence_after();
-      const int64_t jb = (int64_t)(t_begin + t) * kTN + h * (kTN / 2);
-      const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * (kTN / 2));
-#pragma unroll 1
-      for (int c = 0; c < kTN / 64; ++c) {
-        uint32_t rv[32];
-        tmem_ld32_issue(tb + (uint32_t)(c * 32), rv);
-        tmem_wait();
-        pin(rv);
-        if constexpr (kCollect) {
-          collect_chunk(rv, jb + c * 32, n, i, t_row, ra, ca.cnt, ca.buf, ca.cap);
-        } else {
-          fold_chunk<C>(rv, jb + c * 32, n, i, lv, li, thr, mp);
-        }
+    for (int64_t cc = c0; cc < ctas; ++cc) {
+      const int64_t b = range_begin(cc, work, ctas);
+      if (b >= x1) break;
+      const int64_t slot = (cc * 2 + (b / n_tiles == qb ? 0 : 1)) * kTM + r;
+      for (int e = 0; e < C; ++e) {
+        const int32_t j = part_idx[slot * kCandC + h * C + e];
+        const float v = part_val[slot * kCandC + h * C + e];
+        if (j >= 0 && v > thr) list_insert<C>(lv, li, thr, mp, v, j);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->tempty[b]);
     }
-    if (!kCollect && row_ok) {
-      const float sc = out_scale ? *out_scale : 1.f;
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        cand_val[i * kCandC + h * C + c] = lv[c] * sc;
-        cand_idx[i * kCandC + h * C + c] = li[c];
-      }
+    for (int c = 0; c < C; ++c) {
+      cand_val[i * kCandC + h * C + c] = lv[c];
+      cand_idx[i * kCandC + h * C + c] = li[c];
     }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
@@ -351,54 +458,73 @@ __global__ void k_gather_rows(const uint8_t* __restrict__ x, int row_bytes, cons
   for (int c = threadIdx.x; c < row_bytes / 16; c += blockDim.x) dst[c] = src ? src[c] : make_uint4(0, 0, 0, 0);
 }
 
+// One persistent CTA per SM (at most one per work item); list mode adds the
+// partial-list area and the merge of split query blocks.
+template <bool kCollect, bool kE4M3>
+ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, int64_t n_pad,
+                       int64_t n_rows, int kb_count, float* cand_val, int32_t* cand_idx, const float* out_scale,
+                       const CollectArgs& ca, int32_t* err, cudaStream_t s) {
+  int nstages;
+  size_t smem;
+  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
+  int sms = 152, dev = 0;
+  ANCKA_CUDA(cudaGetDevice(&dev));
+  ANCKA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t qblocks = ceil_div(n_rows, kTM);
+  const int n_tiles = (int)ceil_div(n_pad, kTN);
+  const int64_t work = qblocks * n_tiles;
+  const int64_t ctas = std::min<int64_t>(sms, work);
+  float* part_val = nullptr;
+  int32_t* part_idx = nullptr;
+  if (!kCollect) {
+    ANCKA_TRY(ws.alloc(&part_val, (size_t)ctas * 2 * kTM * kCandC));
+    ANCKA_TRY(ws.alloc(&part_idx, (size_t)ctas * 2 * kTM * kCandC));
+  }
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<kCollect, kE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_knn_tc<kCollect, kE4M3><<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, n_pad, qblocks, kb_count, nstages,
+                                                                   cand_val, cand_idx, out_scale, part_val,
+                                                                   part_idx, ca, err);
+  ANCKA_LAUNCHED();
+  if (!kCollect) {
+    k_merge_lists<<<(unsigned)qblocks, kTM, 0, s>>>(n_tiles, work, ctas, part_val, part_idx, ca.a_rows, n_rows,
+                                                    cand_val, cand_idx);
+    ANCKA_LAUNCHED();
+  }
+  return ANCKA_OK;
+}
+
 }  // namespace
 
 bool knn_tc_available() { return true; }
 
 int knn_tc_max_dp() { return 512; }
 
-ancka_status knn_candidates_bf16(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx, int32_t* err,
-                                 cudaStream_t s) {
+ancka_status knn_candidates_bf16(Workspace& ws, const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
+                                 int32_t* err, cudaStream_t s) {
   const int kb_count = pr.dp / 64;
   if (pr.dp % 64 != 0 || kb_count < 1 || pr.dp > knn_tc_max_dp()) {
     set_error("BF16 contraction supports up to %d features (got %d)", knn_tc_max_dp(), pr.dp);
     return ANCKA_ERR_UNSUPPORTED;
   }
-  int nstages;
-  size_t smem;
-  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
   CUtensorMap ta, tb;
   ANCKA_TRY(make_map(&ta, pr.xb, pr.dp, pr.n_pad, kTM, 2));
   ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
-  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CollectArgs none{};
-  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
-  k_knn_tc<false, false><<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(
-      ta, tb, n, pr.n_pad, kb_count, nstages, all_tiles, cand_val, cand_idx, nullptr, none, err);
-  ANCKA_LAUNCHED();
-  return ANCKA_OK;
+  return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n, kb_count, cand_val, cand_idx, nullptr, none, err, s);
 }
 
-ancka_status knn_candidates_fp8(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx, int32_t* err,
-                                cudaStream_t s) {
+ancka_status knn_candidates_fp8(Workspace& ws, const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
+                                int32_t* err, cudaStream_t s) {
   const int kb_count = pr.dp8 / 128;
   if (!pr.x8 || pr.dp8 % 128 != 0 || kb_count < 1 || pr.dp8 > knn_tc_max_dp_fp8()) {
     set_error("FP8 contraction supports up to %d features (got %d)", knn_tc_max_dp_fp8(), pr.dp8);
     return ANCKA_ERR_UNSUPPORTED;
   }
-  int nstages;
-  size_t smem;
-  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
   CUtensorMap ta, tb;
   ANCKA_TRY(make_map(&ta, pr.x8, pr.dp8, pr.n_pad, kTM, 1));
   ANCKA_TRY(make_map(&tb, pr.x8, pr.dp8, pr.n_pad, kTN, 1));
-  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CollectArgs none{};
-  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
-  k_knn_tc<false, true><<<(unsigned)(pr.n_pad / kTM), kThreads, smem, s>>>(
-      ta, tb, n, pr.n_pad, kb_count, nstages, all_tiles, cand_val, cand_idx, pr.inv_s2, none, err);
-  ANCKA_LAUNCHED();
-  return ANCKA_OK;
+  return launch_tc<false, true>(ws, ta, tb, n, pr.n_pad, n, kb_count, cand_val, cand_idx, pr.inv_s2, none, err, s);
 }
 
 int knn_tc_max_dp_fp8() { return 1024; }
@@ -407,9 +533,6 @@ int knn_tc_max_dp_fp8() { return 1024; }
 ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
                                     float* cand_val, int32_t* cand_idx, int32_t* err, cudaStream_t s) {
   const int kb_count = pr.dp / 64;
-  int nstages;
-  size_t smem;
-  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
   const int64_t n_a_pad = round_up(n_a, kTM);
   __nv_bfloat16* af;
   ANCKA_TRY(ws.alloc(&af, (size_t)n_a_pad * pr.dp));
@@ -419,21 +542,13 @@ ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n,
   CUtensorMap ta, tb;
   ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM, 2));
   ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
-  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CollectArgs ca{rows, n_a, nullptr, nullptr, nullptr, 0};
-  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
-  k_knn_tc<false, false><<<(unsigned)(n_a_pad / kTM), kThreads, smem, s>>>(
-      ta, tb, n, pr.n_pad, kb_count, nstages, all_tiles, cand_val, cand_idx, nullptr, ca, err);
-  ANCKA_LAUNCHED();
-  return ANCKA_OK;
+  return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n_a, kb_count, cand_val, cand_idx, nullptr, ca, err, s);
 }
 
 ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
                               const float* thr, int32_t* cnt, int32_t* buf, int cap, int32_t* err, cudaStream_t s) {
   const int kb_count = pr.dp / 64;
-  int nstages;
-  size_t smem;
-  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
   const int64_t n_a_pad = round_up(n_a, kTM);
   __nv_bfloat16* af;
   ANCKA_TRY(ws.alloc(&af, (size_t)n_a_pad * pr.dp));
@@ -443,21 +558,8 @@ ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const
   CUtensorMap ta, tb;
   ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM, 2));
   ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
-  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CollectArgs ca{rows, n_a, thr, cnt, buf, cap};
-  // split the key sweep so that about two waves of CTAs run
-  int sms = 152, dev = 0;
-  ANCKA_CUDA(cudaGetDevice(&dev));
-  ANCKA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int all_tiles = (int)ceil_div(pr.n_pad, kTN);
-  const int64_t qblocks = n_a_pad / kTM;
-  int splits = (int)std::max<int64_t>(1, std::min<int64_t>(all_tiles, (2 * sms) / std::max<int64_t>(1, qblocks)));
-  const int tps = (int)ceil_div(all_tiles, splits);
-  splits = (int)ceil_div(all_tiles, tps);
-  k_knn_tc<true, false><<<dim3((unsigned)qblocks, (unsigned)splits), kThreads, smem, s>>>(
-      ta, tb, n, pr.n_pad, kb_count, nstages, tps, nullptr, nullptr, nullptr, ca, err);
-  ANCKA_LAUNCHED();
-  return ANCKA_OK;
+  return launch_tc<true, false>(ws, ta, tb, n, pr.n_pad, n_a, kb_count, nullptr, nullptr, nullptr, ca, err, s);
 }
 
 }  // namespace ancka
