@@ -220,10 +220,10 @@ def adjusted_rand(a, b):
 
 
 def warm_report(args):
-    """Learned warm start (BASELINE config 5): an MLP 2d -> 256 -> k trained on
-    ANCKA's own blocks of multiplex graphs (the config-3 generator at n =
-    warm_train_n, d = 256, k = 20, seeds 100...), then plain (InitBCM) vs
-    learned start on the DC-SBM generator re-run with k = 20 and d = 256 (seeds
+    """Learned warm start: an MLP 2d -> 256 -> k trained on ANCKA's own
+    blocks of multiplex SBM graphs (three layers, n = warm_train_n, d = 256,
+    k = 20, seeds 100...), then plain (InitBCM) vs learned start on degree-
+    corrected SBM graphs (n = warm_eval_n, 25 n edges, k = 20, d = 256, seeds
     200...), both in the paper's early-termination mode (eps_Q = 0.005, at most
     100 hops, tau = 5, T_i = 1 as for the large graphs)."""
     import torch
@@ -278,14 +278,14 @@ def warm_report(args):
         "graphs": args.warm_graphs, "n": args.warm_train_n, "d": d, "k": k, "epochs": args.warm_epochs,
         "loss_first": round(float(losses[0]), 5), "loss_last": round(float(losses[-1]), 5),
         "train_s": round(t_train, 3), "data_s": round(t_data, 1)},
-        "eval": {"generator": "DC-SBM (config 4) with k=20, d=256", "n": args.warm_eval_n,
+        "eval": {"generator": "DC-SBM, 25 n edges, k=20, d=256", "n": args.warm_eval_n,
                  "mode": "early termination (Eq. tcond-1/2), eps_Q=0.005, at most 100 hops", "runs": runs,
                  "plain_start_fallback_rate": fb}}), flush=True)
 
 
 def spmm_probe(args):
-    """SpMM in the HBM regime: the DC-SBM generator at N nodes (config-4
-    settings: k = 47, d = 100, beta = 0.4, T_i = 1, T = 10), where the block Q
+    """SpMM in the HBM regime: a degree-corrected SBM graph at N nodes (25 N
+    edges, k = 47, d = 100, beta = 0.4, T_i = 1, T = 10), where the block Q
     (N x 48 FP32) exceeds L2.  Compulsory bytes per hop: the merged topology
     CSR (int64 row pointers, int32 columns, FP32 values, row scale), the KNN
     CSR, one read of Q and one write of Z."""
