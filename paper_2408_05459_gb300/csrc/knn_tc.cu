@@ -77,20 +77,56 @@ __device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t
       "l"(da), "l"(db), "r"(kIdescE4M3), "r"(accum)
       : "memory");
 }
+// Row lists are kept sorted in descending score order, lv[0] >= ... >=
+// lv[C-1], so the threshold is lv[C-1] and an insert is C independent
+// select pairs (two levels deep) instead of a C-long minimum scan.  A score
+// equal to an entry goes after it: among equal scores the earlier key stays.
+template <int C>
+__device__ __forceinline__ void sorted_insert(float (&lv)[C], int32_t (&li)[C], float s, int32_t j) {
+#pragma unroll
+  for (int c = C - 1; c >= 1; --c) {
+    const bool at_or_before = s > lv[c];
+    const bool before_prev = s > lv[c - 1];
+    lv[c] = at_or_before ? (before_prev ? lv[c - 1] : s) : lv[c];
+    li[c] = at_or_before ? (before_prev ? li[c - 1] : j) : li[c];
+  }
+  if (s > lv[0]) {
+    lv[0] = s;
+    li[0] = j;
+  }
+}
+
+// r[e] for a lane-dependent e in 0..31: a five-level select tree
+__device__ __forceinline__ float pick32(const uint32_t (&r)[32], int e) {
+  float v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float((e & 16) ? r[q + 16] : r[q]);
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) v[q] = (e & w) ? v[q + w] : v[q];
+  return v[0];
+}
+
 // Fold one 32-key chunk (scores in r, keys j0..j0+31) into the row's list.
 template <int C>
 __device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], int64_t j0, int64_t n, int64_t i,
-                                           float (&lv)[C], int32_t (&li)[C], float& thr, int& mp) {
+                                           float (&lv)[C], int32_t (&li)[C]) {
   // skip the chunk when no lane of the warp has a key above its threshold
-  float mx = __uint_as_float(r[0]);
+  float m[16];
 #pragma unroll
-  for (int e = 1; e < 32; ++e) mx = fmaxf(mx, __uint_as_float(r[e]));
-  if (!__any_sync(0xffffffffu, mx > thr)) return;
+  for (int q = 0; q < 16; ++q) m[q] = fmaxf(__uint_as_float(r[q]), __uint_as_float(r[q + 16]));
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) m[q] = fmaxf(m[q], m[q + w]);
+  const float thr0 = lv[C - 1];
+  if (!__any_sync(0xffffffffu, m[0] > thr0)) return;
   // pass mask against the threshold at chunk start (it only rises, so the
   // mask is a superset); padding keys and the row itself removed
   uint32_t pm = 0;
 #pragma unroll
-  for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(r[e]) > thr ? 1u : 0u) << e;
+  for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(r[e]) > thr0 ? 1u : 0u) << e;
   if (j0 + 32 > n) pm &= (j0 >= n) ? 0u : ((1u << (uint32_t)(n - j0)) - 1u);
   if (i >= j0 && i < j0 + 32) pm &= ~(1u << (uint32_t)(i - j0));
   // one insert per passing key; lanes without keys idle
@@ -98,11 +134,8 @@ __device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], int64_t j0, 
     if (pm) {
       const int e = __ffs(pm) - 1;
       pm &= pm - 1;
-      float val = __uint_as_float(r[0]);
-#pragma unroll
-      for (int q = 1; q < 32; ++q)
-        if (e == q) val = __uint_as_float(r[q]);
-      if (val > thr) list_insert<C>(lv, li, thr, mp, val, (int32_t)(j0 + e));
+      const float val = pick32(r, e);
+      if (val > lv[C - 1]) sorted_insert<C>(lv, li, val, (int32_t)(j0 + e));
     }
   }
 }
@@ -329,8 +362,6 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         lv[c] = -INFINITY;
         li[c] = -1;
       }
-      float thr = -INFINITY;
-      int mp = 0;
       for (int t = t0; t < t1; ++t, ++g) {
         const int b = (int)(g & 1);
         const uint32_t use = (uint32_t)(g >> 1);
@@ -351,7 +382,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           if constexpr (kCollect) {
             collect_chunk(rv, jb + c * 32, n, i, t_row, ra, ca.cnt, ca.buf, ca.cap);
           } else {
-            fold_chunk<C>(rv, jb + c * 32, n, i, lv, li, thr, mp);
+            fold_chunk<C>(rv, jb + c * 32, n, i, lv, li);
           }
         }
         tc_fence_before();
@@ -412,8 +443,6 @@ __global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, 
       lv[c] = -INFINITY;
       li[c] = -1;
     }
-    float thr = -INFINITY;
-    int mp = 0;
     for (int64_t cc = c0; cc < ctas; ++cc) {
       const int64_t b = range_begin(cc, work, ctas);
       if (b >= x1) break;
@@ -421,7 +450,7 @@ __global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, 
       for (int e = 0; e < C; ++e) {
         const int32_t j = part_idx[slot * kCandC + h * C + e];
         const float v = part_val[slot * kCandC + h * C + e];
-        if (j >= 0 && v > thr) list_insert<C>(lv, li, thr, mp, v, j);
+        if (j >= 0 && v > lv[C - 1]) sorted_insert<C>(lv, li, v, j);
       }
     }
 #pragma unroll
