@@ -515,19 +515,20 @@ k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, float2* __re
   float hi[16], lo[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
-  for (int64_t rb = r0; rb < r1; rb += kGramRows) {
-    const int rows = (int)((r1 - rb) < kGramRows ? (r1 - rb) : kGramRows);
+  // tiles as tall as the buffer allows at this width (row stride 4 nb), so
+  // that a CTA's rows arrive in few load waves
+  const int tld = 4 * nb;
+  const int trows = (kGramRows * kGramLd) / tld;
+  for (int64_t rb = r0; rb < r1; rb += trows) {
+    const int rows = (int)((r1 - rb) < trows ? (r1 - rb) : trows);
     __syncthreads();
-    for (int e = t; e < kGramRows * nb; e += kGramThreads) {
+    for (int e = t; e < rows * nb; e += kGramThreads) {
       const int r = e / nb, c = 4 * (e % nb);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < rows) {
-        v = *reinterpret_cast<const float4*>(Z + (rb + r) * ldz + c);
-        if (c + 1 >= w) v.y = 0.f;  // columns >= w read as zero
-        if (c + 2 >= w) v.z = 0.f;
-        if (c + 3 >= w) v.w = 0.f;
-      }
-      *reinterpret_cast<float4*>(&T[r * kGramLd + c]) = v;
+      float4 v = *reinterpret_cast<const float4*>(Z + (rb + r) * ldz + c);
+      if (c + 1 >= w) v.y = 0.f;  // columns >= w read as zero
+      if (c + 2 >= w) v.z = 0.f;
+      if (c + 3 >= w) v.w = 0.f;
+      *reinterpret_cast<float4*>(&T[r * tld + c]) = v;
     }
     __syncthreads();
     if (active) {
@@ -535,8 +536,8 @@ k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, float2* __re
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[e] = 0.f;
       for (int r = sub; r < rows; r += S) {
-        const float4 xa = *reinterpret_cast<const float4*>(&T[r * kGramLd + 4 * A]);
-        const float4 xb = *reinterpret_cast<const float4*>(&T[r * kGramLd + 4 * B]);
+        const float4 xa = *reinterpret_cast<const float4*>(&T[r * tld + 4 * A]);
+        const float4 xb = *reinterpret_cast<const float4*>(&T[r * tld + 4 * B]);
         const float a4[4] = {xa.x, xa.y, xa.z, xa.w}, b4[4] = {xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -582,26 +583,47 @@ k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, float2* __re
 // FP32.  A non-positive pivot marks the status and is replaced by a tiny one
 // so the run finishes.  csm: G, R, X (w*w doubles each); scratch: up to
 // max(w(w+1)/2, 256) float pairs.
+// 1/sqrt(d) for d in [1e-30, 1e30]: FP32 seed, then two Newton-Raphson
+// steps y <- y (3 - d y^2) / 2 in FP64 (the error squares each step:
+// ~2^-22 -> ~2^-43 -> FP64 rounding); outside that range the exact quotient.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  const double h = -0.5 * d;
+  y = y * fma(h, y * y, 1.5);
+  y = y * fma(h, y * y, 1.5);
+  return y;
+}
+
+// Sums the CTA partials into G (FP64), factors G = R^T R and writes R^-1
+// (row-major, upper triangular, FP32).  Right-looking Cholesky: at step j the
+// pivot gives r_j = 1/R_jj, row j of R is G's row j times r_j, and the
+// trailing block loses the outer product of that row.  R^-1 comes from the
+// same steps as Y = L^-1 (L = R^T) by Gauss-Jordan elimination on [L | I]:
+// row j of Y is scaled by r_j and row j times L_ij is taken from every later
+// row i.  Each step is a few dependent FP64 operations across the CTA, with
+// no division or square root on the chain.
 __device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
                                int32_t* __restrict__ status, double* csm, float2* scratch) {
   const int ww = w * w, np = w * (w + 1) / 2;
   double* G = csm;
   double* R = csm + ww;
-  double* X = csm + 2 * ww;
+  double* Y = csm + 2 * ww;
+  double* rj_s = csm + 3 * ww;
   {
     // Tn threads per entry, each summing a strided subset of the CTA
-    // partials with eight loads in flight; subsets combined in fixed order
+    // partials with sixteen loads in flight; subsets combined in fixed order
     const int Tn = max(1, min((int)blockDim.x / np, 16));
     for (int e = threadIdx.x; e < np * Tn; e += blockDim.x) {
       const int entry = e / Tn, sub = e % Tn;
       float h = 0.f, l = 0.f;
       int bb = sub;
-      for (; bb + 7 * Tn < nblk; bb += 8 * Tn) {
-        float2 v[8];
+      for (; bb + 15 * Tn < nblk; bb += 16 * Tn) {
+        float2 v[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcg(partial + (int64_t)(bb + u * Tn) * np + entry);
+        for (int u = 0; u < 16; ++u) v[u] = __ldcg(partial + (int64_t)(bb + u * Tn) * np + entry);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) ff_add(h, l, v[u].x, v[u].y);
+        for (int u = 0; u < 16; ++u) ff_add(h, l, v[u].x, v[u].y);
       }
       for (; bb < nblk; bb += Tn) {
         const float2 v = __ldcg(partial + (int64_t)bb * np + entry);
@@ -611,7 +633,7 @@ __device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int
     }
     for (int e = threadIdx.x; e < ww; e += blockDim.x) {
       R[e] = 0.0;
-      X[e] = 0.0;
+      Y[e] = (e / w == e % w) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < np; e += blockDim.x) {
@@ -629,34 +651,47 @@ __device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int
     __syncthreads();
   }
   for (int j = 0; j < w; ++j) {
+    const int m = w - 1 - j;  // rows / columns after j
     if (threadIdx.x == 0) {
       double d = G[j * w + j];
-      for (int k = 0; k < j; ++k) d -= R[k * w + j] * R[k * w + j];
       if (!(d > 1e-300)) {
         atomicExch(status, 1);
         d = 1e-300;
       }
-      R[j * w + j] = sqrt(d);
+      const double r = rsqrt_newton(d);
+      rj_s[0] = r;
+      R[j * w + j] = d * r;
     }
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) {
-      double v = G[j * w + i];
-      for (int k = 0; k < j; ++k) v -= R[k * w + j] * R[k * w + i];
-      R[j * w + i] = v / R[j * w + j];
+    const double r = rj_s[0];
+    // row j of R right of the pivot; row j of Y (entries 0..j)
+    for (int e = threadIdx.x; e < m + j + 1; e += blockDim.x) {
+      if (e < m) {
+        R[j * w + j + 1 + e] = G[j * w + j + 1 + e] * r;
+      } else {
+        const int a = e - m;
+        Y[j * w + a] *= r;
+      }
+    }
+    __syncthreads();
+    // trailing update of G (upper triangle) and of the later rows of Y
+    for (int e = threadIdx.x; e < m * m + m * (j + 1); e += blockDim.x) {
+      if (e < m * m) {
+        const int i = j + 1 + e / m, l = j + 1 + e % m;
+        if (i <= l) G[i * w + l] = fma(-R[j * w + i], R[j * w + l], G[i * w + l]);
+      } else {
+        const int f = e - m * m;
+        const int i = j + 1 + f / (j + 1), a = f % (j + 1);
+        Y[i * w + a] = fma(-R[j * w + i], Y[j * w + a], Y[i * w + a]);
+      }
     }
     __syncthreads();
   }
-  // columns of R^-1 by back substitution, one thread per column
-  for (int c = threadIdx.x; c < w; c += blockDim.x) {
-    X[c * w + c] = 1.0 / R[c * w + c];
-    for (int i = c - 1; i >= 0; --i) {
-      double v = 0.0;
-      for (int k = i + 1; k <= c; ++k) v += R[i * w + k] * X[k * w + c];
-      X[i * w + c] = -v / R[i * w + i];
-    }
+  // R^-1 = Y^T
+  for (int e = threadIdx.x; e < ww; e += blockDim.x) {
+    const int a = e / w, c = e % w;
+    Rinv_out[e] = a <= c ? (float)Y[c * w + a] : 0.f;
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < ww; e += blockDim.x) Rinv_out[e] = (float)X[e];
 }
 
 // out[i, c] = sum_{a <= c} Z[i, a] Rinv[a, c]  (padding columns -> 0)
@@ -1680,10 +1715,10 @@ ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64
 ancka_status cholqr2(Workspace& ws, const Ctx& c, float* Z, float* Q, int w, float2* gpart, int gblk,
                      unsigned int* ticket, float* Rinv, int32_t* status) {
   cudaStream_t s = c.s;
-  const size_t csmem = (size_t)(3 * w * w) * sizeof(double);
+  const size_t csmem = (size_t)(3 * w * w + 1) * sizeof(double);
   static bool configured = false;
   if (!configured) {
-    ANCKA_CUDA(cudaFuncSetAttribute(k_gram_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 65 * 65 * 8));
+    ANCKA_CUDA(cudaFuncSetAttribute(k_gram_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (3 * 65 * 65 + 1) * 8));
     configured = true;
   }
   k_gram_chol<<<gblk, kGramThreads, csmem, s>>>(Z, c.ld, c.n, w, gpart, ticket, Rinv, status);

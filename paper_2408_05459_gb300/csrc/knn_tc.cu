@@ -34,9 +34,11 @@ namespace {
 
 constexpr int kTM = 128;                 // query rows per CTA = TMEM lanes
 constexpr int kTN = 256;                 // key rows per tile = accumulator columns
-constexpr int kEpiWarps = 8;
+constexpr int kLists = 2;                // lists per row = column slices of every tile
+constexpr int kEpiWarps = 4 * kLists;    // one warp per (TMEM lane quarter, column slice)
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kListC = kCandC / 2;     // per-thread list (two per row)
+constexpr int kListC = kCandC / kLists;  // entries of each list
+constexpr int kSliceN = kTN / kLists;    // columns of a tile per slice
 constexpr int kABytes = kTM * kTKB;      // 16 KB per 128-byte block of A
 constexpr int kBBytes = kTN * kTKB;      // 32 KB per stage of B
 constexpr int kMmaPerStage = 4;          // 32 bytes of K per MMA: 16 BF16 or 32 FP8
@@ -337,7 +339,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   } else {
     const int ew = warp - 2;   // epilogue warp 0..7
     const int q = warp & 3;    // TMEM lane quarter this warp may access
-    const int h = ew >> 2;     // column half of every tile
+    const int h = ew >> 2;     // column slice of every tile
     const int r = q * 32 + lane;
     constexpr int C = kListC;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
@@ -371,10 +373,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           break;
         }
         tc_fence_after();
-        const int64_t jb = (int64_t)t * kTN + h * (kTN / 2);
-        const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * (kTN / 2));
+        const int64_t jb = (int64_t)t * kTN + h * kSliceN;
+        const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * kSliceN);
 #pragma unroll 1
-        for (int c = 0; c < kTN / 64; ++c) {
+        for (int c = 0; c < kSliceN / 32; ++c) {
           uint32_t rv[32];
           tmem_ld32_issue(tb + (uint32_t)(c * 32), rv);
           tmem_wait();
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, 
   if (ra >= n_rows) return;
   const int64_t i = a_rows ? (int64_t)a_rows[ra] : ra;
   constexpr int C = kListC;
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < kLists; ++h) {
     float lv[C];
     int32_t li[C];
 #pragma unroll
