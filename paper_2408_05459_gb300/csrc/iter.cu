@@ -945,16 +945,29 @@ __device__ int polar_jacobi(const float* M, int k, float* A, float* V, float* u,
   return sweeps;
 }
 
+// barrier of the first n threads of the CTA (all of them: __syncthreads)
+__device__ __forceinline__ void ns_sync(int nthr) {
+  if (nthr == (int)blockDim.x)
+    __syncthreads();
+  else
+    asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+}
+
 // R = polar(M)^T by the Newton-Schulz iteration X <- X (3I - X^T X) / 2 from
 // X = M / s, s >= ||M||_2 (min of the Frobenius norm and sqrt(||M||_1
 // ||M||_inf)); every singular value of X then lies in (0, 1] and converges to
 // 1, so X -> U V^T for M = U Omega V^T.  Stops once max |X^T X - I| < tol
 // (after one more step).  Returns false (R untouched) if M is zero or the
-// iteration has not converged after kNsMaxIter steps.
+// iteration has not converged after kNsMaxIter steps.  KM >= k bounds the
+// terms of each k x k product so that they are unrolled (terms past k
+// predicated off) and their shared-memory loads overlap; the largest
+// deviation of each step is left per warp and read back after the barrier.
+template <int KM>
 __device__ bool polar_newton_schulz(const float* M, int k, float* X, float* Xn, float* P, float* Rs, int ldr) {
   __shared__ float rsum[64], csum[64], f2s[64];
-  __shared__ unsigned int dev_s[3];
+  __shared__ float wdl[2][kDiscThreads / 32];
   __shared__ float scale_s;
+  __shared__ int conv_s;
   const int kk = k * k;
   if (threadIdx.x < k) {  // row / column absolute sums and squared row norms
     float rs = 0.f, cs = 0.f, f2 = 0.f;
@@ -968,7 +981,6 @@ __device__ bool polar_newton_schulz(const float* M, int k, float* X, float* Xn, 
     csum[threadIdx.x] = cs;
     f2s[threadIdx.x] = f2;
   }
-  if (threadIdx.x < 3) dev_s[threadIdx.x] = 0u;
   __syncthreads();
   if (threadIdx.x == 0) {
     float n1 = 0.f, ninf = 0.f, fro2 = 0.f;
@@ -989,43 +1001,56 @@ __device__ bool polar_newton_schulz(const float* M, int k, float* X, float* Xn, 
     X[r * kDiscLd + c] = M[r * kDiscLd + c] * inv;
   }
   __syncthreads();
-  bool conv = false;
-  for (int t = 0; t < kNsMaxIter; ++t) {
-    const int slot = t % 3;
-    if (threadIdx.x == 0) dev_s[(t + 1) % 3] = 0u;
-    float dl = 0.f;
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // P = X^T X
-      const int a = e / k, b = e % k;
-      float p = 0.f;
-      for (int r = 0; r < k; ++r) p = fmaf(X[r * kDiscLd + a], X[r * kDiscLd + b], p);
-      P[a * kDiscLd + b] = p;
-      dl = fmaxf(dl, fabsf(p - (a == b ? 1.f : 0.f)));
+  // small matrices run on the first 128 threads behind named barrier 1 (the
+  // other warps wait at the closing __syncthreads); larger ones on the CTA
+  const int nthr = kk <= 128 ? 128 : (int)blockDim.x;
+  const int nw = nthr >> 5;
+  if ((int)threadIdx.x < nthr) {
+    bool conv = false;
+    for (int t = 0; t < kNsMaxIter; ++t) {
+      float dl = 0.f;
+      for (int e = threadIdx.x; e < kk; e += nthr) {  // P = X^T X
+        const int a = e / k, b = e % k;
+        float p = 0.f;
+#pragma unroll
+        for (int r = 0; r < KM; ++r)
+          if (r < k) p = fmaf(X[r * kDiscLd + a], X[r * kDiscLd + b], p);
+        P[a * kDiscLd + b] = p;
+        const float dv = fabsf(p - (a == b ? 1.f : 0.f));
+        dl = (dv == dv) ? fmaxf(dl, dv) : INFINITY;  // a NaN never converges
+      }
+      for (int off = 16; off >= 1; off >>= 1) dl = fmaxf(dl, __shfl_xor_sync(0xffffffffu, dl, off));
+      if ((threadIdx.x & 31) == 0) wdl[t & 1][threadIdx.x >> 5] = dl;
+      ns_sync(nthr);
+      for (int e = threadIdx.x; e < kk; e += nthr) {  // X' = 1.5 X - 0.5 X P
+        const int r = e / k, b = e % k;
+        float s = 0.f;
+#pragma unroll
+        for (int a = 0; a < KM; ++a)
+          if (a < k) s = fmaf(X[r * kDiscLd + a], P[a * kDiscLd + b], s);
+        Xn[r * kDiscLd + b] = fmaf(-0.5f, s, 1.5f * X[r * kDiscLd + b]);
+      }
+      ns_sync(nthr);
+      float* tmp = X;
+      X = Xn;
+      Xn = tmp;
+      float dmax = 0.f;
+#pragma unroll
+      for (int q = 0; q < kDiscThreads / 32; ++q) dmax = fmaxf(dmax, q < nw ? wdl[t & 1][q] : 0.f);
+      if (dmax < tol) {
+        conv = true;
+        break;
+      }
     }
-    for (int off = 16; off >= 1; off >>= 1) dl = fmaxf(dl, __shfl_xor_sync(0xffffffffu, dl, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(&dev_s[slot], __float_as_uint(dl));  // dl >= 0 (or NaN: never converges)
-    __syncthreads();
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // X' = 1.5 X - 0.5 X P
-      const int r = e / k, b = e % k;
-      float s = 0.f;
-      for (int a = 0; a < k; ++a) s = fmaf(X[r * kDiscLd + a], P[a * kDiscLd + b], s);
-      Xn[r * kDiscLd + b] = fmaf(-0.5f, s, 1.5f * X[r * kDiscLd + b]);
-    }
-    __syncthreads();
-    float* tmp = X;
-    X = Xn;
-    Xn = tmp;
-    if (__uint_as_float(dev_s[slot]) < tol) {
-      conv = true;
-      break;
-    }
-  }
-  if (!conv) return false;
-  for (int e = threadIdx.x; e < k * ldr; e += blockDim.x) {  // R = X^T
-    const int a = e / ldr, b = e % ldr;
-    Rs[e] = b < k ? X[b * kDiscLd + a] : 0.f;
+    if (conv)
+      for (int e = threadIdx.x; e < k * ldr; e += nthr) {  // R = X^T
+        const int a = e / ldr, b = e % ldr;
+        Rs[e] = b < k ? X[b * kDiscLd + a] : 0.f;
+      }
+    if (threadIdx.x == 0) conv_s = conv ? 1 : 0;
   }
   __syncthreads();
-  return true;
+  return conv_s != 0;
 }
 
 // Discretize (Def. 2, Alg. 5) as one persistent cooperative kernel.  Per
@@ -1040,7 +1065,7 @@ __device__ bool polar_newton_schulz(const float* M, int k, float* X, float* Xn, 
 //     or Jacobi for rank-deficient M) and obj = n - 2 tr(Omega), and stops
 //     once |obj - obj_prev| <= 4 eps max(1, |obj|).  All CTAs compute the
 //     same R and the same decision from the same totals.
-__global__ void __launch_bounds__(kDiscThreads)
+__global__ void __launch_bounds__(kDiscThreads, 1)
 k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_iter, int32_t* __restrict__ labels,
              DiscState st, int32_t* __restrict__ iters_out, int32_t* __restrict__ flags) {
   extern __shared__ __align__(16) float dsm_f[];
@@ -1184,8 +1209,14 @@ k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_it
     for (int c = 0; c < k; ++c) empty |= cnt_s[c] == 0;
     int sweeps = 0;
     bool ok = false;
-    if (!empty) ok = polar_newton_schulz(M, k, region + kDiscLd * 64, region + 2 * kDiscLd * 64,
-                                         region + 3 * kDiscLd * 64, Rs, ldr);
+    if (!empty) {
+      float* X0 = region + kDiscLd * 64;
+      float* X1 = region + 2 * kDiscLd * 64;
+      float* P0 = region + 3 * kDiscLd * 64;
+      ok = k <= 16   ? polar_newton_schulz<16>(M, k, X0, X1, P0, Rs, ldr)
+           : k <= 32 ? polar_newton_schulz<32>(M, k, X0, X1, P0, Rs, ldr)
+                     : polar_newton_schulz<64>(M, k, X0, X1, P0, Rs, ldr);
+    }
     if (!ok)
       sweeps = polar_jacobi(M, k, region + kDiscLd * 64, region + 2 * kDiscLd * 64, region + 3 * kDiscLd * 64, Rs,
                             ldr, &rotated);
