@@ -113,11 +113,25 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) fma4(accA, w[q], x[q]);
     }
-    for (; p < e; p += S) {
-      const int32_t j = *(a.colA + p);
-      float w = a.valA ? *(a.valA + p) : 1.f;
-      if (a.csA) w *= a.csA[j];
-      fma4(accA, w, *reinterpret_cast<const float4*>(a.srcA + (int64_t)j * a.ldA + 4 * g));
+    if (p < e) {  // at most three entries left: one predicated batch
+      int32_t j[3];
+      float w[3];
+      float4 x[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) j[q] = p + q * S < e ? *(a.colA + p + q * S) : -1;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        w[q] = 0.f;
+        x[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j[q] >= 0) {
+          w[q] = a.valA ? *(a.valA + p + q * S) : 1.f;
+          if (a.csA) w[q] *= a.csA[j[q]];
+          x[q] = *reinterpret_cast<const float4*>(a.srcA + (int64_t)j[q] * a.ldA + 4 * g);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (j[q] >= 0) fma4(accA, w[q], x[q]);
     }
     if (a.ptrB) {
       int64_t pb = a.ptrB[i] + sl;
@@ -132,8 +146,25 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) fma4(accB, *(a.valB + pb + q * S), x[q]);
       }
-      for (; pb < eb; pb += S)
-        fma4(accB, *(a.valB + pb), *reinterpret_cast<const float4*>(a.srcB + (int64_t)*(a.colB + pb) * a.ldB + 4 * g));
+      if (pb < eb) {  // at most three entries left: one predicated batch
+        int32_t j[3];
+        float w[3];
+        float4 x[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) j[q] = pb + q * S < eb ? *(a.colB + pb + q * S) : -1;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          w[q] = 0.f;
+          x[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (j[q] >= 0) {
+            w[q] = *(a.valB + pb + q * S);
+            x[q] = *reinterpret_cast<const float4*>(a.srcB + (int64_t)j[q] * a.ldB + 4 * g);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (j[q] >= 0) fma4(accB, w[q], x[q]);
+      }
     }
   }
   if constexpr (S > 1) {  // every lane of the warp takes part
@@ -436,7 +467,10 @@ ancka_status spmm(const SpmmArgs& a0, cudaStream_t s) {
         if (longs) { k_spmm_long<2><<<lgrid, 256, 0, s>>>(a, part); k_spmm_long_finish<2><<<fgrid, 256, 0, s>>>(a, part); }
         break;
       case 4:
-        launch_spmm_slices<4>(a, S, s);
+        if (nv4 == 3 && S == 1)  // three chunks: three lanes per row, no idle lane
+          launch_spmm<3, 1>(a, s);
+        else
+          launch_spmm_slices<4>(a, S, s);
         if (longs) { k_spmm_long<4><<<lgrid, 256, 0, s>>>(a, part); k_spmm_long_finish<4><<<fgrid, 256, 0, s>>>(a, part); }
         break;
       case 8:
