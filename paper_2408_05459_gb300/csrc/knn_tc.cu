@@ -183,6 +183,18 @@ struct CollectArgs {
 // combines the pieces of every split block.
 __device__ __forceinline__ int64_t range_begin(int64_t c, int64_t work, int64_t ctas) { return c * work / ctas; }
 
+// Position t of query block qb sweeps key tile (t + key_rotation(qb)) mod
+// n_tiles.  The rotation puts the block's first tile at the time its owner
+// CTA (the one whose run holds position 0) reaches it, modulo n_tiles, so at
+// any moment the CTAs read the same key tile and each tile comes from DRAM
+// about once per sweep (only a run's first, split segment is out of step).
+__device__ __forceinline__ int key_rotation(int64_t qb, int n_tiles, int64_t work, int64_t ctas) {
+  const int64_t x0 = qb * n_tiles;
+  const int64_t c0 = ((x0 + 1) * ctas + work - 1) / work - 1;
+  const int64_t lag = x0 - range_begin(c0, work, ctas);  // owner's time at position 0
+  return (int)(lag % n_tiles);
+}
+
 // kCollect: collect mode (keys above a per-row threshold) instead of list
 // mode (two 16-entry lists per row); kE4M3: FP8 operands.  out_scale (list
 // mode, may be null) multiplies the scores written out.
@@ -245,6 +257,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         const int64_t qb = w / n_tiles;
         const int t0 = (int)(w - qb * n_tiles);
         const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
+        const int rot = key_rotation(qb, n_tiles, work, gridDim.x);
         w += t1 - t0;
         // the previous block of A stays in use until its last MMA completes
         if (seg > 0 && !mbar_wait(&bars->a_empty, (uint32_t)((seg - 1) & 1), abort, err, 6)) {
@@ -262,7 +275,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             }
             pending[stage] = false;
             mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
-            tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, t * kTN, &bars->full[stage]);
+            const int kt = t + rot < n_tiles ? t + rot : t + rot - n_tiles;
+            tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, kt * kTN, &bars->full[stage]);
             pending[stage] = true;
             pend_par[stage] = phase;
             if (++stage == nstages) {
@@ -351,6 +365,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       const int64_t qb = w / n_tiles;
       const int t0 = (int)(w - qb * n_tiles);
       const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
+      const int rot = key_rotation(qb, n_tiles, work, gridDim.x);
       w += t1 - t0;
       // A row ra is query row ra, or compact row ra -> global row a_rows[ra]
       const int64_t ra = qb * kTM + r;
@@ -373,7 +388,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           break;
         }
         tc_fence_after();
-        const int64_t jb = (int64_t)t * kTN + h * kSliceN;
+        const int kt = t + rot < n_tiles ? t + rot : t + rot - n_tiles;
+        const int64_t jb = (int64_t)kt * kTN + h * kSliceN;
         const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * kSliceN);
 #pragma unroll 1
         for (int c = 0; c < kSliceN / 32; ++c) {
