@@ -91,6 +91,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
+// (hi, lo) += (bh, bl): float-float addition (TwoSum, then renormalise)
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
 // Dot2 accumulation step: (s, c) += x * y
 __device__ __forceinline__ void dot2_step(float& s, float& c, float x, float y) {
   float p = __fmul_rn(x, y);

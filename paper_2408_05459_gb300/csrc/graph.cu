@@ -20,7 +20,9 @@ namespace ancka {
 
 namespace {
 
-constexpr uint64_t kLowMask = 0xffffffffull;
+// Sort keys pack (row, col) as row << cb | col with cb = bits of the column
+// range, so a sort covers only the bits in use (8 bits per radix pass).
+__host__ __device__ __forceinline__ uint64_t col_mask(int cb) { return (uint64_t(1) << cb) - 1; }
 
 int bits_for(int64_t n) {
   int b = 1;
@@ -89,7 +91,7 @@ __global__ void k_check_ptr(const int64_t* __restrict__ ptr, int64_t rows, int64
 }
 
 __global__ void k_csr_to_keys(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                              int64_t n, int directed, uint64_t* __restrict__ keys,
+                              int64_t n, int directed, int cb, uint64_t* __restrict__ keys,
                               int32_t* __restrict__ bad) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -101,13 +103,13 @@ __global__ void k_csr_to_keys(const int64_t* __restrict__ ptr, const int32_t* __
       j = 0;
     }
     int64_t q = p - base;
-    keys[directed ? 2 * q : q] = ((uint64_t)i << 32) | (uint32_t)j;
-    if (directed) keys[2 * q + 1] = ((uint64_t)j << 32) | (uint32_t)i;
+    keys[directed ? 2 * q : q] = ((uint64_t)i << cb) | (uint32_t)j;
+    if (directed) keys[2 * q + 1] = ((uint64_t)j << cb) | (uint32_t)i;
   }
 }
 
 __global__ void k_hyper_to_keys(const int64_t* __restrict__ he_ptr, const int32_t* __restrict__ nodes,
-                                int64_t m, int64_t n, uint64_t* __restrict__ keys,
+                                int64_t m, int64_t n, int cb, uint64_t* __restrict__ keys,
                                 int32_t* __restrict__ bad) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
@@ -117,26 +119,27 @@ __global__ void k_hyper_to_keys(const int64_t* __restrict__ he_ptr, const int32_
       atomicExch(bad, 1);
       v = 0;
     }
-    keys[p - he_ptr[0]] = ((uint64_t)e << 32) | (uint32_t)v;
+    keys[p - he_ptr[0]] = ((uint64_t)e << cb) | (uint32_t)v;
   }
 }
 
-// counts per high half of the keys; col = low half
-__global__ void k_keys_to_rows(const uint64_t* __restrict__ keys, const int64_t* __restrict__ cnt_dev,
+// counts per row (key >> cb); col = low cb bits
+__global__ void k_keys_to_rows(const uint64_t* __restrict__ keys, const int64_t* __restrict__ cnt_dev, int cb,
                                int32_t* __restrict__ rowcnt, int32_t* __restrict__ col) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= *cnt_dev) return;
   uint64_t k = keys[q];
-  atomicAdd(&rowcnt[k >> 32], 1);
-  if (col) col[q] = (int32_t)(k & kLowMask);
+  atomicAdd(&rowcnt[k >> cb], 1);
+  if (col) col[q] = (int32_t)(k & col_mask(cb));
 }
 
-__global__ void k_swap_halves(const uint64_t* __restrict__ in, const int64_t* __restrict__ cnt_dev,
-                              uint64_t* __restrict__ out) {
+// (row << cb_in | col) -> (col << cb_out | row); cb_out covers the old rows
+__global__ void k_swap_halves(const uint64_t* __restrict__ in, const int64_t* __restrict__ cnt_dev, int cb_in,
+                              int cb_out, uint64_t* __restrict__ out) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= *cnt_dev) return;
   uint64_t k = in[q];
-  out[q] = (k << 32) | (k >> 32);
+  out[q] = ((k & col_mask(cb_in)) << cb_out) | (k >> cb_in);
 }
 
 __global__ void k_int_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
@@ -182,7 +185,7 @@ __global__ void k_sum_deg(int L, int64_t n, const int32_t* const* __restrict__ l
 }
 
 // --- KNN augmentation -------------------------------------------------------
-__global__ void k_knn_mutual(const int32_t* __restrict__ idx, int64_t n, int K,
+__global__ void k_knn_mutual(const int32_t* __restrict__ idx, int64_t n, int K, int cb,
                              uint8_t* __restrict__ mutual, uint64_t* __restrict__ keys,
                              int32_t* __restrict__ in_cnt) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,9 +196,9 @@ __global__ void k_knn_mutual(const int32_t* __restrict__ idx, int64_t n, int K,
   for (int p = 0; p < K; ++p) mu |= (idx[(int64_t)j * K + p] == (int32_t)i);
   mutual[q] = mu ? 1 : 0;
   if (mu) {
-    keys[q] = ~0ull;  // sorts after every real key
+    keys[q] = uint64_t(1) << (2 * cb);  // sorts after every real key
   } else {
-    keys[q] = ((uint64_t)j << 32) | (uint32_t)i;
+    keys[q] = ((uint64_t)j << cb) | (uint32_t)i;
     atomicAdd(&in_cnt[j], 1);
   }
 }
@@ -217,37 +220,46 @@ __global__ void k_knn_fill(const int32_t* __restrict__ idx, const float* __restr
                            int64_t n, int K, const int64_t* __restrict__ ptr,
                            int32_t* __restrict__ col, float* __restrict__ val,
                            const int32_t* __restrict__ zero_row, const int32_t* __restrict__ degree,
-                           float beta, float* __restrict__ beta_out) {
+                           float beta, int cb, float* __restrict__ beta_out) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= n) return;  // uniform over the warp
   const int64_t o = ptr[i];
-  double D = 0.0;
+  // D_K[i] as a float-float pair (compensated FP32; GB300's FP64 pipe is narrow)
+  float Dh = 0.f, Dl = 0.f;
   for (int p = lane; p < K; p += 32) {
     const int64_t q = i * K + p;
     const float a = mutual[q] ? 2.f * sim[q] : sim[q];
     col[o + p] = idx[q];
     val[o + p] = a;
-    D += a;
+    ff_add(Dh, Dl, a, 0.f);
   }
   const int64_t b = in_start[i];
   const int32_t c = in_cnt[i];
   for (int32_t t = lane; t < c; t += 32) {
-    const int32_t src = (int32_t)(skeys[b + t] & kLowMask);
+    const int32_t src = (int32_t)(skeys[b + t] & col_mask(cb));
     float f = 0.f;
     for (int p = 0; p < K; ++p)
       if (idx[(int64_t)src * K + p] == (int32_t)i) f = sim[(int64_t)src * K + p];
     col[o + K + t] = src;
     val[o + K + t] = f;
-    D += f;
+    ff_add(Dh, Dl, f, 0.f);
   }
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) D += __shfl_xor_sync(0xffffffffu, D, off);
+  for (int off = 16; off >= 1; off >>= 1) {  // ff_add is symmetric: every lane ends equal
+    const float oh = __shfl_xor_sync(0xffffffffu, Dh, off), ol = __shfl_xor_sync(0xffffffffu, Dl, off);
+    ff_add(Dh, Dl, oh, ol);
+  }
   // Eq. beta_i, then reading R3 (a non-positive KNN degree disables the KNN walk)
   float bi = zero_row[i] ? 0.f : (degree[i] == 0 ? 1.f : beta);
-  if (!(D > 0.0)) bi = 0.f;
+  if (!(Dh > 0.f)) bi = 0.f;
   if (lane == 0) beta_out[i] = bi;
-  const float scale = D > 0.0 ? (float)((double)bi / D) : 0.f;
+  // bi / (Dh + Dl) with one correction step: q = bi / Dh, then q -= q * Dl / Dh
+  float scale = 0.f;
+  if (Dh > 0.f) {
+    const float q0 = __fdiv_rn(bi, Dh);
+    scale = fmaf(-q0, __fdiv_rn(Dl, Dh), q0);
+  }
   for (int p = lane; p < K; p += 32) val[o + p] *= scale;
   for (int32_t t = lane; t < c; t += 32) val[o + K + t] *= scale;
 }
@@ -263,11 +275,11 @@ inline unsigned grid_for(int64_t n, int b) { return (unsigned)ceil_div(n > 0 ? n
 
 // sorted unique keys -> CSR over the high halves (rows 0..nrows-1)
 ancka_status keys_to_csr(Workspace& ws, const uint64_t* ukeys, const int64_t* ucnt_dev, int64_t ucnt,
-                         int64_t nrows, Csr* out, int32_t** rowcnt_out, cudaStream_t s) {
+                         int64_t nrows, int cb, Csr* out, int32_t** rowcnt_out, cudaStream_t s) {
   int32_t* rowcnt;
   ANCKA_TRY(ws.zeros(&rowcnt, (size_t)nrows + 1));
   ANCKA_TRY(ws.alloc(&out->col, (size_t)ucnt));
-  k_keys_to_rows<<<grid_for(ucnt, 256), 256, 0, s>>>(ukeys, ucnt_dev, rowcnt, out->col);
+  k_keys_to_rows<<<grid_for(ucnt, 256), 256, 0, s>>>(ukeys, ucnt_dev, cb, rowcnt, out->col);
   ANCKA_LAUNCHED();
   int64_t* len;
   ANCKA_TRY(ws.alloc(&len, (size_t)nrows + 1));
@@ -306,24 +318,24 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     ANCKA_TRY(ws.alloc(&k0, (size_t)nnz));
     ANCKA_TRY(ws.alloc(&k1, (size_t)nnz));
     ANCKA_TRY(ws.alloc(&k2, (size_t)nnz));
-    k_hyper_to_keys<<<grid_for(m, 256), 256, 0, s>>>(t.he_ptr, t.he_nodes, m, n, k0, bad);
+    k_hyper_to_keys<<<grid_for(m, 256), 256, 0, s>>>(t.he_ptr, t.he_nodes, m, n, nb, k0, bad);
     ANCKA_LAUNCHED();
     ANCKA_TRY(check_bad(bad, s, "topology: node id out of range [0, n)"));
     const int mb = bits_for(m);
-    ANCKA_TRY(sort_keys(ws, k0, k1, nnz, 32 + mb, s));
+    ANCKA_TRY(sort_keys(ws, k0, k1, nnz, mb + nb, s));
     int64_t* ucnt_dev;
     ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
     if (nnz > 0) ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, nnz, s));
     int64_t ucnt = 0;
     ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
     int32_t* esize;
-    ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, m, &w->edges, &esize, s));
+    ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, m, nb, &w->edges, &esize, s));
     // node -> hyperedge incidence
-    k_swap_halves<<<grid_for(ucnt, 256), 256, 0, s>>>(k2, ucnt_dev, k0);
+    k_swap_halves<<<grid_for(ucnt, 256), 256, 0, s>>>(k2, ucnt_dev, nb, mb, k0);
     ANCKA_LAUNCHED();
-    ANCKA_TRY(sort_keys(ws, k0, k1, ucnt, 32 + nb, s));
+    ANCKA_TRY(sort_keys(ws, k0, k1, ucnt, nb + mb, s));
     int32_t* vdeg;
-    ANCKA_TRY(keys_to_csr(ws, k1, ucnt_dev, ucnt, n, &w->topo, &vdeg, s));
+    ANCKA_TRY(keys_to_csr(ws, k1, ucnt_dev, ucnt, n, mb, &w->topo, &vdeg, s));
     w->degree = vdeg;
     ANCKA_TRY(ws.alloc(&w->inv_size, (size_t)m));
     ANCKA_TRY(ws.alloc(&w->inv_deg, (size_t)n));
@@ -350,10 +362,10 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
       ANCKA_TRY(ws.alloc(&k0, (size_t)cnt));
       ANCKA_TRY(ws.alloc(&k1, (size_t)cnt));
       ANCKA_TRY(ws.alloc(&k2, (size_t)cnt));
-      k_csr_to_keys<<<grid_for(n, 256), 256, 0, s>>>(rp, t.col_idx, n, t.directed, k0, bad);
+      k_csr_to_keys<<<grid_for(n, 256), 256, 0, s>>>(rp, t.col_idx, n, t.directed, nb, k0, bad);
       ANCKA_LAUNCHED();
       ANCKA_TRY(check_bad(bad, s, "topology: node id out of range [0, n)"));
-      ANCKA_TRY(sort_keys(ws, k0, k1, cnt, 32 + nb, s));
+      ANCKA_TRY(sort_keys(ws, k0, k1, cnt, 2 * nb, s));
       int64_t* ucnt_dev;
       ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
       if (cnt > 0) ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, cnt, s));
@@ -361,7 +373,7 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
       ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
       Csr lay;
       int32_t* deg;
-      ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, n, &lay, &deg, s));
+      ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, n, nb, &lay, &deg, s));
       lptr[l] = lay.ptr;
       lcol[l] = lay.col;
       ldeg[l] = deg;
@@ -409,9 +421,10 @@ ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* 
   ANCKA_TRY(ws.alloc(&keys, (size_t)nk));
   ANCKA_TRY(ws.alloc(&skeys, (size_t)nk));
   ANCKA_TRY(ws.zeros(&in_cnt, (size_t)n));
-  k_knn_mutual<<<grid_for(nk, 256), 256, 0, s>>>(idx, n, K, mutual, keys, in_cnt);
+  const int nb = bits_for(n);
+  k_knn_mutual<<<grid_for(nk, 256), 256, 0, s>>>(idx, n, K, nb, mutual, keys, in_cnt);
   ANCKA_LAUNCHED();
-  ANCKA_TRY(sort_keys(ws, keys, skeys, nk, 64, s));
+  ANCKA_TRY(sort_keys(ws, keys, skeys, nk, 2 * nb + 1, s));
   int64_t *len, *in_len, *in_start;
   ANCKA_TRY(ws.alloc(&len, (size_t)n + 1));
   ANCKA_TRY(ws.alloc(&in_len, (size_t)n + 1));
@@ -433,7 +446,7 @@ ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* 
   ANCKA_TRY(ws.alloc(&c.val, (size_t)tot));
   ANCKA_TRY(ws.alloc(&w->beta, (size_t)n));
   k_knn_fill<<<grid_for(n * 32, 256), 256, 0, s>>>(idx, sim, mutual, skeys, in_start, in_cnt, n, K, c.ptr,
-                                              c.col, c.val, zero_row, w->degree, beta, w->beta);
+                                              c.col, c.val, zero_row, w->degree, beta, nb, w->beta);
   ANCKA_LAUNCHED();
   ANCKA_TRY(ws.alloc(&w->rs_topo, (size_t)n));
   k_topo_rowscale<<<grid_for(n, 256), 256, 0, s>>>(w->beta, w->kind == ANCKA_HYPERGRAPH ? w->inv_deg : nullptr,

@@ -506,15 +506,6 @@ constexpr int kGramThreads = 256, kGramRows = 128, kGramLd = kMaxW;
 
 __device__ __forceinline__ int tri_index(int a, int b, int w) { return a * w - a * (a - 1) / 2 + (b - a); }
 
-// (hi, lo) += (bh, bl): float-float addition (TwoSum, then renormalise)
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
-  float s, e;
-  two_sum(hi, bh, s, e);
-  e = __fadd_rn(e, __fadd_rn(lo, bl));
-  hi = __fadd_rn(s, e);
-  lo = __fsub_rn(e, __fsub_rn(hi, s));
-}
-
 // block pair index q -> (A, B), A <= B < nb
 __device__ __forceinline__ void block_pair(int q, int nb, int& A, int& B) {
   A = 0;
