@@ -20,6 +20,31 @@ std::atomic<int64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+struct EventPool {
+  std::vector<cudaEvent_t> free;
+  ~EventPool() {
+    for (cudaEvent_t e : free) cudaEventDestroy(e);
+  }
+};
+thread_local EventPool g_event_pool;
+}  // namespace
+
+cudaEvent_t pooled_event() {
+  if (!g_event_pool.free.empty()) {
+    cudaEvent_t e = g_event_pool.free.back();
+    g_event_pool.free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void release_event(cudaEvent_t e) {
+  if (e) g_event_pool.free.push_back(e);
+}
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -84,14 +109,13 @@ struct Phase {
   int phase;
   Phase(Timer* tt, cudaStream_t st, int p) : t(tt), s(st), phase(p) {
     if (t) {
-      cudaEventCreate(&a);
+      a = pooled_event();
       cudaEventRecord(a, s);
     }
   }
   ~Phase() {
     if (t) {
-      cudaEvent_t b;
-      cudaEventCreate(&b);
+      cudaEvent_t b = pooled_event();
       cudaEventRecord(b, s);
       t->ev.push_back(a);
       t->ev.push_back(b);
@@ -106,7 +130,7 @@ void fill_times(Timer& t, ancka_info* info) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, t.ev[2 * q], t.ev[2 * q + 1]) == cudaSuccess && t.ph[q] < 8) acc[t.ph[q]] += ms;
   }
-  for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : t.ev) release_event(e);
   t.ev.clear();
   cudaGetLastError();
   if (info) {
@@ -192,32 +216,17 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
     ANCKA_TRY(ws.alloc(&cv, (size_t)n * kCandC));
     ANCKA_TRY(ws.alloc(&ci, (size_t)n * kCandC));
     float acc;
+    int32_t* terr = nullptr;  // contraction error flag, read back by the re-rank's first host read
     if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[0], s));
     if (prec == ANCKA_PREC_BF16) {
-      int32_t* terr;
       ANCKA_TRY(ws.zeros(&terr, 1));
       ANCKA_TRY(knn_candidates_bf16(ws, pr, n, cv, ci, terr, s));
       if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
-      int32_t hterr = 0;
-      ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      ANCKA_CUDA(cudaStreamSynchronize(s));
-      if (hterr) {
-        set_error("tensor-core contraction: a pipeline wait expired (role %d)", hterr);
-        return ANCKA_ERR_TIMEOUT;
-      }
       acc = tc_acc_bound(pr.dp, 16, -22);
     } else if (prec == ANCKA_PREC_FP8) {
-      int32_t* terr;
       ANCKA_TRY(ws.zeros(&terr, 1));
       ANCKA_TRY(knn_candidates_fp8(ws, pr, n, cv, ci, terr, s));
       if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[1], s));
-      int32_t hterr = 0;
-      ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      ANCKA_CUDA(cudaStreamSynchronize(s));
-      if (hterr) {
-        set_error("tensor-core FP8 contraction: a pipeline wait expired (role %d)", hterr);
-        return ANCKA_ERR_TIMEOUT;
-      }
       acc = tc_acc_bound(pr.dp8, 32, -18);
     } else {
       ANCKA_TRY(knn_candidates_fp32(pr, n, cv, ci, s));
@@ -229,12 +238,12 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
     // the tensor-core kernel leaves two 16-entry lists per row (one per half
     // of the key columns), the CUDA-core kernel one 32-entry list
     ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, prec, acc, tc_acc_bound(pr.dp, 16, -22), cv, ci,
-                         prec == ANCKA_PREC_FP32 ? 1 : 2, prec == ANCKA_PREC_FP32 ? prec : ANCKA_PREC_BF16, idx, sim,
-                         ncand, nfb, nex, counts, s));
+                         prec == ANCKA_PREC_FP32 ? 1 : 2, prec == ANCKA_PREC_FP32 ? prec : ANCKA_PREC_BF16, terr, idx,
+                         sim, ncand, nfb, nex, counts, s));
     if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[2], s));
   } else {
-    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, ANCKA_PREC_FP32, 0.f, 0.f, nullptr, nullptr, 1, ANCKA_PREC_FP32, idx,
-                         sim, ncand, nfb, nex, counts, s));
+    ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, ANCKA_PREC_FP32, 0.f, 0.f, nullptr, nullptr, 1, ANCKA_PREC_FP32,
+                         nullptr, idx, sim, ncand, nfb, nex, counts, s));
   }
   return ANCKA_OK;
 }
@@ -322,11 +331,11 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
   cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
   bool contract_timed = false;
   if (info) {
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
-    cudaEventCreate(&cev[0]);
-    cudaEventCreate(&cev[1]);
-    cudaEventCreate(&cev[2]);
+    t0 = pooled_event();
+    t1 = pooled_event();
+    cev[0] = pooled_event();
+    cev[1] = pooled_event();
+    cev[2] = pooled_event();
     cudaEventRecord(t0, s);
   }
   ancka_status st = ANCKA_OK;
@@ -435,11 +444,11 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     if (contract_timed && st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[1], cev[2]) == cudaSuccess)
       info->ms_rerank = mc;
     cudaGetLastError();  // an event of a failed call may never have been recorded
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
-    cudaEventDestroy(cev[0]);
-    cudaEventDestroy(cev[1]);
-    cudaEventDestroy(cev[2]);
+    release_event(t0);
+    release_event(t1);
+    release_event(cev[0]);
+    release_event(cev[1]);
+    release_event(cev[2]);
   }
   if (st == ANCKA_OK) {
     cudaError_t e = cudaGetLastError();
@@ -520,8 +529,8 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
   if (info) memset(info, 0, sizeof(*info));
   cudaEvent_t a = nullptr, b = nullptr;
   if (info) {
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
+    a = pooled_event();
+    b = pooled_event();
     cudaEventRecord(a, s);
   }
   ancka_status st;
@@ -529,9 +538,9 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
   cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
   const bool timed = info && K <= max_candidate_K(prec);
   if (timed) {
-    cudaEventCreate(&cev[0]);
-    cudaEventCreate(&cev[1]);
-    cudaEventCreate(&cev[2]);
+    cev[0] = pooled_event();
+    cev[1] = pooled_event();
+    cev[2] = pooled_event();
   }
   {
     Workspace ws(s);
@@ -554,12 +563,12 @@ ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t 
       if (st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[0], cev[1]) == cudaSuccess) info->ms_contract = mc;
       if (st == ANCKA_OK && cudaEventElapsedTime(&mc, cev[1], cev[2]) == cudaSuccess) info->ms_rerank = mc;
       cudaGetLastError();
-      cudaEventDestroy(cev[0]);
-      cudaEventDestroy(cev[1]);
-      cudaEventDestroy(cev[2]);
+      release_event(cev[0]);
+      release_event(cev[1]);
+      release_event(cev[2]);
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    release_event(a);
+    release_event(b);
   }
   return st;
 }

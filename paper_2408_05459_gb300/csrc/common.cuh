@@ -23,6 +23,10 @@ ancka_status cuda_fail(cudaError_t e, const char* what, const char* file, int li
   } while (0)
 
 void count_launch();
+// timing events for the diagnostics (ancka_info): a per-thread pool, so an
+// instrumented call creates no events once the pool is warm
+cudaEvent_t pooled_event();
+void release_event(cudaEvent_t e);
 #define ANCKA_LAUNCHED()            \
   do {                              \
     ::ancka::count_launch();        \
@@ -220,12 +224,15 @@ ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const
 // is its accumulation bound); lists: 1 (one 32-list per row) or 2 (two
 // 16-lists).  FP8: rows the FP8 lists cannot certify get BF16 lists
 // (acc_bf16) and a second certificate.  collect_prec == ANCKA_PREC_BF16 sends
-// rows still uncertified through the tensor-core collect pass.
+// rows still uncertified through the tensor-core collect pass.  list_err
+// (device, may be null): the error flag of the pass that wrote the lists; the
+// re-rank skips its work when it is set, and the call reports it with its
+// first host read (ANCKA_ERR_TIMEOUT), so the list pass needs no sync of its own.
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
                         const PrepOut& pr, int list_prec, float acc_coef, float acc_bf16, float* cand_val,
-                        int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx, float* out_sim,
-                        int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive, bool want_counts,
-                        cudaStream_t s);
+                        int32_t* cand_idx, int lists, int collect_prec, const int32_t* list_err, int32_t* out_idx,
+                        float* out_sim, int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive,
+                        bool want_counts, cudaStream_t s);
 
 // graph.cu: walk structures
 struct Csr {

@@ -307,27 +307,39 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     w->m = m;
     k_check_ptr<<<grid_for(m + 1, 256), 256, 0, s>>>(t.he_ptr, m, -1, bad);
     ANCKA_LAUNCHED();
-    ANCKA_TRY(check_bad(bad, s, "hyperedge pointer must be non-negative and non-decreasing"));
-    int64_t nnz = 0;
+    // the pointer check and the entry count in one host read
+    int64_t nnz = 0, base = 0;
+    int32_t hbad = 0;
     ANCKA_CUDA(cudaMemcpyAsync(&nnz, t.he_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    int64_t base = 0;
     ANCKA_CUDA(cudaMemcpyAsync(&base, t.he_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     ANCKA_CUDA(cudaStreamSynchronize(s));
+    if (hbad) {
+      set_error("hyperedge pointer must be non-negative and non-decreasing");
+      return ANCKA_ERR_INVALID_ARG;
+    }
     nnz -= base;
     uint64_t *k0, *k1, *k2;
     ANCKA_TRY(ws.alloc(&k0, (size_t)nnz));
     ANCKA_TRY(ws.alloc(&k1, (size_t)nnz));
     ANCKA_TRY(ws.alloc(&k2, (size_t)nnz));
+    // out-of-range node ids are replaced by 0 in the keys and reported with
+    // the unique count below (one host read)
     k_hyper_to_keys<<<grid_for(m, 256), 256, 0, s>>>(t.he_ptr, t.he_nodes, m, n, nb, k0, bad);
     ANCKA_LAUNCHED();
-    ANCKA_TRY(check_bad(bad, s, "topology: node id out of range [0, n)"));
     const int mb = bits_for(m);
     ANCKA_TRY(sort_keys(ws, k0, k1, nnz, mb + nb, s));
     int64_t* ucnt_dev;
     ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
     if (nnz > 0) ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, nnz, s));
     int64_t ucnt = 0;
-    ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&ucnt, ucnt_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+    if (hbad) {
+      set_error("topology: node id out of range [0, n)");
+      return ANCKA_ERR_INVALID_ARG;
+    }
     int32_t* esize;
     ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, m, nb, &w->edges, &esize, s));
     // node -> hyperedge incidence
@@ -437,13 +449,14 @@ ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* 
   ANCKA_TRY(ws.alloc(&c.ptr, (size_t)n + 1));
   ANCKA_TRY(exclusive_scan(ws, len, c.ptr, n + 1, s));
   ANCKA_TRY(exclusive_scan(ws, in_len, in_start, n + 1, s));
-  int64_t tot = 0;
-  ANCKA_CUDA(cudaMemcpyAsync(&tot, c.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  ANCKA_CUDA(cudaStreamSynchronize(s));
+  // a row holds its K out-neighbours and at most K in-neighbours per entry of
+  // other lists, so n K + n K bounds the entries; the exact count (c.ptr[n])
+  // stays on the device and nnz holds the bound
+  const int64_t bound = 2 * nk;
   c.nrows = n;
-  c.nnz = tot;
-  ANCKA_TRY(ws.alloc(&c.col, (size_t)tot));
-  ANCKA_TRY(ws.alloc(&c.val, (size_t)tot));
+  c.nnz = bound;
+  ANCKA_TRY(ws.alloc(&c.col, (size_t)(bound > 0 ? bound : 1)));
+  ANCKA_TRY(ws.alloc(&c.val, (size_t)(bound > 0 ? bound : 1)));
   ANCKA_TRY(ws.alloc(&w->beta, (size_t)n));
   k_knn_fill<<<grid_for(n * 32, 256), 256, 0, s>>>(idx, sim, mutual, skeys, in_start, in_cnt, n, K, c.ptr,
                                               c.col, c.val, zero_row, w->degree, beta, nb, w->beta);

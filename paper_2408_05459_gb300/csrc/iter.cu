@@ -327,9 +327,21 @@ __global__ void k_spmm_long_finish(SpmmArgs a, const float4* __restrict__ part) 
   *reinterpret_cast<float4*>(a.out + i * a.ldo + 4 * g) = acc;
 }
 
+// The long-row threshold comes from the mean row length, taken here from the
+// row pointers (meta[1] = mean, meta[2] = threshold) so that the host needs
+// no count before the launch.
 __global__ void k_find_long(const int64_t* __restrict__ ptrA, const int64_t* __restrict__ ptrB, int64_t nrows,
-                            int64_t long_min, int32_t* __restrict__ rows, int32_t* __restrict__ count) {
+                            int big, int32_t* __restrict__ rows, int32_t* __restrict__ count,
+                            int64_t* __restrict__ meta) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nnz = (ptrA[nrows] - ptrA[0]) + (ptrB ? ptrB[nrows] - ptrB[0] : 0);
+  const int64_t mean = nrows > 0 ? (nnz + nrows - 1) / nrows : 0;
+  const int64_t lo = big ? 128 : 256, f = big ? 2 : 4;
+  const int64_t long_min = f * mean > lo ? f * mean : lo;
+  if (i == 0) {
+    meta[1] = mean;
+    meta[2] = long_min;
+  }
   if (i >= nrows) return;
   const int64_t e = (ptrA[i + 1] - ptrA[i]) + (ptrB ? ptrB[i + 1] - ptrB[i] : 0);
   if (e > long_min) rows[atomicAdd(count, 1)] = (int32_t)i;
@@ -337,74 +349,119 @@ __global__ void k_find_long(const int64_t* __restrict__ ptrA, const int64_t* __r
 
 struct LongRows {
   int32_t* rows = nullptr;
-  int32_t* count = nullptr;
-  int64_t count_host = -1;
+  int32_t* count = nullptr;   // device: long rows found
+  int64_t* meta = nullptr;    // device: work items, mean row length, long-row threshold
+  int64_t nrows = 0;
+  int64_t nnz_bound = 0;      // upper bound of the entries (sizes the work-item array)
+  int64_t count_host = -1;    // host copies, valid after read_long_rows
   int64_t min_entries = 0;
   int64_t mean = 0;
   int2* items = nullptr;      // (q, part) work items
-  int32_t* off = nullptr;     // count_host + 1 item offsets
+  int32_t* off = nullptr;     // count + 1 item offsets
   int64_t items_host = 0;
 };
 
-__global__ void k_long_item_counts(const int64_t* __restrict__ ptrA, const int64_t* __restrict__ ptrB,
-                                   const int32_t* __restrict__ rows, int64_t n_long, int32_t* __restrict__ cnt) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q > n_long) return;
-  if (q == n_long) {
-    cnt[q] = 0;
-    return;
+// Work-item offsets of the long rows (count read on the device): one CTA,
+// 1024 rows per round, block-wide exclusive scan; meta[0] = total items.
+__global__ void __launch_bounds__(1024) k_long_item_offsets(const int64_t* __restrict__ ptrA,
+                                                            const int64_t* __restrict__ ptrB,
+                                                            const int32_t* __restrict__ rows,
+                                                            const int32_t* __restrict__ count,
+                                                            int32_t* __restrict__ off, int64_t* __restrict__ meta) {
+  __shared__ int32_t wsum[32];
+  __shared__ int32_t carry_s;
+  const int nl = *count;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < nl; base += blockDim.x) {
+    const int q = base + (int)threadIdx.x;
+    int32_t c = 0;
+    if (q < nl) {
+      const int64_t i = rows[q];
+      const int64_t len = (ptrA[i + 1] - ptrA[i]) + (ptrB ? ptrB[i + 1] - ptrB[i] : 0);
+      c = (int32_t)((len + kLongChunk - 1) / kLongChunk);
+    }
+    int32_t x = c;  // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      wsum[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    const int32_t carry = carry_s;
+    const int32_t before = (wid > 0 ? wsum[wid - 1] : 0) + x - c;
+    if (q < nl) off[q] = carry + before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + wsum[(blockDim.x >> 5) - 1];
+    __syncthreads();
   }
-  const int64_t i = rows[q];
-  const int64_t len = (ptrA[i + 1] - ptrA[i]) + (ptrB ? ptrB[i + 1] - ptrB[i] : 0);
-  cnt[q] = (int32_t)((len + kLongChunk - 1) / kLongChunk);
+  if (threadIdx.x == 0) {
+    off[nl] = carry_s;
+    meta[0] = carry_s;
+  }
 }
 
-__global__ void k_long_item_fill(const int32_t* __restrict__ off, int64_t n_long, int2* __restrict__ items) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n_long) return;
-  for (int32_t it = off[q]; it < off[q + 1]; ++it) items[it] = make_int2((int)q, it - off[q]);
+__global__ void k_long_item_fill(const int32_t* __restrict__ off, const int32_t* __restrict__ count,
+                                 int2* __restrict__ items) {
+  const int64_t nl = *count;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nl; q += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t it = off[q]; it < off[q + 1]; ++it) items[it] = make_int2((int)q, it - off[q]);
 }
 
-// work items of the long rows (after count_host is known): one sync
+// work items of the long rows, on the device (arrays sized by upper bounds)
 ancka_status build_long_items(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, LongRows* lr, cudaStream_t s) {
-  const int64_t nl = lr->count_host;
-  int32_t* cnt;
-  ANCKA_TRY(ws.alloc(&cnt, (size_t)nl + 1));
-  ANCKA_TRY(ws.alloc(&lr->off, (size_t)nl + 1));
-  k_long_item_counts<<<grid_for(nl + 1, 256), 256, 0, s>>>(ptrA, ptrB, lr->rows, nl, cnt);
+  const int64_t nr = lr->nrows > 0 ? lr->nrows : 1;
+  ANCKA_TRY(ws.alloc(&lr->off, (size_t)nr + 1));
+  ANCKA_TRY(ws.alloc(&lr->items, (size_t)(nr + lr->nnz_bound / kLongChunk + 1)));
+  k_long_item_offsets<<<1, 1024, 0, s>>>(ptrA, ptrB, lr->rows, lr->count, lr->off, lr->meta);
   ANCKA_LAUNCHED();
-  size_t tmp = 0;
-  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, cnt, lr->off, (int)(nl + 1), s));
-  void* t;
-  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp > 0 ? tmp : 1));
-  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, cnt, lr->off, (int)(nl + 1), s));
-  int32_t total = 0;
-  ANCKA_CUDA(cudaMemcpyAsync(&total, lr->off + nl, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ANCKA_CUDA(cudaStreamSynchronize(s));
-  lr->items_host = total;
-  ANCKA_TRY(ws.alloc(&lr->items, (size_t)(total > 0 ? total : 1)));
-  if (nl > 0) {
-    k_long_item_fill<<<grid_for(nl, 256), 256, 0, s>>>(lr->off, nl, lr->items);
-    ANCKA_LAUNCHED();
-  }
+  const unsigned g = (unsigned)(ceil_div(nr, 256) < 1216 ? ceil_div(nr, 256) : 1216);
+  k_long_item_fill<<<g, 256, 0, s>>>(lr->off, lr->count, lr->items);
+  ANCKA_LAUNCHED();
   return ANCKA_OK;
 }
 
-// long rows of (ptrA [, ptrB]) (nnz entries in all), listed once per call
-// (list order does not affect the result); block_bytes: size of the block
-// the SpMM gathers from
-ancka_status find_long_rows(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, int64_t nrows, int64_t nnz,
-                            double block_bytes, LongRows* out, cudaStream_t s) {
-  const int64_t mean = nrows > 0 ? ceil_div(nnz, nrows) : 0;
-  out->mean = mean;
+// long rows with a fixed threshold: max(256, 4 x mean), or max(128, 2 x
+// mean) when the gathered block exceeds 64 MB; nnz_bound >= the entries
+ancka_status find_long_rows(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, int64_t nrows,
+                            int64_t nnz_bound, double block_bytes, LongRows* out, cudaStream_t s) {
+  out->nrows = nrows;
+  out->nnz_bound = nnz_bound;
   const bool big = block_bytes > 64.0 * (1 << 20);
-  const int64_t lo = big ? 128 : 256, f = big ? 2 : 4;
-  out->min_entries = f * mean > lo ? f * mean : lo;
   ANCKA_TRY(ws.alloc(&out->rows, (size_t)(nrows > 0 ? nrows : 1)));
   ANCKA_TRY(ws.zeros(&out->count, 1));
-  k_find_long<<<(unsigned)ceil_div(nrows > 0 ? nrows : 1, 256), 256, 0, s>>>(ptrA, ptrB, nrows, out->min_entries,
-                                                                              out->rows, out->count);
+  ANCKA_TRY(ws.zeros(&out->meta, 3));
+  k_find_long<<<(unsigned)ceil_div(nrows > 0 ? nrows : 1, 256), 256, 0, s>>>(ptrA, ptrB, nrows, big ? 1 : 0,
+                                                                              out->rows, out->count, out->meta);
   ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+// the host copies of every LongRows' counts with one stream sync
+ancka_status read_long_rows(LongRows* const* lrs, int nlr, cudaStream_t s) {
+  int32_t cnt[4] = {0, 0, 0, 0};
+  int64_t meta[4][3] = {};
+  for (int q = 0; q < nlr; ++q) {
+    ANCKA_CUDA(cudaMemcpyAsync(&cnt[q], lrs[q]->count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaMemcpyAsync(meta[q], lrs[q]->meta, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost, s));
+  }
+  ANCKA_CUDA(cudaStreamSynchronize(s));
+  for (int q = 0; q < nlr; ++q) {
+    lrs[q]->count_host = cnt[q];
+    lrs[q]->items_host = meta[q][0];
+    lrs[q]->mean = meta[q][1];
+    lrs[q]->min_entries = meta[q][2];
+  }
   return ANCKA_OK;
 }
 
@@ -1523,14 +1580,10 @@ ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld
                              &le, s));
     ANCKA_TRY(ws.alloc(&E, (size_t)w.m * ld));
   }
-  int32_t h[2] = {0, 0};
-  ANCKA_CUDA(cudaMemcpyAsync(&h[0], lt.count, 4, cudaMemcpyDeviceToHost, s));
-  if (hyper) ANCKA_CUDA(cudaMemcpyAsync(&h[1], le.count, 4, cudaMemcpyDeviceToHost, s));
-  ANCKA_CUDA(cudaStreamSynchronize(s));
-  lt.count_host = h[0];
-  le.count_host = h[1];
   ANCKA_TRY(build_long_items(ws, w.topo.ptr, nullptr, &lt, s));
   if (hyper) ANCKA_TRY(build_long_items(ws, w.edges.ptr, nullptr, &le, s));
+  LongRows* lrs[2] = {&lt, &le};
+  ANCKA_TRY(read_long_rows(lrs, hyper ? 2 : 1, s));
   for (int c0 = 0; c0 < ld; c0 += 64) {
     const int cw = ld - c0 < 64 ? ld - c0 : 64;
     SpmmArgs a;
@@ -1794,14 +1847,13 @@ struct PhaseTimer {
   int phase;
   PhaseTimer(IterTrace* t, cudaStream_t st, int ph) : tr(t), s(st), phase(ph) {
     if (tr && tr->events) {
-      cudaEventCreate(&a);
+      a = pooled_event();
       cudaEventRecord(a, s);
     }
   }
   ~PhaseTimer() {
     if (tr && tr->events) {
-      cudaEvent_t b;
-      cudaEventCreate(&b);
+      cudaEvent_t b = pooled_event();
       cudaEventRecord(b, s);
       tr->events->push_back(a);
       tr->events->push_back(b);
@@ -1829,25 +1881,20 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(ws.alloc(&E, (size_t)(w.m > 0 ? w.m : 1) * (ld > ldk ? ld : ldk)));
   Ctx c{w, n, k, ld, ldk, cfg.alpha, E, s, {}, {}, {}};
   const double qbytes = (double)n * ld * 4.0, ebytes = (double)w.m * ld * 4.0;
+  // the KNN part's nnz is an upper bound (its exact count stays on the device)
   ANCKA_TRY(find_long_rows(ws, w.topo.ptr, w.knn.ptr, n, w.topo.nnz + w.knn.nnz,
                            w.kind == ANCKA_HYPERGRAPH ? ebytes : qbytes, &c.lr_walk, s));
   ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, n, w.topo.nnz, w.kind == ANCKA_HYPERGRAPH ? ebytes : qbytes,
                            &c.lr_topo, s));
   if (w.kind == ANCKA_HYPERGRAPH)
     ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, qbytes, &c.lr_edges, s));
-  {
-    int32_t h[3] = {0, 0, 0};
-    ANCKA_CUDA(cudaMemcpyAsync(&h[0], c.lr_walk.count, 4, cudaMemcpyDeviceToHost, s));
-    ANCKA_CUDA(cudaMemcpyAsync(&h[1], c.lr_topo.count, 4, cudaMemcpyDeviceToHost, s));
-    if (c.lr_edges.count) ANCKA_CUDA(cudaMemcpyAsync(&h[2], c.lr_edges.count, 4, cudaMemcpyDeviceToHost, s));
-    ANCKA_CUDA(cudaStreamSynchronize(s));
-    c.lr_walk.count_host = h[0];
-    c.lr_topo.count_host = h[1];
-    c.lr_edges.count_host = h[2];
-  }
   ANCKA_TRY(build_long_items(ws, w.topo.ptr, w.knn.ptr, &c.lr_walk, s));
   ANCKA_TRY(build_long_items(ws, w.topo.ptr, nullptr, &c.lr_topo, s));
   if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(build_long_items(ws, w.edges.ptr, nullptr, &c.lr_edges, s));
+  {
+    LongRows* lrs[3] = {&c.lr_walk, &c.lr_topo, &c.lr_edges};
+    ANCKA_TRY(read_long_rows(lrs, w.kind == ANCKA_HYPERGRAPH ? 3 : 2, s));
+  }
   Scratch sc;
   ANCKA_TRY(ws.alloc(&sc.cnt, 64));
   ANCKA_TRY(ws.alloc(&sc.inv, 64));

@@ -142,7 +142,9 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
          const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ rinv,
          const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx, int lists,
          int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ fb_rows,
-         float* __restrict__ fb_thr, int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand) {
+         float* __restrict__ fb_thr, int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand,
+         const int32_t* __restrict__ list_err) {
+  if (list_err && *list_err) return;  // the list pass failed: its lists are not valid (uniform over the grid)
   __shared__ unsigned int block_cand;
   if (threadIdx.x == 0) block_cand = 0;
   __syncthreads();
@@ -308,7 +310,8 @@ k_rerank_collected(const float* __restrict__ X, int d, int K, const double* __re
                    const int32_t* __restrict__ rows, const int32_t* __restrict__ n_rows_p,
                    const int32_t* __restrict__ cnt, const int32_t* __restrict__ buf, int cap,
                    int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ ov_rows,
-                   int32_t* __restrict__ ov_count) {
+                   int32_t* __restrict__ ov_count, const int32_t* __restrict__ collect_err) {
+  if (*collect_err) return;  // the collect pass failed: its buffers are not valid
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (r >= *n_rows_p) return;
@@ -442,9 +445,9 @@ __global__ void k_exh_merge(const int32_t* __restrict__ rows, const int32_t* __r
 
 ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K,
                         const PrepOut& pr, int list_prec, float acc_coef, float acc_bf16, float* cand_val,
-                        int32_t* cand_idx, int lists, int collect_prec, int32_t* out_idx, float* out_sim,
-                        int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive, bool want_counts,
-                        cudaStream_t s) {
+                        int32_t* cand_idx, int lists, int collect_prec, const int32_t* list_err, int32_t* out_idx,
+                        float* out_sim, int64_t* n_candidates, int64_t* n_fallback, int64_t* n_exhaustive,
+                        bool want_counts, cudaStream_t s) {
   int32_t *fb_rows, *fb_count;
   unsigned long long* ncand;
   double* rinv;
@@ -454,6 +457,8 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
   ANCKA_TRY(ws.alloc(&fb_rows, (size_t)n));
   ANCKA_TRY(ws.zeros(&fb_count, 1));
   ANCKA_TRY(ws.zeros(&ncand, 1));
+  const int32_t* collect_err = nullptr;  // read back with the counts at the end
+  const int32_t* ex_count_dev = nullptr;
   const bool use_candidates = cand_val != nullptr;
   if (use_candidates) {
     const bool fp8 = list_prec == ANCKA_PREC_FP8;
@@ -461,7 +466,7 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     if (collect_prec == ANCKA_PREC_BF16 && !fp8) ANCKA_TRY(ws.alloc(&fb_thr, (size_t)n));
     k_rerank<<<(unsigned)ceil_div(n, kWarps), kWarps * 32, 0, s>>>(
         X, nullptr, n, d, K, fp8 ? pr.err8 : pr.err, fp8 ? pr.err8_max : pr.err_max, acc_coef, rinv, cand_val,
-        cand_idx, lists, out_idx, out_sim, fb_rows, fb_thr, fb_count, ncand);
+        cand_idx, lists, out_idx, out_sim, fb_rows, fb_thr, fb_count, ncand, list_err);
     ANCKA_LAUNCHED();
     int32_t* cl_rows = fb_rows;   // rows for the collect pass, their count and thresholds
     int32_t* cl_count = fb_count;
@@ -469,9 +474,15 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     if (fp8) {
       // rows the FP8 lists could not certify: BF16 lists for those rows, then
       // the BF16 certificate; what it cannot settle goes to the collect pass
-      int32_t nf8 = 0;
+      int32_t nf8 = 0, le = 0;
       ANCKA_CUDA(cudaMemcpyAsync(&nf8, fb_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      if (list_err) ANCKA_CUDA(cudaMemcpyAsync(&le, list_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       ANCKA_CUDA(cudaStreamSynchronize(s));
+      if (le) {
+        set_error("tensor-core contraction: a pipeline wait expired (role %d)", le);
+        return ANCKA_ERR_TIMEOUT;
+      }
+      list_err = nullptr;  // checked
       ANCKA_TRY(ws.alloc(&cl_rows, (size_t)(nf8 > 0 ? nf8 : 1)));
       ANCKA_TRY(ws.zeros(&cl_count, 1));
       ANCKA_TRY(ws.alloc(&cl_thr, (size_t)(nf8 > 0 ? nf8 : 1)));
@@ -481,15 +492,9 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
         ANCKA_TRY(knn_list_gathered_bf16(ws, pr, n, fb_rows, nf8, cand_val, cand_idx, terr, s));
         k_rerank<<<(unsigned)ceil_div(nf8, kWarps), kWarps * 32, 0, s>>>(
             X, fb_rows, nf8, d, K, pr.err, pr.err_max, acc_bf16, rinv, cand_val, cand_idx, 2, out_idx, out_sim,
-            cl_rows, cl_thr, cl_count, ncand);
+            cl_rows, cl_thr, cl_count, ncand, terr);
         ANCKA_LAUNCHED();
-        int32_t hterr = 0;
-        ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        ANCKA_CUDA(cudaStreamSynchronize(s));
-        if (hterr) {
-          set_error("tensor-core BF16 list pass: a pipeline wait expired (role %d)", hterr);
-          return ANCKA_ERR_TIMEOUT;
-        }
+        list_err = terr;  // reported with the next read
       }
     }
     int32_t* ex_rows = cl_rows;
@@ -497,9 +502,15 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     if (collect_prec == ANCKA_PREC_BF16) {
       // flagged rows: collect every key above the row's certified threshold
       // with the tensor-core contraction, then re-rank those exactly
-      int32_t nf = 0;
+      int32_t nf = 0, le = 0;
       ANCKA_CUDA(cudaMemcpyAsync(&nf, cl_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      if (list_err) ANCKA_CUDA(cudaMemcpyAsync(&le, list_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       ANCKA_CUDA(cudaStreamSynchronize(s));
+      if (le) {
+        set_error("tensor-core list pass: a pipeline wait expired (role %d)", le);
+        return ANCKA_ERR_TIMEOUT;
+      }
+      list_err = nullptr;  // checked
       ANCKA_TRY(ws.zeros(&ex_count, 1));
       ANCKA_TRY(ws.alloc(&ex_rows, (size_t)(nf > 0 ? nf : 1)));
       if (nf > 0) {
@@ -510,15 +521,9 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
         ANCKA_TRY(ws.zeros(&terr, 1));
         ANCKA_TRY(knn_collect_bf16(ws, pr, n, cl_rows, nf, cl_thr, cnt, buf, kCap, terr, s));
         k_rerank_collected<<<(unsigned)ceil_div(nf, kWarps), kWarps * 32, 0, s>>>(
-            X, d, K, rinv, cl_rows, cl_count, cnt, buf, kCap, out_idx, out_sim, ex_rows, ex_count);
+            X, d, K, rinv, cl_rows, cl_count, cnt, buf, kCap, out_idx, out_sim, ex_rows, ex_count, terr);
         ANCKA_LAUNCHED();
-        int32_t hterr = 0;
-        ANCKA_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        ANCKA_CUDA(cudaStreamSynchronize(s));
-        if (hterr) {
-          set_error("tensor-core collect pass: a pipeline wait expired (role %d)", hterr);
-          return ANCKA_ERR_TIMEOUT;
-        }
+        collect_err = terr;  // reported with the final read
       }
     }
     // rows left: sliced over the whole GPU when few, one CTA per row when many
@@ -533,12 +538,7 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     k_knn_exhaustive<<<304, kExWarps * 32, 0, s>>>(X, n, d, K, rinv, ex_rows, ex_count, 0, out_idx,
                                                    out_sim);
     ANCKA_LAUNCHED();
-    if (want_counts) {
-      int32_t ex = 0;
-      ANCKA_CUDA(cudaMemcpyAsync(&ex, ex_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      ANCKA_CUDA(cudaStreamSynchronize(s));
-      if (n_exhaustive) *n_exhaustive = ex;
-    }
+    ex_count_dev = ex_count;
   } else {
     const unsigned g = (unsigned)(n < 4096 ? n : 4096);
     k_knn_exhaustive<<<g, kExWarps * 32, 0, s>>>(X, n, d, K, rinv, nullptr, nullptr, n, out_idx,
@@ -546,14 +546,29 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     ANCKA_LAUNCHED();
     if (n_exhaustive) *n_exhaustive = n;
   }
-  if (want_counts) {
-    int32_t fb = 0;
+  // one host read for the counts and the error flags not read yet
+  if (want_counts || collect_err || list_err) {
+    int32_t fb = 0, ex = 0, ce = 0, le = 0;
     unsigned long long nc = 0;
     ANCKA_CUDA(cudaMemcpyAsync(&fb, fb_count, sizeof(fb), cudaMemcpyDeviceToHost, s));
     ANCKA_CUDA(cudaMemcpyAsync(&nc, ncand, sizeof(nc), cudaMemcpyDeviceToHost, s));
+    if (ex_count_dev) ANCKA_CUDA(cudaMemcpyAsync(&ex, ex_count_dev, sizeof(ex), cudaMemcpyDeviceToHost, s));
+    if (collect_err) ANCKA_CUDA(cudaMemcpyAsync(&ce, collect_err, sizeof(ce), cudaMemcpyDeviceToHost, s));
+    if (list_err) ANCKA_CUDA(cudaMemcpyAsync(&le, list_err, sizeof(le), cudaMemcpyDeviceToHost, s));
     ANCKA_CUDA(cudaStreamSynchronize(s));
-    *n_fallback = use_candidates ? fb : n;
-    *n_candidates = (int64_t)nc;
+    if (le) {
+      set_error("tensor-core list pass: a pipeline wait expired (role %d)", le);
+      return ANCKA_ERR_TIMEOUT;
+    }
+    if (ce) {
+      set_error("tensor-core collect pass: a pipeline wait expired (role %d)", ce);
+      return ANCKA_ERR_TIMEOUT;
+    }
+    if (want_counts) {
+      *n_fallback = use_candidates ? fb : n;
+      *n_candidates = (int64_t)nc;
+      if (ex_count_dev && n_exhaustive) *n_exhaustive = ex;
+    }
   }
   return ANCKA_OK;
 }
