@@ -41,12 +41,23 @@ __device__ __forceinline__ double dkey_value(unsigned long long k) {
   return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
 }
 
-// bitonic sort of one (value, index) pair per lane: lane 0 ends with the
-// first element of the (value desc, index asc) order.  Compares integer keys
-// (the FP64 pipe is narrow on this part).
-__device__ __forceinline__ void warp_sort(double& v, int32_t& j) {
+// order-preserving map of a float to 32 bits
+__device__ __forceinline__ uint32_t fkey(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_value(uint32_t k) { return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k); }
+
+// key of a normalised float-float value hi + lo (|lo| <= ulp(hi) / 2): by hi,
+// then by lo
+__device__ __forceinline__ unsigned long long ffkey(float hi, float lo) {
+  return ((unsigned long long)fkey(hi) << 32) | fkey(lo);
+}
+
+// bitonic sort of one (key, index) pair per lane: lane 0 ends with the first
+// element of the (key desc, index asc) order
+__device__ __forceinline__ void warp_sort_key(unsigned long long& key, int32_t& j) {
   const int lane = threadIdx.x & 31;
-  unsigned long long key = dkey(v);
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
@@ -63,6 +74,13 @@ __device__ __forceinline__ void warp_sort(double& v, int32_t& j) {
       }
     }
   }
+}
+
+// the same order on FP64 values, through integer keys (the FP64 pipe is
+// narrow on this part)
+__device__ __forceinline__ void warp_sort(double& v, int32_t& j) {
+  unsigned long long key = dkey(v);
+  warp_sort_key(key, j);
   v = dkey_value(key);
 }
 
@@ -93,6 +111,29 @@ __device__ __forceinline__ void dot2_rows(const float* __restrict__ xi, const fl
 // (0 for a zero row), evaluated in double; +0 for a zero result
 __device__ __forceinline__ double cos_from(float s, float c, double ri, double rj) {
   return ((double)s + (double)c) * ri * rj + 0.0;
+}
+
+// (ah + al)(bh + bl) as a normalised float-float pair (TwoProd by FMA, the
+// cross terms added to the error, then a fast TwoSum)
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  ph = p + e;
+  pl = e - (ph - p);
+}
+
+// the same cosine in float-float on the FP32 pipe: the Dot2 pair times the
+// inverse norms (float-float pairs); +0 for a zero result.  Its error is
+// that of the Dot2 sum (~2^-44 relative), as in the FP64 form.
+__device__ __forceinline__ void cos_ff(float s, float c, float2 ri, float2 rj, float& h, float& l) {
+  float sh, sl;
+  two_sum(s, c, sh, sl);
+  float th, tl;
+  ff_mul(sh, sl, ri.x, ri.y, th, tl);
+  ff_mul(th, tl, rj.x, rj.y, h, l);
+  h = h + 0.f;
 }
 
 // Dot2 dot products of row i with up to four rows j[u] (j[u] < 0: skipped)
@@ -131,15 +172,20 @@ __device__ __forceinline__ void dot2_rows4(const float* __restrict__ X, const fl
   for (int u = 0; u < 4; ++u) dot2_warp_reduce(s[u], c[u]);
 }
 
-__global__ void k_inv_norms(const double* __restrict__ nrm2, int64_t n, double* __restrict__ rinv) {
+__global__ void k_inv_norms(const double* __restrict__ nrm2, int64_t n, double* __restrict__ rinv,
+                            float2* __restrict__ rinv2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) rinv[i] = nrm2[i] > 0.0 ? 1.0 / sqrt(nrm2[i]) : 0.0;
+  if (i >= n) return;
+  const double r = nrm2[i] > 0.0 ? 1.0 / sqrt(nrm2[i]) : 0.0;
+  rinv[i] = r;
+  const float h = (float)r;
+  rinv2[i] = make_float2(h, (float)(r - (double)h));
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
 k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64_t n_rows, int d, int K,
          const float* __restrict__ err,
-         const float* __restrict__ err_max_p, float acc_coef, const double* __restrict__ rinv,
+         const float* __restrict__ err_max_p, float acc_coef, const float2* __restrict__ rinv2,
          const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx, int lists,
          int32_t* __restrict__ out_idx, float* __restrict__ out_sim, int32_t* __restrict__ fb_rows,
          float* __restrict__ fb_thr, int32_t* __restrict__ fb_count, unsigned long long* __restrict__ n_cand,
@@ -201,8 +247,8 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
       unsigned rmask = __ballot_sync(0xffffffffu, inR);
       if (lane == 0) atomicAdd(&block_cand, (unsigned)__popc(rmask));
       const float* xi = X + i * (int64_t)d;
-      const double ri = rinv[i];
-      double myv = -INFINITY;
+      const float2 ri = rinv2[i];
+      unsigned long long myk = 0;  // below every cosine's key
       int32_t myj = INT32_MAX;
       while (rmask) {  // four candidates per pass
         int tl[4];
@@ -219,14 +265,16 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
 #pragma unroll
         for (int u = 0; u < 4; ++u)
           if (lane == tl[u]) {  // the owner lane alone evaluates its cosine
-            myv = cos_from(ds[u], dc[u], ri, rinv[jt[u]]);
+            float h, l;
+            cos_ff(ds[u], dc[u], ri, rinv2[jt[u]], h, l);
+            myk = ffkey(h, l);
             myj = jt[u];
           }
       }
-      warp_sort(myv, myj);
+      warp_sort_key(myk, myj);
       if (lane < K) {
         out_idx[i * K + lane] = myj;
-        out_sim[i * K + lane] = (float)myv;
+        out_sim[i * K + lane] = fkey_value((uint32_t)(myk >> 32));
       }
     }
   }
@@ -451,8 +499,10 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
   int32_t *fb_rows, *fb_count;
   unsigned long long* ncand;
   double* rinv;
+  float2* rinv2;
   ANCKA_TRY(ws.alloc(&rinv, (size_t)n));
-  k_inv_norms<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(pr.nrm2, n, rinv);
+  ANCKA_TRY(ws.alloc(&rinv2, (size_t)n));
+  k_inv_norms<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(pr.nrm2, n, rinv, rinv2);
   ANCKA_LAUNCHED();
   ANCKA_TRY(ws.alloc(&fb_rows, (size_t)n));
   ANCKA_TRY(ws.zeros(&fb_count, 1));
@@ -465,7 +515,7 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
     float* fb_thr = nullptr;
     if (collect_prec == ANCKA_PREC_BF16 && !fp8) ANCKA_TRY(ws.alloc(&fb_thr, (size_t)n));
     k_rerank<<<(unsigned)ceil_div(n, kWarps), kWarps * 32, 0, s>>>(
-        X, nullptr, n, d, K, fp8 ? pr.err8 : pr.err, fp8 ? pr.err8_max : pr.err_max, acc_coef, rinv, cand_val,
+        X, nullptr, n, d, K, fp8 ? pr.err8 : pr.err, fp8 ? pr.err8_max : pr.err_max, acc_coef, rinv2, cand_val,
         cand_idx, lists, out_idx, out_sim, fb_rows, fb_thr, fb_count, ncand, list_err);
     ANCKA_LAUNCHED();
     int32_t* cl_rows = fb_rows;   // rows for the collect pass, their count and thresholds
@@ -491,7 +541,7 @@ ancka_status knn_rerank(Workspace& ws, const float* X, int64_t n, int32_t d, int
         ANCKA_TRY(ws.zeros(&terr, 1));
         ANCKA_TRY(knn_list_gathered_bf16(ws, pr, n, fb_rows, nf8, cand_val, cand_idx, terr, s));
         k_rerank<<<(unsigned)ceil_div(nf8, kWarps), kWarps * 32, 0, s>>>(
-            X, fb_rows, nf8, d, K, pr.err, pr.err_max, acc_bf16, rinv, cand_val, cand_idx, 2, out_idx, out_sim,
+            X, fb_rows, nf8, d, K, pr.err, pr.err_max, acc_bf16, rinv2, cand_val, cand_idx, 2, out_idx, out_sim,
             cl_rows, cl_thr, cl_count, ncand, terr);
         ANCKA_LAUNCHED();
         list_err = terr;  // reported with the next read
