@@ -311,9 +311,12 @@ ancka_status warm_predict_impl(Workspace& ws, const Walk& w, const float* X, int
   return ANCKA_OK;
 }
 
+// x_ready (may be null): an event after which X is valid on the device; the
+// topology build, which does not read X, runs before the stream waits on it.
 ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d, const int32_t* knn_idx_in,
                           const float* knn_sim_in, const ancka_params* p, int32_t* labels,
-                          const ancka_outputs* out, ancka_info* info, cudaStream_t s) {
+                          const ancka_outputs* out, ancka_info* info, cudaStream_t s,
+                          cudaEvent_t x_ready = nullptr) {
   ANCKA_TRY(device_check());
   ANCKA_TRY(validate_topology(topo));
   const int64_t n = topo->n;
@@ -348,6 +351,12 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     int64_t ncand = 0, nfb = 0, nex = 0;
     int32_t* bad;
     st = ws.zeros(&bad, 1);
+    Walk w;
+    if (st == ANCKA_OK) {  // the topology part of the walk needs no attributes
+      Phase ph(tp, s, 1);
+      st = build_topology(ws, *topo, &w, s);
+    }
+    if (st == ANCKA_OK && x_ready) ANCKA_CUDA(cudaStreamWaitEvent(s, x_ready, 0));
     if (st == ANCKA_OK && !knn_idx_in) {
       Phase ph(tp, s, 0);
       if (!idx) st = ws.alloc(&idx, (size_t)n * K);
@@ -386,11 +395,9 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
         st = ANCKA_ERR_INVALID_ARG;
       }
     }
-    Walk w;
     if (st == ANCKA_OK) {
       Phase ph(tp, s, 1);
-      st = build_topology(ws, *topo, &w, s);
-      if (st == ANCKA_OK) st = build_knn_part(ws, n, K, idx, sim, zero_row, p->beta, &w, s);
+      st = build_knn_part(ws, n, K, idx, sim, zero_row, p->beta, &w, s);
     }
     IterTrace tr{};
     if (st == ANCKA_OK) {
@@ -635,13 +642,26 @@ ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int3
   ANCKA_REQUIRE(d >= 1 && d <= 4096, "d out of range");
   ancka_topology dt = *topo;
   ancka_status st = ANCKA_OK;
+  // X (the large copy) goes on a second stream so that the topology build
+  // overlaps it; the call's stream waits for it before the KNN
+  static thread_local cudaStream_t xs = nullptr;
+  if (!xs) ANCKA_CUDA(cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking));
+  // on every exit: s waits for the copy before the workspace frees dX on s,
+  // and the events go back to the pool
+  struct CopyGuard {
+    cudaStream_t s;
+    cudaEvent_t alloc_ev, x_ev;
+    bool recorded = false;
+    ~CopyGuard() {
+      if (recorded) cudaStreamWaitEvent(s, x_ev, 0);
+      release_event(alloc_ev);
+      release_event(x_ev);
+    }
+  };
   {
     Workspace ws(s);
-    float* dX;
-    int32_t* dlab;
-    ANCKA_TRY(ws.alloc(&dX, (size_t)n * d));
-    ANCKA_TRY(ws.alloc(&dlab, (size_t)n));
-    ANCKA_CUDA(cudaMemcpyAsync(dX, X, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
+    CopyGuard guard{s, pooled_event(), pooled_event()};
+    cudaEvent_t alloc_ev = guard.alloc_ev, x_ev = guard.x_ev;
     if (topo->kind == ANCKA_HYPERGRAPH) {
       const int64_t m = topo->m;
       const int64_t nnz = topo->he_ptr[m];
@@ -665,6 +685,17 @@ ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int3
       dt.row_ptr = rp;
       dt.col_idx = ci;
     }
+    // X after the topology: copies on one engine run in issue order, and the
+    // topology build should not wait behind the large copy
+    float* dX;
+    int32_t* dlab;
+    ANCKA_TRY(ws.alloc(&dX, (size_t)n * d));
+    ANCKA_TRY(ws.alloc(&dlab, (size_t)n));
+    ANCKA_CUDA(cudaEventRecord(alloc_ev, s));  // the allocation is valid on xs after this point of s
+    ANCKA_CUDA(cudaStreamWaitEvent(xs, alloc_ev, 0));
+    ANCKA_CUDA(cudaMemcpyAsync(dX, X, sizeof(float) * n * d, cudaMemcpyHostToDevice, xs));
+    ANCKA_CUDA(cudaEventRecord(x_ev, xs));
+    guard.recorded = true;
     ancka_params dp = *p;
     int32_t* dinit = nullptr;
     if (p->init == 1) {
@@ -672,7 +703,7 @@ ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int3
       ANCKA_CUDA(cudaMemcpyAsync(dinit, p->init_labels, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
       dp.init_labels = dinit;
     }
-    st = cluster_impl(&dt, dX, d, nullptr, nullptr, &dp, dlab, nullptr, info, s);
+    st = cluster_impl(&dt, dX, d, nullptr, nullptr, &dp, dlab, nullptr, info, s, x_ev);
     if (st == ANCKA_OK) ANCKA_CUDA(cudaMemcpyAsync(labels, dlab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
   }
   ANCKA_CUDA(cudaStreamSynchronize(s));

@@ -577,10 +577,16 @@ __device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int
                                int32_t* __restrict__ status, double* csm, float2* scratch);
 
 // Gram partials of Z; the CTA that finishes last (atomic ticket) sums the
-// partials and factors them (chol_inv_block), so one launch does both.
+// partials and factors them (chol_inv_block), so one launch does both.  With
+// Rin (an R^-1 of the previous pass) the launch first forms each tile's rows
+// Q = Z R^-1 (the same terms in the same order as k_apply_rinv), writes them
+// to Qout and takes the Gram matrix of Q: CholeskyQR2's middle step in one
+// pass.  Dynamic shared memory: the k x k factorisation, or (with Rin) R^-1
+// padded to 4 nb columns and the Q tile.
 __global__ void __launch_bounds__(kGramThreads)
-k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, float2* __restrict__ partial,
-            unsigned int* __restrict__ ticket, float* __restrict__ Rinv_out, int32_t* __restrict__ status) {
+k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, const float* __restrict__ Rin,
+            float* __restrict__ Qout, float2* __restrict__ partial, unsigned int* __restrict__ ticket,
+            float* __restrict__ Rinv_out, int32_t* __restrict__ status) {
   __shared__ __align__(16) float T[kGramRows * kGramLd];
   __shared__ unsigned int my_ticket;
   extern __shared__ double csm[];
@@ -601,6 +607,14 @@ k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, float2* __re
   // that a CTA's rows arrive in few load waves
   const int tld = 4 * nb;
   const int trows = (kGramRows * kGramLd) / tld;
+  float* Rs = reinterpret_cast<float*>(csm);  // with Rin: R^-1 (tld x tld), then the Q tile
+  float* TQ = Rs + tld * tld;
+  if (Rin)
+    for (int e = t; e < tld * tld; e += kGramThreads) {
+      const int a = e / tld, c = e % tld;
+      Rs[e] = (c < w && a <= c) ? Rin[a * w + c] : 0.f;
+    }
+  const float* src = Rin ? TQ : T;
   for (int64_t rb = r0; rb < r1; rb += trows) {
     const int rows = (int)((r1 - rb) < trows ? (r1 - rb) : trows);
     __syncthreads();
@@ -613,13 +627,31 @@ k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, float2* __re
       *reinterpret_cast<float4*>(&T[r * tld + c]) = v;
     }
     __syncthreads();
+    if (Rin) {  // Q rows of the tile: q[c] = sum_{a <= c} z[a] R^-1[a, c]
+      for (int e = t; e < rows * nb; e += kGramThreads) {
+        const int r = e / nb, g = e % nb;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int amax = (4 * g + 3 < w - 1) ? 4 * g + 3 : w - 1;
+        for (int a = 0; a <= amax; ++a) {
+          const float za = T[r * tld + a];
+          const float4 rv = *reinterpret_cast<const float4*>(&Rs[a * tld + 4 * g]);
+          acc.x = fmaf(za, rv.x, acc.x);
+          acc.y = fmaf(za, rv.y, acc.y);
+          acc.z = fmaf(za, rv.z, acc.z);
+          acc.w = fmaf(za, rv.w, acc.w);
+        }
+        *reinterpret_cast<float4*>(&TQ[r * tld + 4 * g]) = acc;
+        *reinterpret_cast<float4*>(Qout + (rb + r) * ldz + 4 * g) = acc;
+      }
+      __syncthreads();
+    }
     if (active) {
       float acc[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[e] = 0.f;
       for (int r = sub; r < rows; r += S) {
-        const float4 xa = *reinterpret_cast<const float4*>(&T[r * tld + 4 * A]);
-        const float4 xb = *reinterpret_cast<const float4*>(&T[r * tld + 4 * B]);
+        const float4 xa = *reinterpret_cast<const float4*>(&src[r * tld + 4 * A]);
+        const float4 xb = *reinterpret_cast<const float4*>(&src[r * tld + 4 * B]);
         const float a4[4] = {xa.x, xa.y, xa.z, xa.w}, b4[4] = {xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -1820,22 +1852,28 @@ ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64
   return ANCKA_OK;
 }
 
-// CholeskyQR2: Q = Z R^-1 twice (diag(R) > 0), result in Z
+// CholeskyQR2 (diag(R) > 0) of the n x w block Z (result in Z, Q is scratch): Gram +
+// factor of Z; Q = Z R1^-1 with the Gram + factor of Q in one pass; Z = Q
+// R2^-1.  Rinv holds two w x w matrices.
 ancka_status cholqr2(Workspace& ws, const Ctx& c, float* Z, float* Q, int w, float2* gpart, int gblk,
                      unsigned int* ticket, float* Rinv, int32_t* status) {
   cudaStream_t s = c.s;
-  const size_t csmem = (size_t)(3 * w * w + 1) * sizeof(double);
+  const int tld = 4 * ((w + 3) / 4);
+  const size_t chol_bytes = (size_t)(3 * w * w + 1) * sizeof(double);
+  const size_t fused_bytes = (size_t)(tld * tld + kGramRows * kGramLd) * sizeof(float);
   static bool configured = false;
   if (!configured) {
     ANCKA_CUDA(cudaFuncSetAttribute(k_gram_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (3 * 65 * 65 + 1) * 8));
     configured = true;
   }
-  k_gram_chol<<<gblk, kGramThreads, csmem, s>>>(Z, c.ld, c.n, w, gpart, ticket, Rinv, status);
+  float* R1 = Rinv;
+  float* R2 = Rinv + (size_t)w * w;
+  k_gram_chol<<<gblk, kGramThreads, chol_bytes, s>>>(Z, c.ld, c.n, w, nullptr, nullptr, gpart, ticket, R1, status);
   ANCKA_LAUNCHED();
-  ANCKA_TRY(apply_rinv(Z, c.ld, c.n, w, Rinv, Q, s));
-  k_gram_chol<<<gblk, kGramThreads, csmem, s>>>(Q, c.ld, c.n, w, gpart, ticket, Rinv, status);
+  k_gram_chol<<<gblk, kGramThreads, chol_bytes > fused_bytes ? chol_bytes : fused_bytes, s>>>(
+      Z, c.ld, c.n, w, R1, Q, gpart, ticket, R2, status);
   ANCKA_LAUNCHED();
-  ANCKA_TRY(apply_rinv(Q, c.ld, c.n, w, Rinv, Z, s));
+  ANCKA_TRY(apply_rinv(Q, c.ld, c.n, w, R2, Z, s));
   (void)ws;
   return ANCKA_OK;
 }
@@ -1877,7 +1915,7 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   ANCKA_TRY(ws.alloc(&Qa, (size_t)n * ld));
   ANCKA_TRY(ws.alloc(&Qb, (size_t)n * ld));
   ANCKA_TRY(ws.alloc(&Qt, (size_t)n * ldk));
-  ANCKA_TRY(ws.alloc(&Rinv, (size_t)wq * wq));
+  ANCKA_TRY(ws.alloc(&Rinv, (size_t)2 * wq * wq));
   if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(ws.alloc(&E, (size_t)(w.m > 0 ? w.m : 1) * (ld > ldk ? ld : ldk)));
   Ctx c{w, n, k, ld, ldk, cfg.alpha, E, s, {}, {}, {}};
   const double qbytes = (double)n * ld * 4.0, ebytes = (double)w.m * ld * 4.0;
