@@ -9,6 +9,8 @@
 #include <cmath>
 #include <vector>
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace ancka {
@@ -202,9 +204,13 @@ float tc_acc_bound(int dp, int k_per_mma, int ulp_log2) {
 }
 
 // the KNN lists with every step on the device
+// after_contraction (may be empty): called once the contraction kernel is
+// enqueued, before the first host read (the cluster call starts InitBCM on a
+// second stream there, so that its kernels queue behind the contraction's)
 ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
                       int32_t* idx, float* sim, int32_t** zero_row, int64_t* ncand, int64_t* nfb,
-                      int64_t* nex, bool counts, cudaStream_t s, cudaEvent_t* contract_ev = nullptr) {
+                      int64_t* nex, bool counts, cudaStream_t s, cudaEvent_t* contract_ev = nullptr,
+                      const std::function<ancka_status()>& after_contraction = {}) {
   PrepOut pr;
   ANCKA_TRY(prep_rows(ws, X, n, d, prec, &pr, s));
   if (zero_row) *zero_row = pr.zero_row;
@@ -235,6 +241,7 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
       const double g = pr.dp * 5.960464477539063e-08;
       acc = (float)(1.01 * g / (1.0 - g));
     }
+    if (after_contraction) ANCKA_TRY(after_contraction());
     // the tensor-core kernel leaves two 16-entry lists per row (one per half
     // of the key columns), the CUDA-core kernel one 32-entry list
     ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, prec, acc, tc_acc_bound(pr.dp, 16, -22), cv, ci,
@@ -242,6 +249,7 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
                          sim, ncand, nfb, nex, counts, s));
     if (contract_ev) ANCKA_CUDA(cudaEventRecord(contract_ev[2], s));
   } else {
+    if (after_contraction) ANCKA_TRY(after_contraction());
     ANCKA_TRY(knn_rerank(ws, X, n, d, K, pr, ANCKA_PREC_FP32, 0.f, 0.f, nullptr, nullptr, 1, ANCKA_PREC_FP32,
                          nullptr, idx, sim, ncand, nfb, nex, counts, s));
   }
@@ -356,6 +364,41 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       Phase ph(tp, s, 1);
       st = build_topology(ws, *topo, &w, s);
     }
+    // InitBCM needs only the topology: with the default start it runs on a
+    // second stream, launched right after the contraction kernel so that its
+    // blocks take the room the contraction leaves (and, for host inputs, the
+    // time X is still being copied); the call's stream waits for it before
+    // the iteration, and on every exit before the workspace is released
+    static thread_local cudaStream_t is = nullptr;
+    if (!is) ANCKA_CUDA(cudaStreamCreateWithFlags(&is, cudaStreamNonBlocking));
+    struct InitJoin {
+      cudaStream_t s;
+      cudaEvent_t topo_ev = nullptr, done_ev = nullptr;
+      bool launched = false;
+      ~InitJoin() {
+        if (launched) cudaStreamWaitEvent(s, done_ev, 0);
+        if (topo_ev) release_event(topo_ev);
+        if (done_ev) release_event(done_ev);
+      }
+    } ij{s};
+    Workspace wsi(is);  // InitBCM's scratch, used and released on its stream
+    int32_t* y0_async = nullptr;
+    const IterCfg cfg{p->k, p->T, p->gamma, p->T_i, p->tau, p->disc_max_iter, p->alpha, p->early_stop, p->eps_Q};
+    auto start_init = [&]() -> ancka_status {
+      if (p->init == 1) return ANCKA_OK;  // labels given
+      ANCKA_TRY(ws.alloc(&y0_async, (size_t)n));
+      ij.topo_ev = pooled_event();
+      ij.done_ev = pooled_event();
+      ANCKA_CUDA(cudaEventRecord(ij.topo_ev, s));  // the walk's topology and y0_async are ready on s here
+      ANCKA_CUDA(cudaStreamWaitEvent(is, ij.topo_ev, 0));
+      {
+        Phase ph(tp, is, 2);
+        ANCKA_TRY(initbcm_labels(wsi, w, cfg, y0_async, is));
+      }
+      ANCKA_CUDA(cudaEventRecord(ij.done_ev, is));
+      ij.launched = true;
+      return ANCKA_OK;
+    };
     if (st == ANCKA_OK && x_ready) ANCKA_CUDA(cudaStreamWaitEvent(s, x_ready, 0));
     if (st == ANCKA_OK && !knn_idx_in) {
       Phase ph(tp, s, 0);
@@ -363,7 +406,7 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       if (st == ANCKA_OK && !sim) st = ws.alloc(&sim, (size_t)n * K);
       if (st == ANCKA_OK)
         st = knn_impl(ws, X, n, d, K, p->knn_prec, idx, sim, &zero_row, &ncand, &nfb, &nex, info != nullptr, s,
-                      info && K <= max_candidate_K(p->knn_prec) ? cev : nullptr);
+                      info && K <= max_candidate_K(p->knn_prec) ? cev : nullptr, start_init);
       contract_timed = info && K <= max_candidate_K(p->knn_prec);
     } else if (st == ANCKA_OK) {
       Phase ph(tp, s, 0);
@@ -386,6 +429,7 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       idx = const_cast<int32_t*>(knn_idx_in);
       sim = const_cast<float*>(knn_sim_in);
     }
+    if (st == ANCKA_OK && knn_idx_in) st = start_init();  // no contraction to queue behind
     if (st == ANCKA_OK && p->init == 1) {
       k_check_labels<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(p->init_labels, n, p->k, bad);
       int32_t hb = 0;
@@ -418,9 +462,10 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     if (st == ANCKA_OK) {
       tr.events = tp ? &timer.ev : nullptr;
       tr.phases = tp ? &timer.ph : nullptr;
-      IterCfg cfg{p->k, p->T, p->gamma, p->T_i, p->tau, p->disc_max_iter, p->alpha, p->early_stop, p->eps_Q};
-      st = run_ancka(ws, w, cfg, p->init == 1 ? p->init_labels : nullptr, warmW, ldwarm, labels,
-                     out ? out->Q : nullptr, out ? out->init_labels : nullptr, &tr, s);
+      const int32_t* y_init = p->init == 1 ? p->init_labels : y0_async;
+      if (y0_async && ij.launched) ANCKA_CUDA(cudaStreamWaitEvent(s, ij.done_ev, 0));
+      st = run_ancka(ws, w, cfg, y_init, warmW, ldwarm, labels, out ? out->Q : nullptr,
+                     out ? out->init_labels : nullptr, &tr, s);
     }
     if (info) cudaEventRecord(t1, s);
     if (info && (st == ANCKA_OK || st == ANCKA_ERR_NUMERIC)) {

@@ -277,6 +277,9 @@ struct IterTrace {
   std::vector<cudaEvent_t>* events;  // (phase, start, stop) triples
   std::vector<int>* phases;
 };
+// InitBCM's Y^(0) from the topology part of the walk alone (no attributes, no
+// KNN part): may run on its own stream while the KNN is computed
+ancka_status initbcm_labels(Workspace& ws, const Walk& w, const IterCfg& cfg, int32_t* y0, cudaStream_t s);
 // warm_W: n x k block predicted by the warm-start MLP (row stride ldw), or null
 ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& c, const int32_t* init_labels,
                        const float* warm_W, int ldw, int32_t* labels_out, float* Q_out, int32_t* init_out,

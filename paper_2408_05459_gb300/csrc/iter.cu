@@ -1902,6 +1902,63 @@ struct PhaseTimer {
 
 }  // namespace
 
+// InitBCM (Alg. 4 lines 3-11) on its own: the k highest-degree nodes (ties by
+// index) seed one column each, T_i hops of the topology walk, then the
+// argmax of each row gives Y^(0).  It reads only the topology part of the walk
+// (no attributes, no KNN part), with its own scratch, so it may run on a
+// stream of its own while the KNN is computed.
+ancka_status initbcm_labels(Workspace& ws, const Walk& w, const IterCfg& cfg, int32_t* y0, cudaStream_t s) {
+  const int64_t n = w.n;
+  const int k = cfg.k;
+  const int ld = (int)round_up(k + 1, 4);
+  const int ldk = (int)round_up(k, 4);
+  const bool hyper = w.kind == ANCKA_HYPERGRAPH;
+  float* E = nullptr;
+  if (hyper) ANCKA_TRY(ws.alloc(&E, (size_t)(w.m > 0 ? w.m : 1) * ldk));
+  Ctx c{w, n, k, ld, ldk, cfg.alpha, E, s, {}, {}, {}};
+  // the same long-row classes as the iteration's (block sizes at width ld)
+  const double qbytes = (double)n * ld * 4.0, ebytes = (double)w.m * ld * 4.0;
+  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, n, w.topo.nnz, hyper ? ebytes : qbytes, &c.lr_topo, s));
+  if (hyper) ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, qbytes, &c.lr_edges, s));
+  ANCKA_TRY(build_long_items(ws, w.topo.ptr, nullptr, &c.lr_topo, s));
+  if (hyper) ANCKA_TRY(build_long_items(ws, w.edges.ptr, nullptr, &c.lr_edges, s));
+  {
+    LongRows* lrs[2] = {&c.lr_topo, &c.lr_edges};
+    ANCKA_TRY(read_long_rows(lrs, hyper ? 2 : 1, s));
+  }
+  float *Fa, *Fb;
+  ANCKA_TRY(ws.alloc(&Fa, (size_t)n * ldk));
+  ANCKA_TRY(ws.alloc(&Fb, (size_t)n * ldk));
+  uint64_t *keys, *skeys;
+  int32_t* seedcol;
+  ANCKA_TRY(ws.alloc(&keys, (size_t)n));
+  ANCKA_TRY(ws.alloc(&skeys, (size_t)n));
+  ANCKA_TRY(ws.alloc(&seedcol, (size_t)n));
+  ANCKA_CUDA(cudaMemsetAsync(seedcol, 0xff, sizeof(int32_t) * n, s));
+  k_degree_keys<<<grid_for(n, 256), 256, 0, s>>>(w.degree, n, keys);
+  ANCKA_LAUNCHED();
+  size_t tmp = 0;
+  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, keys, skeys, n, 0, 64, s));
+  char* t;
+  ANCKA_TRY(ws.alloc(&t, tmp));
+  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, keys, skeys, n, 0, 64, s));
+  k_seed_setup<<<1, 32, 0, s>>>(skeys, k, seedcol);
+  ANCKA_LAUNCHED();
+  k_fill_seed<<<grid_for(n * ldk, 256), 256, 0, s>>>(seedcol, n, ldk, cfg.alpha, Fa);
+  ANCKA_LAUNCHED();
+  float* cur = Fa;
+  float* nxt = Fb;
+  for (int t2 = 0; t2 < cfg.T_i; ++t2) {
+    ANCKA_TRY(initbcm_hop(c, cur, nxt, seedcol));
+    float* tt = cur;
+    cur = nxt;
+    nxt = tt;
+  }
+  k_argmax_rows<<<grid_for(n, 256), 256, 0, s>>>(cur, ldk, n, k, y0);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
 // phases: 2 = init, 3 = iteration, 4 = discretize, 5 = mhc, 6 = the walk products inside 3
 ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const int32_t* init_labels,
                        const float* warm_W, int ldw, int32_t* labels_out, float* Q_out, int32_t* init_out,
@@ -1922,16 +1979,13 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   // the KNN part's nnz is an upper bound (its exact count stays on the device)
   ANCKA_TRY(find_long_rows(ws, w.topo.ptr, w.knn.ptr, n, w.topo.nnz + w.knn.nnz,
                            w.kind == ANCKA_HYPERGRAPH ? ebytes : qbytes, &c.lr_walk, s));
-  ANCKA_TRY(find_long_rows(ws, w.topo.ptr, nullptr, n, w.topo.nnz, w.kind == ANCKA_HYPERGRAPH ? ebytes : qbytes,
-                           &c.lr_topo, s));
   if (w.kind == ANCKA_HYPERGRAPH)
     ANCKA_TRY(find_long_rows(ws, w.edges.ptr, nullptr, w.m, w.edges.nnz, qbytes, &c.lr_edges, s));
   ANCKA_TRY(build_long_items(ws, w.topo.ptr, w.knn.ptr, &c.lr_walk, s));
-  ANCKA_TRY(build_long_items(ws, w.topo.ptr, nullptr, &c.lr_topo, s));
   if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(build_long_items(ws, w.edges.ptr, nullptr, &c.lr_edges, s));
   {
-    LongRows* lrs[3] = {&c.lr_walk, &c.lr_topo, &c.lr_edges};
-    ANCKA_TRY(read_long_rows(lrs, w.kind == ANCKA_HYPERGRAPH ? 3 : 2, s));
+    LongRows* lrs[2] = {&c.lr_walk, &c.lr_edges};
+    ANCKA_TRY(read_long_rows(lrs, w.kind == ANCKA_HYPERGRAPH ? 2 : 1, s));
   }
   Scratch sc;
   ANCKA_TRY(ws.alloc(&sc.cnt, 64));
@@ -1960,33 +2014,7 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     if (init_labels) {
       ANCKA_CUDA(cudaMemcpyAsync(y0, init_labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     } else {
-      uint64_t *keys, *skeys;
-      int32_t* seedcol;
-      ANCKA_TRY(ws.alloc(&keys, (size_t)n));
-      ANCKA_TRY(ws.alloc(&skeys, (size_t)n));
-      ANCKA_TRY(ws.alloc(&seedcol, (size_t)n));
-      ANCKA_CUDA(cudaMemsetAsync(seedcol, 0xff, sizeof(int32_t) * n, s));
-      k_degree_keys<<<grid_for(n, 256), 256, 0, s>>>(w.degree, n, keys);
-      ANCKA_LAUNCHED();
-      size_t tmp = 0;
-      ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, keys, skeys, n, 0, 64, s));
-      char* t;
-      ANCKA_TRY(ws.alloc(&t, tmp));
-      ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, keys, skeys, n, 0, 64, s));
-      k_seed_setup<<<1, 32, 0, s>>>(skeys, k, seedcol);
-      ANCKA_LAUNCHED();
-      k_fill_seed<<<grid_for(n * ldk, 256), 256, 0, s>>>(seedcol, n, ldk, cfg.alpha, sc.Fa);
-      ANCKA_LAUNCHED();
-      float* cur = sc.Fa;
-      float* nxt = sc.Fb;
-      for (int t2 = 0; t2 < cfg.T_i; ++t2) {
-        ANCKA_TRY(initbcm_hop(c, cur, nxt, seedcol));
-        float* tt = cur;
-        cur = nxt;
-        nxt = tt;
-      }
-      k_argmax_rows<<<grid_for(n, 256), 256, 0, s>>>(cur, ldk, n, k, y0);
-      ANCKA_LAUNCHED();
+      ANCKA_TRY(initbcm_labels(ws, w, cfg, y0, s));
     }
     // Q^(0) = [n^-1/2 1 | h(Y^(0))]
     ANCKA_CUDA(cudaMemsetAsync(sc.cnt, 0, sizeof(int32_t) * k, s));
