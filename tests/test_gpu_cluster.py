@@ -178,3 +178,41 @@ def test_wide_block_k64(ak):
     assert np.array_equal(ex["init_labels"], o["init_labels"])
     assert O.max_principal_angle(ex["Q"], o["Q"]) <= ANGLE_MAX
     assert abs(info["phi"][0] - o["phi"][0]) <= 1e-4   # later phi follow the near-tie labels
+
+
+def test_multiplex_workload_with_verified_knn(ak):
+    """Full-size multiplex workload (n = 5e5, three SBM layers with mean degree
+    20, k = 20, d = 256, T = 8): the BF16 KNN checked on sampled rows, then the
+    oracle's Algorithm 4 on the same lists against the GPU's labels and block."""
+    g = synth.config_multiplex(0)
+    labels, ex, info = _gpu_cluster(ak, g, "bf16", k=20, T=8)
+    rows = np.random.default_rng(2).choice(g["n"], 128, replace=False)
+    compare_knn(g["X"], 10, rows, ex["knn_idx"], ex["knn_sim"])
+    p = _params(ak, k=20, T=8)
+    o = O.ancka(g, g["X"], _oracle_params(p), knn=ex["knn_idx"])
+    assert np.array_equal(ex["init_labels"], o["init_labels"])
+    ari, ang = compare_iteration(o, labels, ex["Q"])
+    assert ang <= ANGLE_MAX and ari >= ARI_MIN, (ari, ang)
+
+
+def test_large_dcsbm_workload_properties(ak):
+    """Full-size DC-SBM workload (n = 2.4e6, 6e7 edges, power-law degrees,
+    k = 47, d = 100, beta = 0.4, T_i = 1), too large for the oracle's iteration:
+    the BF16 KNN exact on sampled rows; the final block orthonormal, with first
+    column +-n^-1/2 (every node has an edge, so the walk is row-stochastic);
+    labels in [0, k); the kept labelling never worse than the initial one;
+    agreement with the planted partition."""
+    g = synth.config_large_dcsbm(0)
+    n, k = g["n"], 47
+    labels, ex, info = _gpu_cluster(ak, g, "bf16", k=k, beta=0.4, T_i=1)
+    rows = np.random.default_rng(3).choice(n, 48, replace=False)
+    compare_knn(g["X"], 10, rows, ex["knn_idx"], ex["knn_sim"])
+    Q = ex["Q"].astype(np.float64)
+    assert Q.shape == (n, k + 1)
+    assert np.max(np.abs(Q.T @ Q - np.eye(k + 1))) <= 1e-4
+    assert np.max(np.abs(np.abs(Q[:, 0]) * np.sqrt(n) - 1.0)) <= 1e-3
+    assert labels.min() >= 0 and labels.max() < k
+    assert info["phi_best"] <= info["phi"][0] + 1e-12
+    # a regression guard on the method's result for this seeded input (0.80 measured)
+    ari = O.adjusted_rand_index(labels, g["labels"])
+    assert ari >= 0.75, ari
