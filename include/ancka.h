@@ -178,6 +178,16 @@ ancka_status ancka_device_check(void);
  * scans of the graph build are not counted). */
 int64_t ancka_kernel_launches(void);
 
+/* Tuning (process-wide, thread-safe): BF16 KNN lists of inputs with at least
+ * n_min rows come from the symmetric contraction, which multiplies only the
+ * pairs j > i (Section 3.1: the cosine is symmetric) and pushes each score to
+ * both rows through thresholds taken from a sampled pass; the lists, and so
+ * ancka_knn's results, are the same as the full sweep's.  Smaller inputs use
+ * the full sweep.  Default INT64_MAX (never: its appends still cost more than
+ * the full sweep's list upkeep saves); n_min <= 1 selects the symmetric form
+ * for every size.  FP32 and FP8 are not affected. */
+void ancka_set_symmetric_knn_min_rows(int64_t n_min);
+
 /* KNN lists of Section 3.1 (Eq. AK inputs).
  *   X        n x d FP32 attributes (device, row-major, any values; a zero row
  *            has similarity 0 to everything)

@@ -115,6 +115,8 @@ def load(path: str = LIB_PATH):
     L.ancka_device_check.restype = ctypes.c_int
     L.ancka_kernel_launches.argtypes = []
     L.ancka_kernel_launches.restype = ctypes.c_int64
+    L.ancka_set_symmetric_knn_min_rows.argtypes = [ctypes.c_int64]
+    L.ancka_set_symmetric_knn_min_rows.restype = None
     L.ancka_knn.argtypes = [vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(Info), vp]
     L.ancka_knn.restype = ctypes.c_int
     L.ancka_knn_candidates.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
@@ -162,6 +164,12 @@ def _ptr(t):
 def kernel_launches() -> int:
     """Kernels this library has launched in this process so far."""
     return int(load().ancka_kernel_launches())
+
+
+def set_symmetric_knn_min_rows(n_min: int) -> None:
+    """BF16 KNN lists of inputs with at least n_min rows come from the
+    symmetric contraction (1 = always; the default, 2**63 - 1, never)."""
+    load().ancka_set_symmetric_knn_min_rows(int(n_min))
 
 
 def default_params(**kw) -> Params:

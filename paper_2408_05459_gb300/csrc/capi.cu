@@ -572,6 +572,8 @@ ancka_status ancka_device_check(void) { return device_check(); }
 
 int64_t ancka_kernel_launches(void) { return g_launches.load(); }
 
+void ancka_set_symmetric_knn_min_rows(int64_t n_min) { knn_set_symmetric_min_rows(n_min); }
+
 ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t prec, int32_t* out_idx,
                        float* out_sim, ancka_info* info, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -213,6 +213,8 @@ ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n,
                                     float* cand_val, int32_t* cand_idx, int32_t* err, cudaStream_t s);
 bool knn_tc_available();
 int knn_tc_max_dp();
+// BF16 lists of n >= n_min rows come from the symmetric contraction
+void knn_set_symmetric_min_rows(int64_t n_min);
 // collect pass: for the n_a query rows listed in `rows`, every key j != row
 // with a BF16 score >= thr[r] is appended to buf[r * cap ..] (cnt[r] counts,
 // also past cap)

@@ -25,6 +25,7 @@
 // an error code, stops all roles, drains its own copies and MMAs (bounded),
 // frees TMEM and returns.
 #include <algorithm>
+#include <atomic>
 
 #include "tc_common.cuh"
 
@@ -198,10 +199,12 @@ __device__ __forceinline__ int key_rotation(int64_t qb, int n_tiles, int64_t wor
 // kCollect: collect mode (keys above a per-row threshold) instead of list
 // mode (two 16-entry lists per row); kE4M3: FP8 operands.  out_scale (list
 // mode, may be null) multiplies the scores written out.
+// key_stride > 1: only every key_stride-th key tile is swept (the sampled
+// pass of the symmetric contraction).
 template <bool kCollect, bool kE4M3>
 __global__ void __launch_bounds__(kThreads, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-         int64_t n_pad, int64_t qblocks, int kb_count, int nstages, float* __restrict__ cand_val,
+         int64_t n_pad, int64_t qblocks, int kb_count, int nstages, int key_stride, float* __restrict__ cand_val,
          int32_t* __restrict__ cand_idx, const float* __restrict__ out_scale, float* __restrict__ part_val,
          int32_t* __restrict__ part_idx, CollectArgs ca, int* __restrict__ err) {
   constexpr int kTK = kE4M3 ? 128 : 64;  // features per stage
@@ -211,7 +214,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   uint8_t* sB = sA + kb_count * kABytes;
   Bars* bars = reinterpret_cast<Bars*>(sB + nstages * kBBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tiles = (int)ceil_div(n_pad, kTN);
+  const int n_tiles = (int)ceil_div(ceil_div(n_pad, kTN), key_stride);
   const int64_t work = qblocks * n_tiles;
   const int64_t w_begin = range_begin(blockIdx.x, work, gridDim.x);
   const int64_t w_end = range_begin((int64_t)blockIdx.x + 1, work, gridDim.x);
@@ -275,7 +278,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             }
             pending[stage] = false;
             mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
-            const int kt = t + rot < n_tiles ? t + rot : t + rot - n_tiles;
+            const int kt = (t + rot < n_tiles ? t + rot : t + rot - n_tiles) * key_stride;
             tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, kt * kTN, &bars->full[stage]);
             pending[stage] = true;
             pend_par[stage] = phase;
@@ -388,7 +391,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           break;
         }
         tc_fence_after();
-        const int kt = t + rot < n_tiles ? t + rot : t + rot - n_tiles;
+        const int kt = (t + rot < n_tiles ? t + rot : t + rot - n_tiles) * key_stride;
         const int64_t jb = (int64_t)kt * kTN + h * kSliceN;
         const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * kSliceN);
 #pragma unroll 1
@@ -496,6 +499,359 @@ ancka_status tc_smem(int kb_count, int* nstages, size_t* smem) {
   return ANCKA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric contraction (the scores are symmetric: s_ij = s_ji).
+//
+// Only the pairs j > i are multiplied: the tiles (query block qb, key tile t)
+// with t >= qb / 2, in stream-K runs as above.  Every row-half (the keys of
+// one column half of the 256-key tiles, the halves of the two lists) has a
+// threshold L, the 16th-best score of that row-half over every 8th key tile
+// (the list kernel with key_stride 8): at least 16 keys of the full half
+// score >= L.  A tile's score s_ij is appended to row i's buffer when s_ij >=
+// L_i (row path, half = the key's column half) and to row j's buffer when
+// s_ij >= L_j (column path, half = (i mod 256) / 128 = qb & 1, the same for
+// the whole CTA); a per-32-key minimum of the column thresholds skips most
+// chunks.  k_sym_select then takes each row-half's 16 best, which are the
+// lists of a full sweep: a key left out scored below L or below the 16th
+// collected score.  A row whose buffer overflowed gets empty lists, which
+// the certificate sends to the exact fallback.
+// ---------------------------------------------------------------------------
+constexpr int kSymStride = 8;  // key tiles of the sampled pass
+
+// first work item of query block qb: sum over q < qb of (n_tiles - q / 2)
+__device__ __forceinline__ int64_t sym_start(int64_t qb, int64_t n_tiles) {
+  const int64_t a = qb >> 1;
+  const int64_t s = (qb & 1) ? a * a : a * (a - 1);
+  return qb * n_tiles - s;
+}
+
+// the query block holding work item w (binary search over qb)
+__device__ __forceinline__ int64_t sym_block(int64_t w, int64_t qblocks, int64_t n_tiles) {
+  int64_t lo = 0, hi = qblocks - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (sym_start(mid, n_tiles) <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct SymArgs {
+  const float* L;      // 2 x lstride thresholds (half-major); lstride = 256 x key tiles
+  const float* Lmin;   // 2 x (lstride / 32) minima over 32 consecutive rows
+  int32_t* cnt;        // n x 2 appended entries (also counts past cap)
+  float* bufv;         // (n x 2) x cap scores
+  int32_t* bufi;       // (n x 2) x cap keys
+  int cap;
+};
+
+__device__ __forceinline__ void sym_append(const SymArgs& sa, int64_t row, int half, float v, int32_t key) {
+  const int64_t slot = row * 2 + half;
+  const int pos = atomicAdd(&sa.cnt[slot], 1);
+  if (pos < sa.cap) {
+    sa.bufv[slot * sa.cap + pos] = v;
+    sa.bufi[slot * sa.cap + pos] = key;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_knn_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
+          int64_t n_pad, int64_t qblocks, int kb_count, int nstages, SymArgs sa, int* __restrict__ err) {
+  constexpr int kTK = 64;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + kb_count * kABytes;
+  Bars* bars = reinterpret_cast<Bars*>(sB + nstages * kBBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_tiles = ceil_div(n_pad, kTN);
+  const int64_t work = sym_start(qblocks, n_tiles);
+  const int64_t w_begin = range_begin(blockIdx.x, work, gridDim.x);
+  const int64_t w_end = range_begin((int64_t)blockIdx.x + 1, work, gridDim.x);
+  volatile int* abort = &bars->abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(&bars->full[s], 1);
+      mbar_init(&bars->empty[s], 1);
+    }
+    mbar_init(&bars->a_full, 1);
+    mbar_init(&bars->a_empty, 1);
+    mbar_init(&bars->tfull[0], 1);
+    mbar_init(&bars->tfull[1], 1);
+    mbar_init(&bars->tempty[0], kEpiWarps);
+    mbar_init(&bars->tempty[1], kEpiWarps);
+    mbar_init(&bars->drain, 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  // segment of a run: (qb, t0, t1) with t in [qb / 2, n_tiles)
+  auto segment = [&](int64_t w, int64_t& qb, int64_t& t0, int64_t& t1) {
+    qb = sym_block(w, qblocks, n_tiles);
+    t0 = (qb >> 1) + (w - sym_start(qb, n_tiles));
+    t1 = w_end - w < n_tiles - t0 ? t0 + (w_end - w) : n_tiles;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool pending[kMaxStages];
+      uint32_t pend_par[kMaxStages];
+      for (int s = 0; s < kMaxStages; ++s) pending[s] = false;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int seg = 0;
+      for (int64_t w = w_begin; w < w_end && ok; ++seg) {
+        int64_t qb, t0, t1;
+        segment(w, qb, t0, t1);
+        w += t1 - t0;
+        if (seg > 0 && !mbar_wait(&bars->a_empty, (uint32_t)((seg - 1) & 1), abort, err, 6)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&bars->a_full, (uint32_t)(kb_count * kABytes));
+        for (int kb = 0; kb < kb_count; ++kb)
+          tma_load_2d(smem_u32(sA + kb * kABytes), &tmA, kb * kTK, (int)(qb * kTM), &bars->a_full);
+        for (int64_t t = t0; t < t1 && ok; ++t) {
+          for (int kb = 0; kb < kb_count; ++kb) {
+            if (!mbar_wait(&bars->empty[stage], phase ^ 1, abort, err, 1)) {
+              ok = false;
+              break;
+            }
+            pending[stage] = false;
+            mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
+            tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, (int)(t * kTN), &bars->full[stage]);
+            pending[stage] = true;
+            pend_par[stage] = phase;
+            if (++stage == nstages) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        if (seg > 0) mbar_wait(&bars->a_full, (uint32_t)((seg - 1) & 1), nullptr, nullptr, 0);
+        for (int s = 0; s < nstages; ++s)
+          if (pending[s]) mbar_wait(&bars->full[s], pend_par[s], nullptr, nullptr, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool issued = false;
+      int64_t g = 0;
+      int seg = 0;
+      for (int64_t w = w_begin; w < w_end && ok; ++seg) {
+        int64_t qb, t0, t1;
+        segment(w, qb, t0, t1);
+        w += t1 - t0;
+        if (!mbar_wait(&bars->a_full, (uint32_t)(seg & 1), abort, err, 2)) {
+          ok = false;
+          break;
+        }
+        for (int64_t t = t0; t < t1; ++t, ++g) {
+          const int b = (int)(g & 1);
+          const uint32_t use = (uint32_t)(g >> 1);
+          if (!mbar_wait(&bars->tempty[b], (use & 1) ^ 1, abort, err, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(b * kTN);
+          for (int kb = 0; kb < kb_count; ++kb) {
+            if (!mbar_wait(&bars->full[stage], phase, abort, err, 4)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + kb * kABytes);
+            const uint32_t b0 = smem_u32(sB + stage * kBBytes);
+#pragma unroll
+            for (int kk = 0; kk < kMmaPerStage; ++kk)
+              umma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
+            issued = true;
+            umma_commit(&bars->empty[stage]);
+            if (++stage == nstages) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          if (!ok) break;
+          umma_commit(&bars->tfull[b]);
+        }
+        if (ok) umma_commit(&bars->a_empty);
+      }
+      if (!ok && issued) {
+        umma_commit(&bars->drain);
+        mbar_wait(&bars->drain, 0, nullptr, nullptr, 0);
+      }
+    }
+  } else {
+    const int ew = warp - 2;
+    const int q = warp & 3;
+    const int h = ew >> 2;  // column half of the tile = the row path's list half
+    const int r = q * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t w = w_begin; w < w_end && ok;) {
+      int64_t qb, t0, t1;
+      segment(w, qb, t0, t1);
+      w += t1 - t0;
+      const int64_t i = qb * kTM + r;
+      const int64_t lstride = n_tiles * kTN;
+      const float Lrow = i < n ? sa.L[(int64_t)h * lstride + i] : INFINITY;
+      const int hc = (int)(qb & 1);  // the column path's list half
+      const float* Lc = sa.L + (int64_t)hc * lstride;
+      const float* Lm = sa.Lmin + (int64_t)hc * (lstride / 32);
+      for (int64_t t = t0; t < t1; ++t, ++g) {
+        const int b = (int)(g & 1);
+        const uint32_t use = (uint32_t)(g >> 1);
+        const bool got = mbar_wait(&bars->tfull[b], use & 1, abort, err, 5);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int64_t jb = t * kTN + h * kSliceN;
+        const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * kSliceN);
+#pragma unroll 1
+        for (int c = 0; c < kSliceN / 32; ++c) {
+          uint32_t rv[32];
+          tmem_ld32_issue(tb + (uint32_t)(c * 32), rv);
+          tmem_wait();
+          pin(rv);
+          const int64_t j0 = jb + c * 32;
+          // keys j0 + e with i < j < n
+          const int64_t lo = i + 1 - j0, hi = n - j0;
+          const int e0 = lo < 0 ? 0 : (lo > 32 ? 32 : (int)lo);
+          const int e1 = hi < 0 ? 0 : (hi > 32 ? 32 : (int)hi);
+          uint32_t vm = 0;
+          if (e1 > e0) vm = (e1 - e0 == 32 ? 0xffffffffu : ((1u << (e1 - e0)) - 1u)) << e0;
+          float m[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) m[u] = fmaxf(__uint_as_float(rv[u]), __uint_as_float(rv[u + 16]));
+#pragma unroll
+          for (int u2 = 8; u2 >= 1; u2 >>= 1)
+#pragma unroll
+            for (int u = 0; u < u2; ++u) m[u] = fmaxf(m[u], m[u + u2]);
+          const float mx = vm ? m[0] : -INFINITY;
+          if (__any_sync(0xffffffffu, mx >= Lrow)) {  // row path
+            uint32_t pm = 0;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(rv[e]) >= Lrow ? 1u : 0u) << e;
+            pm &= vm;
+            while (pm) {
+              const int e = __ffs(pm) - 1;
+              pm &= pm - 1;
+              sym_append(sa, i, h, pick32(rv, e), (int32_t)(j0 + e));
+            }
+          }
+          const float lmin = Lm[j0 >> 5];
+          if (__any_sync(0xffffffffu, mx >= lmin)) {  // column path
+            float lc[32];
+#pragma unroll
+            for (int e4 = 0; e4 < 8; ++e4) {
+              const float4 v4 = *reinterpret_cast<const float4*>(Lc + j0 + 4 * e4);
+              lc[4 * e4] = v4.x;
+              lc[4 * e4 + 1] = v4.y;
+              lc[4 * e4 + 2] = v4.z;
+              lc[4 * e4 + 3] = v4.w;
+            }
+            uint32_t pm = 0;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(rv[e]) >= lc[e] ? 1u : 0u) << e;
+            pm &= vm;
+            while (pm) {
+              const int e = __ffs(pm) - 1;
+              pm &= pm - 1;
+              sym_append(sa, j0 + e, hc, pick32(rv, e), (int32_t)i);
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->tempty[b]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// thresholds from the sampled lists: L[h][i] = the 16th score of row i's
+// half-h list (sorted descending), -inf if that list is not full; rows >= n
+// +inf; Lmin[h][g] = min over rows 32g .. 32g + 31 (lstride a multiple of 256)
+__global__ void k_sym_thresholds(const float* __restrict__ cand_val, const int32_t* __restrict__ cand_idx,
+                                 int64_t n, int64_t lstride, float* __restrict__ L, float* __restrict__ Lmin) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= lstride) return;
+  const int64_t n_pad = lstride;
+  for (int h = 0; h < 2; ++h) {
+    float v = INFINITY;
+    if (i < n) {
+      const int64_t last = i * kCandC + h * kListC + (kListC - 1);
+      v = cand_idx[last] >= 0 ? cand_val[last] : -INFINITY;
+    }
+    L[(int64_t)h * n_pad + i] = v;
+    float mn = v;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+    if ((threadIdx.x & 31) == 0) Lmin[(int64_t)h * (n_pad / 32) + (i >> 5)] = mn;
+  }
+}
+
+// each row's two lists: the 16 best collected entries per half, sorted
+// descending; a row with an overflowing half gets two empty lists (sent to
+// the exact fallback by the certificate)
+__global__ void k_sym_select(const int32_t* __restrict__ cnt, const float* __restrict__ bufv,
+                             const int32_t* __restrict__ bufi, int cap, int64_t n, float* __restrict__ cand_val,
+                             int32_t* __restrict__ cand_idx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool over = cnt[i * 2] > cap || cnt[i * 2 + 1] > cap;
+  constexpr int C = kListC;
+  for (int h = 0; h < 2; ++h) {
+    float lv[C];
+    int32_t li[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      lv[c] = -INFINITY;
+      li[c] = -1;
+    }
+    if (!over) {
+      const int64_t slot = i * 2 + h;
+      const int c_n = cnt[slot];
+      for (int e = 0; e < c_n; ++e) {
+        const float v = bufv[slot * cap + e];
+        if (v > lv[C - 1]) sorted_insert<C>(lv, li, v, bufi[slot * cap + e]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      cand_val[i * kCandC + h * C + c] = lv[c];
+      cand_idx[i * kCandC + h * C + c] = li[c];
+    }
+  }
+}
+
 __global__ void k_gather_rows(const uint8_t* __restrict__ x, int row_bytes, const int32_t* __restrict__ rows,
                               int64_t n_a, int64_t n_a_pad, uint8_t* __restrict__ out) {
   const int64_t r = blockIdx.x;
@@ -510,7 +866,7 @@ __global__ void k_gather_rows(const uint8_t* __restrict__ x, int row_bytes, cons
 template <bool kCollect, bool kE4M3>
 ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, int64_t n_pad,
                        int64_t n_rows, int kb_count, float* cand_val, int32_t* cand_idx, const float* out_scale,
-                       const CollectArgs& ca, int32_t* err, cudaStream_t s) {
+                       const CollectArgs& ca, int32_t* err, cudaStream_t s, int key_stride = 1) {
   int nstages;
   size_t smem;
   ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
@@ -518,7 +874,7 @@ ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& 
   ANCKA_CUDA(cudaGetDevice(&dev));
   ANCKA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t qblocks = ceil_div(n_rows, kTM);
-  const int n_tiles = (int)ceil_div(n_pad, kTN);
+  const int n_tiles = (int)ceil_div(ceil_div(n_pad, kTN), key_stride);
   const int64_t work = qblocks * n_tiles;
   const int64_t ctas = std::min<int64_t>(sms, work);
   float* part_val = nullptr;
@@ -529,14 +885,67 @@ ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& 
   }
   ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<kCollect, kE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_knn_tc<kCollect, kE4M3><<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, n_pad, qblocks, kb_count, nstages,
-                                                                   cand_val, cand_idx, out_scale, part_val,
-                                                                   part_idx, ca, err);
+                                                                   key_stride, cand_val, cand_idx, out_scale,
+                                                                   part_val, part_idx, ca, err);
   ANCKA_LAUNCHED();
   if (!kCollect) {
     k_merge_lists<<<(unsigned)qblocks, kTM, 0, s>>>(n_tiles, work, ctas, part_val, part_idx, ca.a_rows, n_rows,
                                                     cand_val, cand_idx);
     ANCKA_LAUNCHED();
   }
+  return ANCKA_OK;
+}
+
+int64_t sym_start_host(int64_t qb, int64_t n_tiles) {
+  const int64_t a = qb >> 1;
+  return qb * n_tiles - ((qb & 1) ? a * a : a * (a - 1));
+}
+
+std::atomic<int64_t> g_sym_min_rows{INT64_MAX};  // off by default: slower than the full sweep so far
+
+// BF16 lists by the symmetric contraction (sampled thresholds, the j > i
+// tiles with both paths, selection)
+ancka_status knn_candidates_bf16_sym(Workspace& ws, const PrepOut& pr, int64_t n, const CUtensorMap& ta,
+                                     const CUtensorMap& tb, int kb_count, float* cand_val, int32_t* cand_idx,
+                                     int32_t* err, cudaStream_t s) {
+  // 1. sampled lists: every kSymStride-th key tile
+  float* sv;
+  int32_t* si;
+  ANCKA_TRY(ws.alloc(&sv, (size_t)n * kCandC));
+  ANCKA_TRY(ws.alloc(&si, (size_t)n * kCandC));
+  CollectArgs none{};
+  const ancka_status st = launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n, kb_count, sv, si, nullptr, none, err,
+                                                  s, kSymStride);
+  if (st != ANCKA_OK) return st;
+  // 2. thresholds
+  const int64_t n_tiles = ceil_div(pr.n_pad, kTN);
+  const int64_t lstride = n_tiles * kTN;
+  float *L, *Lmin;
+  ANCKA_TRY(ws.alloc(&L, (size_t)2 * lstride));
+  ANCKA_TRY(ws.alloc(&Lmin, (size_t)2 * (lstride / 32)));
+  k_sym_thresholds<<<(unsigned)(lstride / 256), 256, 0, s>>>(sv, si, n, lstride, L, Lmin);
+  ANCKA_LAUNCHED();
+  // 3. the j > i tiles, both paths
+  constexpr int kCap = 320;  // ~16 x kSymStride entries expected per row-half
+  SymArgs sa{L, Lmin, nullptr, nullptr, nullptr, kCap};
+  ANCKA_TRY(ws.zeros(&sa.cnt, (size_t)n * 2));
+  ANCKA_TRY(ws.alloc(&sa.bufv, (size_t)n * 2 * kCap));
+  ANCKA_TRY(ws.alloc(&sa.bufi, (size_t)n * 2 * kCap));
+  int nstages;
+  size_t smem;
+  ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
+  int sms = 152, dev = 0;
+  ANCKA_CUDA(cudaGetDevice(&dev));
+  ANCKA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t qblocks = ceil_div(n, kTM);
+  const int64_t work = sym_start_host(qblocks, n_tiles);
+  const int64_t ctas = std::min<int64_t>(sms, work);
+  ANCKA_CUDA(cudaFuncSetAttribute(k_knn_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_knn_sym<<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, pr.n_pad, qblocks, kb_count, nstages, sa, err);
+  ANCKA_LAUNCHED();
+  // 4. the two lists of every row
+  k_sym_select<<<(unsigned)ceil_div(n, 128), 128, 0, s>>>(sa.cnt, sa.bufv, sa.bufi, kCap, n, cand_val, cand_idx);
+  ANCKA_LAUNCHED();
   return ANCKA_OK;
 }
 
@@ -556,9 +965,13 @@ ancka_status knn_candidates_bf16(Workspace& ws, const PrepOut& pr, int64_t n, fl
   CUtensorMap ta, tb;
   ANCKA_TRY(make_map(&ta, pr.xb, pr.dp, pr.n_pad, kTM, 2));
   ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
+  if (n >= g_sym_min_rows.load(std::memory_order_relaxed))
+    return knn_candidates_bf16_sym(ws, pr, n, ta, tb, kb_count, cand_val, cand_idx, err, s);
   CollectArgs none{};
   return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n, kb_count, cand_val, cand_idx, nullptr, none, err, s);
 }
+
+void knn_set_symmetric_min_rows(int64_t n_min) { g_sym_min_rows.store(n_min, std::memory_order_relaxed); }
 
 ancka_status knn_candidates_fp8(Workspace& ws, const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
                                 int32_t* err, cudaStream_t s) {

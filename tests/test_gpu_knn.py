@@ -185,3 +185,57 @@ def test_candidate_error_model(ak, prec, n, d):
                 assert not others.any(), f"row {i} list {h}: list not full but keys left out"
     print(f"{prec}: max |score - q.q| / (acc |q||q|) = {worst:.3g} (acc = {acc:.3g})")
     assert worst <= 1.0
+
+
+class _SymmetricMinRows:
+    """Sets the symmetric-contraction crossover for one block, then restores
+    the default."""
+
+    def __init__(self, ak, n_min):
+        self.ak, self.n_min = ak, n_min
+
+    def __enter__(self):
+        self.ak.set_symmetric_knn_min_rows(self.n_min)
+
+    def __exit__(self, *exc):
+        self.ak.set_symmetric_knn_min_rows(2**63 - 1)
+
+
+@pytest.mark.parametrize("n,d", [(70000, 64), (9000, 96)])
+def test_symmetric_contraction_lists(ak, n, d):
+    """The symmetric contraction (pairs j > i only, thresholds from every 8th
+    key tile, scores pushed to both rows) leaves the same two 16-entry lists
+    per row as the full sweep: s_ij and s_ji sum the same products in the same
+    order, so the scores agree bit for bit; the keys agree except where equal
+    scores sit at the 16th place."""
+    rng = np.random.default_rng(n + d)
+    labels = rng.integers(0, 8, n)
+    X = torch.as_tensor(synth.gaussian_mixture(rng, labels, 8, d, 1.0), device="cuda")
+    with _SymmetricMinRows(ak, 2**63 - 1):
+        cv0, ci0, _, _, _ = ak.knn_candidates(X, "bf16")
+    with _SymmetricMinRows(ak, 1):
+        cv1, ci1, _, _, _ = ak.knn_candidates(X, "bf16")
+    torch.cuda.synchronize()
+    cv0, ci0, cv1, ci1 = [t.cpu().numpy() for t in (cv0, ci0, cv1, ci1)]
+    same_keys = 0
+    for h in range(2):
+        a, b = cv0[:, 16 * h:16 * h + 16], cv1[:, 16 * h:16 * h + 16]
+        assert np.array_equal(np.sort(a, axis=1), np.sort(b, axis=1)), f"half {h}: scores differ"
+        ka, kb = np.sort(ci0[:, 16 * h:16 * h + 16], axis=1), np.sort(ci1[:, 16 * h:16 * h + 16], axis=1)
+        same_keys += int(np.all(ka == kb, axis=1).sum())
+        assert np.all((ci1[:, 16 * h:16 * h + 16] // 128) % 2 == h), "key in the wrong half"
+    assert same_keys >= 2 * n - n // 1000, same_keys
+
+
+@pytest.mark.parametrize("n,d,K", [(2000, 128, 10), (300, 5, 4), (777, 130, 7), (20000, 48, 10)])
+def test_symmetric_contraction_knn_exact(ak, n, d, K):
+    """Exact KNN through the symmetric contraction at small and ragged sizes
+    (forced below its default crossover)."""
+    rng = np.random.default_rng(n + 3 * d + K)
+    labels = rng.integers(0, 5, n)
+    X = synth.gaussian_mixture(rng, labels, 5, d, 1.5)
+    with _SymmetricMinRows(ak, 1):
+        idx, sim, info = _run(ak, X, K, "bf16")
+    rows = np.arange(n) if n <= 4000 else np.random.default_rng(5).choice(n, 512, replace=False)
+    c = compare_knn(X, K, rows, idx, sim)
+    assert c["exact_rows"] + c["near_tie_rows"] == rows.size
