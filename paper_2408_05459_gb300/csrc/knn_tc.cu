@@ -536,21 +536,27 @@ __device__ __forceinline__ int64_t sym_block(int64_t w, int64_t qblocks, int64_t
   return lo;
 }
 
+// The contraction stages (row-half, key, score) entries: each epilogue warp
+// reserves blocks of kSymBlock entries with one atomic and fills them without
+// waiting on atomics (unused tails are marked -1); k_sym_scatter then appends
+// the entries to per-row-half buffers.
+constexpr int kSymBlock = 256;
+
 struct SymArgs {
   const float* L;      // 2 x lstride thresholds (half-major); lstride = 256 x key tiles
   const float* Lmin;   // 2 x (lstride / 32) minima over 32 consecutive rows
-  int32_t* cnt;        // n x 2 appended entries (also counts past cap)
-  float* bufv;         // (n x 2) x cap scores
-  int32_t* bufi;       // (n x 2) x cap keys
-  int cap;
+  int32_t* st_slot;    // staging: row * 2 + half, -1 unused
+  int32_t* st_key;
+  float* st_val;
+  unsigned long long* st_count;  // entries reserved (may exceed st_cap: overflow)
+  int64_t st_cap;
 };
 
-__device__ __forceinline__ void sym_append(const SymArgs& sa, int64_t row, int half, float v, int32_t key) {
-  const int64_t slot = row * 2 + half;
-  const int pos = atomicAdd(&sa.cnt[slot], 1);
-  if (pos < sa.cap) {
-    sa.bufv[slot * sa.cap + pos] = v;
-    sa.bufi[slot * sa.cap + pos] = key;
+__device__ __forceinline__ void sym_stage(const SymArgs& sa, int64_t pos, int32_t slot, int32_t key, float v) {
+  if (pos < sa.st_cap) {
+    sa.st_slot[pos] = slot;
+    sa.st_key[pos] = key;
+    sa.st_val[pos] = v;
   }
 }
 
@@ -707,6 +713,8 @@ k_knn_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     int64_t g = 0;
     bool ok = true;
+    int64_t blk_base = 0;  // the warp's staging block (uniform over the warp)
+    int blk_cap = 0, blk_used = 0;
     for (int64_t w = w_begin; w < w_end && ok;) {
       int64_t qb, t0, t1;
       segment(w, qb, t0, t1);
@@ -720,13 +728,17 @@ k_knn_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       for (int64_t t = t0; t < t1; ++t, ++g) {
         const int b = (int)(g & 1);
         const uint32_t use = (uint32_t)(g >> 1);
+        const int64_t jb = t * kTN + h * kSliceN;
+        // the tile's column thresholds (lane: keys jb + 4 lane .. + 3) and
+        // per-chunk minima, loaded before the wait so that their latency hides
+        const float4 lcol = *reinterpret_cast<const float4*>(Lc + jb + 4 * lane);
+        const float4 lmin4 = *reinterpret_cast<const float4*>(Lm + (jb >> 5));
         const bool got = mbar_wait(&bars->tfull[b], use & 1, abort, err, 5);
         if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const int64_t jb = t * kTN + h * kSliceN;
         const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * kSliceN);
 #pragma unroll 1
         for (int c = 0; c < kSliceN / 32; ++c) {
@@ -749,37 +761,59 @@ k_knn_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
             for (int u = 0; u < u2; ++u) m[u] = fmaxf(m[u], m[u + u2]);
           const float mx = vm ? m[0] : -INFINITY;
+          uint32_t pr = 0, pc = 0;
           if (__any_sync(0xffffffffu, mx >= Lrow)) {  // row path
-            uint32_t pm = 0;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(rv[e]) >= Lrow ? 1u : 0u) << e;
-            pm &= vm;
-            while (pm) {
-              const int e = __ffs(pm) - 1;
-              pm &= pm - 1;
-              sym_append(sa, i, h, pick32(rv, e), (int32_t)(j0 + e));
-            }
+            for (int e = 0; e < 32; ++e) pr |= (__uint_as_float(rv[e]) >= Lrow ? 1u : 0u) << e;
+            pr &= vm;
           }
-          const float lmin = Lm[j0 >> 5];
+          const float lmin = c == 0 ? lmin4.x : c == 1 ? lmin4.y : c == 2 ? lmin4.z : lmin4.w;
           if (__any_sync(0xffffffffu, mx >= lmin)) {  // column path
-            float lc[32];
 #pragma unroll
-            for (int e4 = 0; e4 < 8; ++e4) {
-              const float4 v4 = *reinterpret_cast<const float4*>(Lc + j0 + 4 * e4);
-              lc[4 * e4] = v4.x;
-              lc[4 * e4 + 1] = v4.y;
-              lc[4 * e4 + 2] = v4.z;
-              lc[4 * e4 + 3] = v4.w;
+            for (int e4 = 0; e4 < 8; ++e4) {  // chunk c's thresholds sit in lanes 8c .. 8c + 7
+              const int src = c * 8 + e4;
+              const float t0v = __shfl_sync(0xffffffffu, lcol.x, src);
+              const float t1v = __shfl_sync(0xffffffffu, lcol.y, src);
+              const float t2v = __shfl_sync(0xffffffffu, lcol.z, src);
+              const float t3v = __shfl_sync(0xffffffffu, lcol.w, src);
+              pc |= (__uint_as_float(rv[4 * e4]) >= t0v ? 1u : 0u) << (4 * e4);
+              pc |= (__uint_as_float(rv[4 * e4 + 1]) >= t1v ? 1u : 0u) << (4 * e4 + 1);
+              pc |= (__uint_as_float(rv[4 * e4 + 2]) >= t2v ? 1u : 0u) << (4 * e4 + 2);
+              pc |= (__uint_as_float(rv[4 * e4 + 3]) >= t3v ? 1u : 0u) << (4 * e4 + 3);
             }
-            uint32_t pm = 0;
+            pc &= vm;
+          }
+          // the warp's entries: one exclusive prefix, one block reservation when needed
+          const int cl = __popc(pr) + __popc(pc);
+          int incl = cl;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) pm |= (__uint_as_float(rv[e]) >= lc[e] ? 1u : 0u) << e;
-            pm &= vm;
-            while (pm) {
-              const int e = __ffs(pm) - 1;
-              pm &= pm - 1;
-              sym_append(sa, j0 + e, hc, pick32(rv, e), (int32_t)i);
+          for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+          }
+          const int ctot = __shfl_sync(0xffffffffu, incl, 31);
+          if (ctot > 0) {
+            if (blk_used + ctot > blk_cap) {
+              for (int e = blk_used + lane; e < blk_cap; e += 32) sym_stage(sa, blk_base + e, -1, -1, 0.f);
+              const int nblk = (ctot + kSymBlock - 1) / kSymBlock;
+              unsigned long long b = 0;
+              if (lane == 0) b = atomicAdd(sa.st_count, (unsigned long long)nblk * kSymBlock);
+              blk_base = (int64_t)__shfl_sync(0xffffffffu, b, 0);
+              blk_cap = nblk * kSymBlock;
+              blk_used = 0;
             }
+            int64_t pos = blk_base + blk_used + (incl - cl);
+            while (pr) {
+              const int e = __ffs(pr) - 1;
+              pr &= pr - 1;
+              sym_stage(sa, pos++, (int32_t)(i * 2 + h), (int32_t)(j0 + e), pick32(rv, e));
+            }
+            while (pc) {
+              const int e = __ffs(pc) - 1;
+              pc &= pc - 1;
+              sym_stage(sa, pos++, (int32_t)((j0 + e) * 2 + hc), (int32_t)i, pick32(rv, e));
+            }
+            blk_used += ctot;
           }
         }
         tc_fence_before();
@@ -787,12 +821,37 @@ k_knn_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (lane == 0) mbar_arrive(&bars->tempty[b]);
       }
     }
+    for (int e = blk_used + lane; e < blk_cap; e += 32) sym_stage(sa, blk_base + e, -1, -1, 0.f);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// the staged entries into per-row-half buffers (cnt counts past cap); a
+// staging overflow marks every row (overflow flag), so that all go to the
+// exact fallback
+__global__ void k_sym_scatter(const int32_t* __restrict__ st_slot, const int32_t* __restrict__ st_key,
+                              const float* __restrict__ st_val, const unsigned long long* __restrict__ st_count,
+                              int64_t st_cap, int32_t* __restrict__ cnt, float* __restrict__ bufv,
+                              int32_t* __restrict__ bufi, int cap, int32_t* __restrict__ overflow) {
+  const unsigned long long tot = *st_count;
+  if (tot > (unsigned long long)st_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *overflow = 1;
+    return;
+  }
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)tot;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t slot = st_slot[q];
+    if (slot < 0) continue;
+    const int pos = atomicAdd(&cnt[slot], 1);
+    if (pos < cap) {
+      bufv[(int64_t)slot * cap + pos] = st_val[q];
+      bufi[(int64_t)slot * cap + pos] = st_key[q];
+    }
   }
 }
 
@@ -822,11 +881,12 @@ __global__ void k_sym_thresholds(const float* __restrict__ cand_val, const int32
 // descending; a row with an overflowing half gets two empty lists (sent to
 // the exact fallback by the certificate)
 __global__ void k_sym_select(const int32_t* __restrict__ cnt, const float* __restrict__ bufv,
-                             const int32_t* __restrict__ bufi, int cap, int64_t n, float* __restrict__ cand_val,
+                             const int32_t* __restrict__ bufi, int cap, int64_t n,
+                             const int32_t* __restrict__ overflow, float* __restrict__ cand_val,
                              int32_t* __restrict__ cand_idx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const bool over = cnt[i * 2] > cap || cnt[i * 2 + 1] > cap;
+  const bool over = *overflow || cnt[i * 2] > cap || cnt[i * 2 + 1] > cap;
   constexpr int C = kListC;
   for (int h = 0; h < 2; ++h) {
     float lv[C];
@@ -901,7 +961,11 @@ int64_t sym_start_host(int64_t qb, int64_t n_tiles) {
   return qb * n_tiles - ((qb & 1) ? a * a : a * (a - 1));
 }
 
-std::atomic<int64_t> g_sym_min_rows{INT64_MAX};  // off by default: slower than the full sweep so far
+// off by default: on the measured workloads the symmetric form is slower than
+// the full sweep (its fixed thresholds admit ~8x more candidates than the
+// full sweep's running ones, so its epilogue does about twice the work per
+// tile over half the tiles)
+std::atomic<int64_t> g_sym_min_rows{INT64_MAX};
 
 // BF16 lists by the symmetric contraction (sampled thresholds, the j > i
 // tiles with both paths, selection)
@@ -927,10 +991,18 @@ ancka_status knn_candidates_bf16_sym(Workspace& ws, const PrepOut& pr, int64_t n
   ANCKA_LAUNCHED();
   // 3. the j > i tiles, both paths
   constexpr int kCap = 320;  // ~16 x kSymStride entries expected per row-half
-  SymArgs sa{L, Lmin, nullptr, nullptr, nullptr, kCap};
-  ANCKA_TRY(ws.zeros(&sa.cnt, (size_t)n * 2));
-  ANCKA_TRY(ws.alloc(&sa.bufv, (size_t)n * 2 * kCap));
-  ANCKA_TRY(ws.alloc(&sa.bufi, (size_t)n * 2 * kCap));
+  SymArgs sa{L, Lmin, nullptr, nullptr, nullptr, nullptr, 0};
+  sa.st_cap = n * 2 * 16 * kSymStride * 5 / 2 + (int64_t)8 * kThreads / 32 * kSymBlock * 152;
+  ANCKA_TRY(ws.alloc(&sa.st_slot, (size_t)sa.st_cap));
+  ANCKA_TRY(ws.alloc(&sa.st_key, (size_t)sa.st_cap));
+  ANCKA_TRY(ws.alloc(&sa.st_val, (size_t)sa.st_cap));
+  ANCKA_TRY(ws.zeros(&sa.st_count, 1));
+  int32_t *cnt, *bufi, *overflow;
+  float* bufv;
+  ANCKA_TRY(ws.zeros(&cnt, (size_t)n * 2));
+  ANCKA_TRY(ws.alloc(&bufv, (size_t)n * 2 * kCap));
+  ANCKA_TRY(ws.alloc(&bufi, (size_t)n * 2 * kCap));
+  ANCKA_TRY(ws.zeros(&overflow, 1));
   int nstages;
   size_t smem;
   ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
@@ -943,8 +1015,11 @@ ancka_status knn_candidates_bf16_sym(Workspace& ws, const PrepOut& pr, int64_t n
   ANCKA_CUDA(cudaFuncSetAttribute(k_knn_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_knn_sym<<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, pr.n_pad, qblocks, kb_count, nstages, sa, err);
   ANCKA_LAUNCHED();
-  // 4. the two lists of every row
-  k_sym_select<<<(unsigned)ceil_div(n, 128), 128, 0, s>>>(sa.cnt, sa.bufv, sa.bufi, kCap, n, cand_val, cand_idx);
+  // 4. staged entries into the row-half buffers, then the two lists of every row
+  k_sym_scatter<<<(unsigned)(4 * sms), 256, 0, s>>>(sa.st_slot, sa.st_key, sa.st_val, sa.st_count, sa.st_cap, cnt,
+                                                   bufv, bufi, kCap, overflow);
+  ANCKA_LAUNCHED();
+  k_sym_select<<<(unsigned)ceil_div(n, 128), 128, 0, s>>>(cnt, bufv, bufi, kCap, n, overflow, cand_val, cand_idx);
   ANCKA_LAUNCHED();
   return ANCKA_OK;
 }
