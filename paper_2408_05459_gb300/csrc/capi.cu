@@ -357,7 +357,7 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     float* sim = (out && out->knn_sim) ? out->knn_sim : nullptr;
     int32_t* zero_row = nullptr;
     int64_t ncand = 0, nfb = 0, nex = 0;
-    int32_t* bad;
+    int32_t* bad = nullptr;
     st = ws.zeros(&bad, 1);
     Walk w;
     if (st == ANCKA_OK) {  // the topology part of the walk needs no attributes
