@@ -22,20 +22,32 @@ std::atomic<int64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+int device_slot() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  return dev < 0 ? 0 : (dev < kMaxDevices ? dev : kMaxDevices - 1);
+}
+
 namespace {
+// events belong to the device they were created on: one pool per device
 struct EventPool {
-  std::vector<cudaEvent_t> free;
+  std::vector<cudaEvent_t> free[kMaxDevices];
   ~EventPool() {
-    for (cudaEvent_t e : free) cudaEventDestroy(e);
+    for (auto& v : free)
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
   }
 };
 thread_local EventPool g_event_pool;
 }  // namespace
 
 cudaEvent_t pooled_event() {
-  if (!g_event_pool.free.empty()) {
-    cudaEvent_t e = g_event_pool.free.back();
-    g_event_pool.free.pop_back();
+  auto& v = g_event_pool.free[device_slot()];
+  if (!v.empty()) {
+    cudaEvent_t e = v.back();
+    v.pop_back();
     return e;
   }
   cudaEvent_t e = nullptr;
@@ -43,8 +55,10 @@ cudaEvent_t pooled_event() {
   return e;
 }
 
+// the event goes back to the pool of the current device, which is the
+// device it was taken on (a call does not switch devices)
 void release_event(cudaEvent_t e) {
-  if (e) g_event_pool.free.push_back(e);
+  if (e) g_event_pool.free[device_slot()].push_back(e);
 }
 
 void set_error(const char* fmt, ...) {
@@ -369,7 +383,8 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     // blocks take the room the contraction leaves (and, for host inputs, the
     // time X is still being copied); the call's stream waits for it before
     // the iteration, and on every exit before the workspace is released
-    static thread_local cudaStream_t is = nullptr;
+    static thread_local cudaStream_t init_streams[kMaxDevices] = {};
+    cudaStream_t& is = init_streams[device_slot()];
     if (!is) ANCKA_CUDA(cudaStreamCreateWithFlags(&is, cudaStreamNonBlocking));
     struct InitJoin {
       cudaStream_t s;
@@ -691,7 +706,8 @@ ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int3
   ancka_status st = ANCKA_OK;
   // X (the large copy) goes on a second stream so that the topology build
   // overlaps it; the call's stream waits for it before the KNN
-  static thread_local cudaStream_t xs = nullptr;
+  static thread_local cudaStream_t copy_streams[kMaxDevices] = {};
+  cudaStream_t& xs = copy_streams[device_slot()];
   if (!xs) ANCKA_CUDA(cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking));
   // on every exit: s waits for the copy before the workspace frees dX on s,
   // and the events go back to the pool

@@ -27,6 +27,10 @@ void count_launch();
 // instrumented call creates no events once the pool is warm
 cudaEvent_t pooled_event();
 void release_event(cudaEvent_t e);
+// the current device's ordinal, clamped to [0, kMaxDevices) (the per-device
+// caches: streams, pooled events, kernel attributes)
+constexpr int kMaxDevices = 64;
+int device_slot();
 #define ANCKA_LAUNCHED()            \
   do {                              \
     ::ancka::count_launch();        \

@@ -1827,7 +1827,8 @@ ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64
   k_disc_init<<<1, 32, 0, s>>>(st.bar, st.err);
   ANCKA_LAUNCHED();
   const size_t smem = disc_smem_bytes();
-  static int max_grid = 0;
+  static int max_grids[kMaxDevices] = {};
+  int& max_grid = max_grids[device_slot()];
   if (max_grid == 0) {
     ANCKA_CUDA(cudaFuncSetAttribute(k_discretize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, occ = 0;
@@ -1861,10 +1862,10 @@ ancka_status cholqr2(Workspace& ws, const Ctx& c, float* Z, float* Q, int w, flo
   const int tld = 4 * ((w + 3) / 4);
   const size_t chol_bytes = (size_t)(3 * w * w + 1) * sizeof(double);
   const size_t fused_bytes = (size_t)(tld * tld + kGramRows * kGramLd) * sizeof(float);
-  static bool configured = false;
-  if (!configured) {
+  static bool configured[kMaxDevices] = {};
+  if (!configured[device_slot()]) {
     ANCKA_CUDA(cudaFuncSetAttribute(k_gram_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (3 * 65 * 65 + 1) * 8));
-    configured = true;
+    configured[device_slot()] = true;
   }
   float* R1 = Rinv;
   float* R2 = Rinv + (size_t)w * w;

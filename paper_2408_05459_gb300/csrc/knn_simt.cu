@@ -131,10 +131,10 @@ k_knn_simt(const float* __restrict__ Xu, int64_t n, int64_t n_pad, int dp,
 ancka_status knn_candidates_fp32(const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
                                  cudaStream_t s) {
   const size_t smem = (size_t)kBM * kSPad * sizeof(float);
-  static bool configured = false;
-  if (!configured) {
+  static bool configured[kMaxDevices] = {};
+  if (!configured[device_slot()]) {
     ANCKA_CUDA(cudaFuncSetAttribute(k_knn_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = true;
+    configured[device_slot()] = true;
   }
   dim3 grid((unsigned)(pr.n_pad / kBM));
   k_knn_simt<<<grid, kThreads, smem, s>>>(pr.xu32, n, pr.n_pad, pr.dp, cand_val, cand_idx);
