@@ -136,9 +136,9 @@ __device__ __forceinline__ void cos_ff(float s, float c, float2 ri, float2 rj, f
   h = h + 0.f;
 }
 
-// Dot2 dot products of row i with up to four rows j[u] (j[u] < 0: skipped)
-// with one warp: the loads of all four rows are issued before the Dot2
-// steps, and each sees the same per-lane order as dot2_rows.
+// Per-lane Dot2 partials of row i with up to four rows j[u] (j[u] < 0:
+// skipped) for dot2_reduce4: the loads of all four rows are issued before the
+// Dot2 steps, and each sees the same per-lane order as dot2_rows.
 __device__ __forceinline__ void dot2_rows4(const float* __restrict__ X, const float* __restrict__ xi, int d,
                                            const int32_t (&j)[4], float (&s)[4], float (&c)[4]) {
   const int lane = threadIdx.x & 31;
@@ -149,27 +149,142 @@ __device__ __forceinline__ void dot2_rows4(const float* __restrict__ X, const fl
     s[u] = 0.f;
     c[u] = 0.f;
   }
-  for (int t0 = lane; t0 < d; t0 += 32 * 8) {
-    float a[8], b[4][8];
+  for (int t0 = lane; t0 < d; t0 += 32 * 4) {
+    float a[4], b[4][4];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 4; ++v) {
       const int t = t0 + 32 * v;
       a[v] = t < d ? xi[t] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 8; ++v) {
+      for (int v = 0; v < 4; ++v) {
         const int t = t0 + 32 * v;
         b[u][v] = (t < d && j[u] >= 0) ? xj[u][t] : 0.f;
       }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 8; ++v) dot2_step(s[u], c[u], a[v], b[u][v]);
+      for (int v = 0; v < 4; ++v) dot2_step(s[u], c[u], a[v], b[u][v]);
+  }
+}
+
+// (s, c) += (s2, c2) with the lower lane's partial first, as in
+// dot2_warp_reduce (`upper`: this lane has the level's bit set)
+__device__ __forceinline__ void dot2_merge_lanes(float& s, float& c, float s2, float c2, bool upper) {
+  if (upper) {
+    const float ts = s, tc = c;
+    s = s2;
+    c = c2;
+    s2 = ts;
+    c2 = tc;
+  }
+  dot2_merge(s, c, s2, c2);
+}
+
+// The butterfly of dot2_warp_reduce applied to four partials at once, each
+// of the first two levels keeping half of them (a reduce-scatter): after it
+// lane L holds the full sum of partial 2*bit4(L) + bit3(L), with every merge
+// taking the same operands in the same order as the one-partial butterfly,
+// so the bits are the same.  14 shuffles instead of 40.
+__device__ __forceinline__ void dot2_reduce4(const float (&s)[4], const float (&c)[4], float& rs, float& rc) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  // level 16: keep {0,1} (bit clear) or {2,3}; send the other pair
+  float ks0 = h16 ? s[2] : s[0], kc0 = h16 ? c[2] : c[0];
+  float ks1 = h16 ? s[3] : s[1], kc1 = h16 ? c[3] : c[1];
+  {
+    const float o0 = __shfl_xor_sync(0xffffffffu, h16 ? s[0] : s[2], 16);
+    const float p0 = __shfl_xor_sync(0xffffffffu, h16 ? c[0] : c[2], 16);
+    const float o1 = __shfl_xor_sync(0xffffffffu, h16 ? s[1] : s[3], 16);
+    const float p1 = __shfl_xor_sync(0xffffffffu, h16 ? c[1] : c[3], 16);
+    dot2_merge_lanes(ks0, kc0, o0, p0, h16);
+    dot2_merge_lanes(ks1, kc1, o1, p1, h16);
+  }
+  // level 8: keep the first (bit clear) or second of the pair
+  rs = h8 ? ks1 : ks0;
+  rc = h8 ? kc1 : kc0;
+  {
+    const float o = __shfl_xor_sync(0xffffffffu, h8 ? ks0 : ks1, 8);
+    const float p = __shfl_xor_sync(0xffffffffu, h8 ? kc0 : kc1, 8);
+    dot2_merge_lanes(rs, rc, o, p, h8);
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) dot2_warp_reduce(s[u], c[u]);
+  for (int off = 4; off >= 1; off >>= 1) {
+    const float o = __shfl_xor_sync(0xffffffffu, rs, off);
+    const float p = __shfl_xor_sync(0xffffffffu, rc, off);
+    dot2_merge_lanes(rs, rc, o, p, (lane & off) != 0);
+  }
+}
+
+// the lane of the same octet position that holds partial u after dot2_reduce4
+__device__ __forceinline__ int dot2_reduce4_src(int u, int lane) { return ((u >> 1) << 4) | ((u & 1) << 3) | (lane & 7); }
+
+// Sparse row i: each lane keeps the positions t of its strided share
+// (t = lane + 32m) where x_i[t] != 0, in increasing order.  A zero x_i[t]
+// makes the Dot2 step (s, c) += x_i[t] x_j[t] an exact no-op (for finite
+// x_j[t]), so stepping over only these positions gives the dense loop's
+// values; only x_j at these positions is read.
+constexpr int kSpLane = 4;  // positions kept per lane; a row with more uses the dense loop
+struct SparseRow {
+  int t[kSpLane];
+  float a[kSpLane];
+  int cnt;   // this lane's nonzeros (may exceed kSpLane)
+  int cmax;  // the largest count over the warp
+};
+
+__device__ __forceinline__ void sparse_row(const float* __restrict__ xi, int d, SparseRow& r) {
+  const int lane = threadIdx.x & 31;
+  r.cnt = 0;
+#pragma unroll
+  for (int q = 0; q < kSpLane; ++q) {
+    r.t[q] = 0;
+    r.a[q] = 0.f;
+  }
+  for (int t0 = lane; t0 < d; t0 += 32 * 8) {
+    float x[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int t = t0 + 32 * v;
+      x[v] = t < d ? xi[t] : 0.f;
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      if (x[v] != 0.f) {
+#pragma unroll
+        for (int q = 0; q < kSpLane; ++q)
+          if (r.cnt == q) {
+            r.t[q] = t0 + 32 * v;
+            r.a[q] = x[v];
+          }
+        ++r.cnt;
+      }
+    }
+  }
+  r.cmax = __reduce_max_sync(0xffffffffu, (unsigned)r.cnt);
+}
+
+// Dot2 partials of row i (sparse form, r.cmax <= kSpLane) with up to four
+// rows j[u] (j[u] < 0: skipped); the gathers of all four are issued first
+__device__ __forceinline__ void dot2_sparse4(const float* __restrict__ X, int d, const SparseRow& r,
+                                             const int32_t (&j)[4], float (&s)[4], float (&c)[4]) {
+  float b[4][kSpLane];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float* xj = X + (int64_t)(j[u] >= 0 ? j[u] : 0) * d;
+    s[u] = 0.f;
+    c[u] = 0.f;
+#pragma unroll
+    for (int q = 0; q < kSpLane; ++q) b[u][q] = (q < r.cnt && j[u] >= 0) ? xj[r.t[q]] : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < kSpLane; ++q) {
+    if (q < r.cmax) {  // warp-uniform
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dot2_step(s[u], c[u], r.a[q], b[u][q]);
+    }
+  }
 }
 
 __global__ void k_inv_norms(const double* __restrict__ nrm2, int64_t n, double* __restrict__ rinv,
@@ -182,7 +297,7 @@ __global__ void k_inv_norms(const double* __restrict__ nrm2, int64_t n, double* 
   rinv2[i] = make_float2(h, (float)(r - (double)h));
 }
 
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 3)
 k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64_t n_rows, int d, int K,
          const float* __restrict__ err,
          const float* __restrict__ err_max_p, float acc_coef, const float2* __restrict__ rinv2,
@@ -250,6 +365,9 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
       const float2 ri = rinv2[i];
       unsigned long long myk = 0;  // below every cosine's key
       int32_t myj = INT32_MAX;
+      SparseRow sp;
+      sparse_row(xi, d, sp);
+      const bool sparse = sp.cmax <= kSpLane && sp.cmax < (d + 31) / 32;  // warp-uniform
       while (rmask) {  // four candidates per pass
         int tl[4];
         int32_t jt[4];
@@ -261,15 +379,30 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
           if (tl[u] < 0) jt[u] = -1;
         }
         float ds[4], dc[4];
-        dot2_rows4(X, xi, d, jt, ds, dc);
+        if (sparse)
+          dot2_sparse4(X, d, sp, jt, ds, dc);
+        else
+          dot2_rows4(X, xi, d, jt, ds, dc);
+        float rs, rc;
+        dot2_reduce4(ds, dc, rs, rc);
+        // each lane owns at most one of the four candidates; fetch its sum
+        int own = -1;
+        int32_t jown = -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (lane == tl[u]) {  // the owner lane alone evaluates its cosine
-            float h, l;
-            cos_ff(ds[u], dc[u], ri, rinv2[jt[u]], h, l);
-            myk = ffkey(h, l);
-            myj = jt[u];
+          if (lane == tl[u]) {
+            own = u;
+            jown = jt[u];
           }
+        const int src = own >= 0 ? dot2_reduce4_src(own, lane) : lane;
+        rs = __shfl_sync(0xffffffffu, rs, src);
+        rc = __shfl_sync(0xffffffffu, rc, src);
+        if (own >= 0) {  // the owner lane alone evaluates its cosine
+          float h, l;
+          cos_ff(rs, rc, ri, rinv2[jown], h, l);
+          myk = ffkey(h, l);
+          myj = jown;
+        }
       }
       warp_sort_key(myk, myj);
       if (lane < K) {

@@ -86,6 +86,39 @@ def test_knn_hypergraph_workload_sampled(ak):
         assert info["knn_exhaustive_rows"] < X.shape[0] // 100
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_knn_sparse_rows_mixed(ak, prec):
+    """Rows of every sparsity the re-rank meets: a few nonzeros spread over
+    the lanes' strided shares (the sparse-row gather), nonzeros packed into
+    one share (t = 5 mod 32: too many for one lane, the dense loop), dense
+    rows, zero rows, duplicates and sign changes.  Every list must be exact."""
+    rng = np.random.default_rng(31)
+    n, d, K = 3000, 300, 8
+    X = np.zeros((n, d), np.float32)
+    topics = [rng.choice(d, 24, replace=False) for _ in range(6)]
+    lab = rng.integers(0, 6, n)
+    for i in range(n):
+        nnz = int(rng.integers(1, 30))
+        own = rng.random(nnz) < 0.7
+        cols = np.where(own, rng.choice(topics[lab[i]], nnz), rng.integers(0, d, nnz))
+        X[i, cols] = rng.exponential(1.0, nnz).astype(np.float32)
+    packed = rng.choice(n, 200, replace=False)
+    X[packed] = 0.0
+    share = np.arange(5, d, 32)
+    X[np.ix_(packed, share)] = rng.standard_normal((200, share.size)).astype(np.float32)
+    dense = rng.choice(n, 150, replace=False)
+    X[dense] = rng.standard_normal((150, d)).astype(np.float32)
+    X[7] = 0.0
+    X[100] = X[200] = X[300]
+    X[400] = -X[401]
+    X[500] = 2.5 * X[501]
+    idx, sim, _ = _run(ak, X, K, prec)
+    c = compare_knn(X, K, np.arange(n), idx, sim)
+    assert c["exact_rows"] + c["near_tie_rows"] == n
+    assert idx[7].tolist() == [j for j in range(n) if j != 7][:K]
+    assert set(idx[300][:2].tolist()) == {100, 200}
+
+
 def test_knn_invalid_arguments(ak):
     X = torch.zeros((5, 3), device="cuda")
     with pytest.raises(ak.AnckaError) as e:
