@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--prec", default=None, choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
-    ap.add_argument("--knn-probe", default=None, metavar="N,D",
-                    help="only run the BF16 KNN twice on a seeded N x D Gaussian matrix (profiling aid)")
+    ap.add_argument("--knn-probe", default=None, metavar="N,D[,tfidf]",
+                    help="only run the BF16 KNN twice on a seeded N x D Gaussian matrix, or on the hypergraph "
+                         "generator's TF-IDF attributes at N nodes (D = 500) with ',tfidf' (profiling aid)")
     ap.add_argument("--spmm-probe", type=int, default=None, metavar="N",
                     help="Algorithm 4 on the DC-SBM generator (k=47, d=100, 25 N edges) at N nodes: the walk "
                          "products' time against their compulsory bytes (one JSON line; profiling aid)")
@@ -188,19 +189,29 @@ def reference_arm(args, rank, world):
 
 def knn_probe(args):
     """Kernel-focused run for profiling: ancka_knn (BF16) twice on a seeded
-    N x D standard-normal matrix; prints the second call's contraction time."""
+    N x D standard-normal matrix (or the hypergraph generator's sparse TF-IDF
+    attributes); prints the second call's contraction time."""
     import torch
     from paper_2408_05459_gb300 import ancka, build as B
     if not os.path.exists(B.LIB):
         B.build()
     ancka.load()
-    n, d = (int(v) for v in args.knn_probe.split(","))
-    X = torch.as_tensor(np.random.default_rng(0).standard_normal((n, d)).astype(np.float32), device="cuda")
+    parts = args.knn_probe.split(",")
+    n, d = int(parts[0]), int(parts[1])
+    if len(parts) > 2 and parts[2] == "tfidf":
+        from paper_2408_05459_gb300 import synth
+        Xh = synth.config_hypergraph(0, n=n, m=2 * n)["X"]
+        if Xh.shape[1] != d:
+            raise SystemExit(f"the TF-IDF generator has D = {Xh.shape[1]}")
+        X = torch.as_tensor(Xh, device="cuda")
+    else:
+        X = torch.as_tensor(np.random.default_rng(0).standard_normal((n, d)).astype(np.float32), device="cuda")
     for _ in range(2):
         _, _, info = ancka.knn(X, 10, "bf16")
     torch.cuda.synchronize()
     ms = info["ms_contract"]
-    print(json.dumps({"probe": "knn_bf16", "n": n, "d": d, "ms_contract": round(ms, 3),
+    print(json.dumps({"probe": "knn_bf16", "n": n, "d": d, "x": "tfidf" if len(parts) > 2 else "gaussian",
+                      "ms_contract": round(ms, 3),
                       "ms_knn": round(info["ms_knn"], 3), "knn_exhaustive_rows": info["knn_exhaustive_rows"],
                       "tflops": round(2.0 * n * n * d / (ms * 1e-3) / 1e12, 1),
                       "knn_fallback_rows": info["knn_fallback_rows"]}), flush=True)

@@ -379,10 +379,12 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       st = build_topology(ws, *topo, &w, s);
     }
     // InitBCM needs only the topology: with the default start it runs on a
-    // second stream, launched right after the contraction kernel so that its
-    // blocks take the room the contraction leaves (and, for host inputs, the
-    // time X is still being copied); the call's stream waits for it before
-    // the iteration, and on every exit before the workspace is released
+    // second stream.  For host inputs it starts as soon as the topology is
+    // built, while X is still being copied; otherwise it is launched right
+    // after the contraction kernel, so that it never holds SMs the
+    // contraction's persistent CTAs wait for, and overlaps the re-rank and
+    // the build.  The call's stream waits for it before the iteration, and
+    // on every exit before the workspace is released.
     static thread_local cudaStream_t init_streams[kMaxDevices] = {};
     cudaStream_t& is = init_streams[device_slot()];
     if (!is) ANCKA_CUDA(cudaStreamCreateWithFlags(&is, cudaStreamNonBlocking));
@@ -414,6 +416,8 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       ij.launched = true;
       return ANCKA_OK;
     };
+    const bool early_init = x_ready != nullptr;
+    if (st == ANCKA_OK && early_init) st = start_init();
     if (st == ANCKA_OK && x_ready) ANCKA_CUDA(cudaStreamWaitEvent(s, x_ready, 0));
     if (st == ANCKA_OK && !knn_idx_in) {
       Phase ph(tp, s, 0);
@@ -421,7 +425,8 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       if (st == ANCKA_OK && !sim) st = ws.alloc(&sim, (size_t)n * K);
       if (st == ANCKA_OK)
         st = knn_impl(ws, X, n, d, K, p->knn_prec, idx, sim, &zero_row, &ncand, &nfb, &nex, info != nullptr, s,
-                      info && K <= max_candidate_K(p->knn_prec) ? cev : nullptr, start_init);
+                      info && K <= max_candidate_K(p->knn_prec) ? cev : nullptr,
+                      early_init ? std::function<ancka_status()>() : std::function<ancka_status()>(start_init));
       contract_timed = info && K <= max_candidate_K(p->knn_prec);
     } else if (st == ANCKA_OK) {
       Phase ph(tp, s, 0);
@@ -444,7 +449,7 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       idx = const_cast<int32_t*>(knn_idx_in);
       sim = const_cast<float*>(knn_sim_in);
     }
-    if (st == ANCKA_OK && knn_idx_in) st = start_init();  // no contraction to queue behind
+    if (st == ANCKA_OK && knn_idx_in && !early_init) st = start_init();  // no contraction to queue behind
     if (st == ANCKA_OK && p->init == 1) {
       k_check_labels<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(p->init_labels, n, p->k, bad);
       int32_t hb = 0;

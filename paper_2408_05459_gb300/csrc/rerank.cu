@@ -320,6 +320,11 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
     const int nvalid = __popc(vmask);
     const float ei = err[i], emax = *err_max_p;
     const float ej = valid ? err[j] : 0.f;
+    const float2 rj2 = valid ? rinv2[j] : make_float2(0.f, 0.f);  // used by this lane if j is re-scored
+    // row i's nonzeros, read while the candidate loads are in flight
+    const float* xi = X + i * (int64_t)d;
+    SparseRow sp;
+    sparse_row(xi, d, sp);
     const float m = ei * (1.f + ej) + ej + acc_coef * (1.f + ei) * (1.f + ej);
     const float lower = valid ? v - m : -INFINITY;
     const float upper = valid ? v + m : -INFINITY;
@@ -361,12 +366,9 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
       const bool inR = valid && upper >= lb;
       unsigned rmask = __ballot_sync(0xffffffffu, inR);
       if (lane == 0) atomicAdd(&block_cand, (unsigned)__popc(rmask));
-      const float* xi = X + i * (int64_t)d;
       const float2 ri = rinv2[i];
       unsigned long long myk = 0;  // below every cosine's key
       int32_t myj = INT32_MAX;
-      SparseRow sp;
-      sparse_row(xi, d, sp);
       const bool sparse = sp.cmax <= kSpLane && sp.cmax < (d + 31) / 32;  // warp-uniform
       while (rmask) {  // four candidates per pass
         int tl[4];
@@ -385,23 +387,19 @@ k_rerank(const float* __restrict__ X, const int32_t* __restrict__ rows_in, int64
           dot2_rows4(X, xi, d, jt, ds, dc);
         float rs, rc;
         dot2_reduce4(ds, dc, rs, rc);
-        // each lane owns at most one of the four candidates; fetch its sum
+        // each lane owns at most one of the four candidates (its own j); fetch its sum
         int own = -1;
-        int32_t jown = -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (lane == tl[u]) {
-            own = u;
-            jown = jt[u];
-          }
+          if (lane == tl[u]) own = u;
         const int src = own >= 0 ? dot2_reduce4_src(own, lane) : lane;
         rs = __shfl_sync(0xffffffffu, rs, src);
         rc = __shfl_sync(0xffffffffu, rc, src);
         if (own >= 0) {  // the owner lane alone evaluates its cosine
           float h, l;
-          cos_ff(rs, rc, ri, rinv2[jown], h, l);
+          cos_ff(rs, rc, ri, rj2, h, l);
           myk = ffkey(h, l);
-          myj = jown;
+          myj = j;
         }
       }
       warp_sort_key(myk, myj);

@@ -104,11 +104,17 @@ def test_cliques_closed_form_on_gpu(ak):
     assert O.max_principal_angle(ex["Q"][:, :k].astype(np.float64), ind) < 1e-3
 
 
-def test_cluster_host_matches_device(ak):
-    g = synth.config_small_sbm(1)
-    p = _params(ak, k=5, knn_prec="fp32")
+@pytest.mark.parametrize("kind", ["graph", "hypergraph"])
+def test_cluster_host_matches_device(ak, kind):
+    """Host buffers in (InitBCM then starts while X is being copied) give the
+    labels of the device-input call."""
+    if kind == "graph":
+        g, prec = synth.config_small_sbm(1), "fp32"
+    else:
+        g, prec = synth.config_hypergraph(3, n=20000, m=40000), "bf16"
+    p = _params(ak, k=g["k"], knn_prec=prec)
     lab_h, info_h = ak.cluster_host(g, g["X"], p)
-    lab_d, _, _ = _gpu_cluster(ak, g, "fp32")
+    lab_d, _, _ = _gpu_cluster(ak, g, prec)
     assert np.array_equal(lab_h, lab_d)
     assert info_h["ms_total"] > 0
 
