@@ -1179,7 +1179,7 @@ __device__ bool polar_newton_schulz(const float* M, int k, float* X, float* Xn, 
 //     or Jacobi for rank-deficient M) and obj = n - 2 tr(Omega), and stops
 //     once |obj - obj_prev| <= 4 eps max(1, |obj|).  All CTAs compute the
 //     same R and the same decision from the same totals.
-__global__ void __launch_bounds__(kDiscThreads, 1)
+__global__ void __launch_bounds__(kDiscThreads, 2)  // <= 64 registers: half an SM's file, room for the hops' blocks
 k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_iter, int32_t* __restrict__ labels,
              DiscState st, int32_t* __restrict__ iters_out, int32_t* __restrict__ flags) {
   extern __shared__ __align__(16) float dsm_f[];
@@ -1901,6 +1901,35 @@ struct PhaseTimer {
   }
 };
 
+// the keep-best chain's stream (one per device and host thread), at the
+// highest priority: its work ends the call
+ancka_status side_stream(cudaStream_t* out) {
+  static thread_local cudaStream_t streams[kMaxDevices] = {};
+  cudaStream_t& ds = streams[device_slot()];
+  if (!ds) {
+    int lo = 0, hi = 0;
+    ANCKA_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    ANCKA_CUDA(cudaStreamCreateWithPriority(&ds, cudaStreamNonBlocking, hi));
+  }
+  *out = ds;
+  return ANCKA_OK;
+}
+
+// on every exit: the call's stream waits for the side stream's work (which
+// uses the call's workspace) before anything is released
+struct SideJoin {
+  cudaStream_t s = nullptr, ds = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool active = false;
+  ~SideJoin() {
+    if (active) {
+      cudaEventRecord(ev, ds);
+      cudaStreamWaitEvent(s, ev, 0);
+    }
+    if (ev) release_event(ev);
+  }
+};
+
 }  // namespace
 
 // InitBCM (Alg. 4 lines 3-11) on its own: the k highest-degree nodes (ties by
@@ -2008,6 +2037,22 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   ANCKA_TRY(ws.zeros(&chol_status, 1));
   DiscState st;
   ANCKA_TRY(make_disc_state(ws, n, k, &st));
+  // Fixed schedule: the keep-best chain (CalMHC of Y^(0), then Discretize and
+  // CalMHC at each check point) reads Q^(t) but feeds nothing back into the
+  // hops, so it runs on a second stream beside them, in its own order, with
+  // its own edge buffer and two row-normalised snapshots of Q (alternating
+  // between check points).  Paper mode decides whether to go on from phi, so
+  // there the chain stays on the call's stream.
+  const bool side = !cfg.early_stop;
+  cudaStream_t ds = s;
+  if (side) ANCKA_TRY(side_stream(&ds));
+  Ctx cd = c;
+  cd.s = ds;
+  float* Qt2[2] = {Qt, Qt};
+  if (side) {
+    ANCKA_TRY(ws.alloc(&Qt2[1], (size_t)n * ldk));
+    if (w.kind == ANCKA_HYPERGRAPH) ANCKA_TRY(ws.alloc(&cd.E, (size_t)(w.m > 0 ? w.m : 1) * (ld > ldk ? ld : ldk)));
+  }
 
   // ---- InitBCM (Alg. 4 lines 3-11) ----
   {
@@ -2028,7 +2073,7 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     ANCKA_LAUNCHED();
   }
   tr->warm_used = 0;
-  {  // phi(Y^(0)) (reading R8)
+  if (warm_W) {  // phi(Y^(0)) (reading R8), compared with the warm start's below
     PhaseTimer pt(tr, s, 5);
     ANCKA_TRY(cal_mhc(c, sc, y0, cfg.gamma, tr->phi_dev + 0, tr->phi_best_dev, nullptr, ybest, true));
   }
@@ -2072,6 +2117,32 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     }
   }
   if (init_out) ANCKA_CUDA(cudaMemcpyAsync(init_out, y0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  // fork: everything above (Y^(0), Q^(0), the scratch) is ready on s here
+  SideJoin sj;
+  cudaEvent_t q_ev = nullptr, disc_done[2] = {nullptr, nullptr};
+  bool qt_used[2] = {false, false};
+  struct Events {
+    cudaEvent_t* e[3];
+    ~Events() {
+      for (cudaEvent_t* p : e)
+        if (*p) release_event(*p);
+    }
+  } evs{{&q_ev, &disc_done[0], &disc_done[1]}};
+  if (side) {
+    sj.s = s;
+    sj.ds = ds;
+    sj.ev = pooled_event();
+    q_ev = pooled_event();
+    disc_done[0] = pooled_event();
+    disc_done[1] = pooled_event();
+    ANCKA_CUDA(cudaEventRecord(q_ev, s));
+    ANCKA_CUDA(cudaStreamWaitEvent(ds, q_ev, 0));
+    sj.active = true;
+  }
+  if (!warm_W) {  // phi(Y^(0)) (reading R8)
+    PhaseTimer pt(tr, ds, 5);
+    ANCKA_TRY(cal_mhc(cd, sc, y0, cfg.gamma, tr->phi_dev + 0, tr->phi_best_dev, nullptr, ybest, true));
+  }
   // paper mode (Eq. tcond-1 / tcond-2): Q(t-1) kept at the check points
   float* Qprev = nullptr;
   float* dq_part = nullptr;
@@ -2114,16 +2185,26 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
       // trace slots beyond ANCKA_MAX_TRACE are not recorded
       const bool rec = slot < ANCKA_MAX_TRACE;
       double* phi_slot = rec ? tr->phi_dev + slot : phi_spare;
-      {
-        PhaseTimer pt(tr, s, 4);
-        k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Q, ld, 1, n, k, Qt, ldk);
-        ANCKA_LAUNCHED();
-        ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, cfg.disc_max_iter, yt, rec ? tr->disc_iters_dev + slot : di_spare,
-                                 tr->flags_dev, s));
+      const int b = side ? slot & 1 : 0;
+      if (side && qt_used[b]) ANCKA_CUDA(cudaStreamWaitEvent(s, disc_done[b], 0));  // its last reader is done
+      k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Q, ld, 1, n, k, Qt2[b], ldk);  // the snapshot of Q^(t)
+      ANCKA_LAUNCHED();
+      if (side) {
+        ANCKA_CUDA(cudaEventRecord(q_ev, s));
+        ANCKA_CUDA(cudaStreamWaitEvent(ds, q_ev, 0));
       }
       {
-        PhaseTimer pt(tr, s, 5);
-        ANCKA_TRY(cal_mhc(c, sc, yt, cfg.gamma, phi_slot, tr->phi_best_dev, rec ? tr->taken_dev + slot : tk_spare,
+        PhaseTimer pt(tr, ds, 4);
+        ANCKA_TRY(run_discretize(st, Qt2[b], ldk, n, k, cfg.disc_max_iter, yt,
+                                 rec ? tr->disc_iters_dev + slot : di_spare, tr->flags_dev, ds));
+      }
+      if (side) {
+        ANCKA_CUDA(cudaEventRecord(disc_done[b], ds));
+        qt_used[b] = true;
+      }
+      {
+        PhaseTimer pt(tr, ds, 5);
+        ANCKA_TRY(cal_mhc(cd, sc, yt, cfg.gamma, phi_slot, tr->phi_best_dev, rec ? tr->taken_dev + slot : tk_spare,
                           ybest, false));
       }
       ++slot;
@@ -2152,6 +2233,11 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
   }
   tr->n_phi = slot < ANCKA_MAX_TRACE ? slot : ANCKA_MAX_TRACE;
   tr->iters_run = t_run;
+  if (sj.active) {  // join: ybest, the trace and the Discretize flags are final on s after this
+    ANCKA_CUDA(cudaEventRecord(sj.ev, ds));
+    ANCKA_CUDA(cudaStreamWaitEvent(s, sj.ev, 0));
+    sj.active = false;
+  }
   ANCKA_CUDA(cudaMemcpyAsync(labels_out, ybest, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
   if (Q_out) ANCKA_CUDA(cudaMemcpy2DAsync(Q_out, sizeof(float) * wq, Q, sizeof(float) * ld, sizeof(float) * wq, n,
                                          cudaMemcpyDeviceToDevice, s));
