@@ -1822,8 +1822,11 @@ ancka_status make_disc_state(Workspace& ws, int64_t n, int k, DiscState* st) {
 size_t disc_smem_bytes() { return (size_t)(kDiscRegion + kDiscLabels + kDiscSlices + kDiscR) * sizeof(float); }
 
 // Launch Discretize on a row-normalised block (one cooperative launch).
+// half_grid: at most half the SMs, for a Discretize that shares the GPU with
+// other work (the rows per CTA, and so the FP32 partial sums, follow the grid)
 ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64_t n, int k, int max_iter,
-                            int32_t* labels, int32_t* iters_out, int32_t* flags, cudaStream_t s) {
+                            int32_t* labels, int32_t* iters_out, int32_t* flags, cudaStream_t s,
+                            bool half_grid = false) {
   k_disc_init<<<1, 32, 0, s>>>(st.bar, st.err);
   ANCKA_LAUNCHED();
   const size_t smem = disc_smem_bytes();
@@ -1843,7 +1846,8 @@ ancka_status run_discretize(const DiscState& st, const float* Qt, int ldt, int64
     }
   }
   int grid = (int)ceil_div(n, 512);
-  if (grid > max_grid) grid = max_grid;
+  const int cap = half_grid ? (max_grid + 1) / 2 : max_grid;
+  if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   DiscState stc = st;
   void* args[] = {(void*)&Qt, (void*)&ldt, (void*)&n, (void*)&k, (void*)&max_iter, (void*)&labels,
@@ -2195,8 +2199,9 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
       }
       {
         PhaseTimer pt(tr, ds, 4);
+        // beside the hops on half the SMs; the last one runs alone, on all
         ANCKA_TRY(run_discretize(st, Qt2[b], ldk, n, k, cfg.disc_max_iter, yt,
-                                 rec ? tr->disc_iters_dev + slot : di_spare, tr->flags_dev, ds));
+                                 rec ? tr->disc_iters_dev + slot : di_spare, tr->flags_dev, ds, side && t < cfg.T));
       }
       if (side) {
         ANCKA_CUDA(cudaEventRecord(disc_done[b], ds));
