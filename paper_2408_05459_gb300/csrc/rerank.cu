@@ -11,9 +11,11 @@
 // lower bound of the true K-th similarity.  Candidates with s^ + m < lb and
 // every non-candidate (s^ <= thr_i) when thr_i + m_max < lb cannot be in the
 // list.  The remaining candidates are re-scored with a compensated (Dot2)
-// dot product of the raw FP32 rows, evaluated in double, and sorted by
-// (cosine desc, index asc).  A row that fails the certificate is flagged and
-// recomputed exhaustively by k_knn_exhaustive.
+// dot product of the raw FP32 rows (over row i's nonzero positions alone when
+// it is sparse), scaled by the inverse norms in float-float, and sorted by
+// (cosine desc, index asc).  A row that fails the certificate goes to the
+// collect pass, and one that overflows it to the exhaustive kernels (FP64
+// cosines there).
 #include "common.cuh"
 
 namespace ancka {
