@@ -155,6 +155,18 @@ def cpu_baseline(g, knn_idx, rows_sample=256, seed=1):
                             f"the default BLAS thread pool (up to {os.cpu_count()} threads)")
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (the job ends with its slowest
+    replica), then a barrier; `dist` is None for one process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def reference_arm(args, rank, world):
     """The oracle as the reference arm: each step is the bounded sample of
     cpu_baseline().  The iteration needs KNN lists for every node, which the
@@ -400,12 +412,7 @@ def main():
         clocks = clk.stop()
         launches = ancka.kernel_launches() - l0
         torch.cuda.synchronize()
-        ms = float(np.mean(durs))
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-            dist.barrier()
+        ms = max_over_ranks(float(np.mean(durs)), dist, "cuda")
         torch.cuda.synchronize()
         return ms, durs, (float(np.mean(contract)) if contract else None), infos, clocks, launches, wall
 
