@@ -219,8 +219,9 @@ float tc_acc_bound(int dp, int k_per_mma, int ulp_log2) {
 
 // the KNN lists with every step on the device
 // after_contraction (may be empty): called once the contraction kernel is
-// enqueued, before the first host read (the cluster call starts InitBCM on a
-// second stream there, so that its kernels queue behind the contraction's)
+// enqueued, before the first host read (with device inputs the cluster call
+// starts InitBCM on a second stream there, so that its kernels queue behind
+// the contraction's)
 ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
                       int32_t* idx, float* sim, int32_t** zero_row, int64_t* ncand, int64_t* nfb,
                       int64_t* nex, bool counts, cudaStream_t s, cudaEvent_t* contract_ev = nullptr,
