@@ -78,3 +78,18 @@ def test_oracle_and_cuda_path_are_independent():
                 assert not re.search(r"^\s*(from|import)\s+oracle", text, re.M), f
     osrc = open(os.path.join(ROOT, "oracle", "ancka_oracle.py")).read()
     assert "paper_2408_05459_gb300" not in osrc
+
+
+def test_no_gpu_means_an_error_not_a_host_fallback(lib):
+    """Without a GPU the compute entry points return an error status (and the
+    binding raises); nothing is computed on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2408_05459_gb300 import synth
+    assert lib.ancka_device_check() != 0
+    assert lib.ancka_last_error()
+    g = synth.config_small_sbm(0)
+    with pytest.raises(ancka.AnckaError) as e:
+        ancka.cluster_host(g, g["X"], ancka.default_params(k=5), stream=ctypes.c_void_p(0))
+    assert e.value.status != 0
