@@ -19,6 +19,10 @@
  *     buffer; the library allocates its own workspace with stream-ordered
  *     cudaMallocAsync on `stream` and frees it before returning.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Parts of a call with no data dependence on each other may run on the
+ *     library's own streams (one set per device and host thread); each is
+ *     joined back into `stream` before the outputs are written and before
+ *     the workspace is released, so the outputs are ordered on `stream`.
  *   - Matrices are row-major and dense unless stated; int32 node ids.
  *   - Inputs are validated on the host before any launch; a bad argument
  *     returns ANCKA_ERR_INVALID_ARG and launches nothing.
