@@ -60,7 +60,8 @@ typedef enum {
 typedef enum {
   ANCKA_PREC_FP32 = 0,  /* CUDA-core FP32 contraction */
   ANCKA_PREC_BF16 = 1,  /* tcgen05 BF16 x BF16 -> FP32 (TMEM) contraction */
-  ANCKA_PREC_FP8 = 2    /* reserved: FP8 e4m3 contraction */
+  ANCKA_PREC_FP8 = 2    /* tcgen05 FP8-E4M3 x E4M3 -> FP32 contraction (d <= 512); rows
+                           it cannot certify are redone from BF16 candidates */
 } ancka_prec;
 
 typedef enum { ANCKA_GRAPH = 0, ANCKA_HYPERGRAPH = 1, ANCKA_MULTIPLEX = 2 } ancka_topo_kind;
@@ -253,9 +254,28 @@ ancka_status ancka_cluster_host(const ancka_topology* topo, const float* X, int3
  *   labels  n int32 output: the last Y of the alternation
  *   iters   host int32 out (may be NULL): inner iterations executed
  * R starts at I; stops when |obj - obj_prev| <= 4 eps max(1,|obj|) or after
- * max_iter iterations.  The k x k SVD runs in FP64. 1 <= k <= 64. */
+ * max_iter iterations.  1 <= k <= 64.
+ * Precision: M = Y~^T Q~ is summed in float-float (compensated FP32) and
+ * rounded to FP32; the k x k polar factor R = V U^T is computed in FP32 by
+ * the Newton-Schulz iteration (an FP32 one-sided Jacobi SVD when M is
+ * rank-deficient or the iteration does not settle); tr(Omega) = tr(M R) and
+ * obj are accumulated in FP64.  R feeds only the FP32 argmax of Q~ R, so no
+ * part of the k x k work is carried out in FP64 arithmetic on GB300's narrow
+ * FP64 pipe. */
 ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq,
                               int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
+
+/* Diagnostic: the k x k polar factor Discretize computes from
+ * M = Y~^T Q~ (Alg. 5, Eq. svd-in-discr): R = V U^T for M = U Omega V^T,
+ * by the same device routines (FP32 Newton-Schulz; FP32 Jacobi SVD when a
+ * row of M is zero or the iteration does not settle), so that R can be
+ * compared with an FP64 SVD.
+ *   M       k x k FP32 row-major (device, caller-owned)
+ *   R       k x k FP32 row-major output (device, caller-owned)
+ *   method  host int32 out (may be NULL): 0 = Newton-Schulz, 1 = Jacobi;
+ *           when non-NULL the call synchronises `stream`.
+ * 1 <= k <= 64; ANCKA_ERR_INVALID_ARG otherwise. */
+ancka_status ancka_polar_factor(const float* M, int32_t k, float* R, int32_t* method, void* stream);
 
 /* Discretize exactly as ancka_discretize, but without allocating any device
  * memory (the paper has no counterpart: this serves callers that must not
@@ -266,8 +286,11 @@ ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq
  * every GPU that loads it until exit; sizes needing more (about
  * n * round_up(k, 4) * 4 bytes plus small state) return
  * ANCKA_ERR_INVALID_ARG.  The first call on a device looks up that array's
- * address and should come before any stream capture.  Calls share the array:
- * calls that overlap on the GPU race.  Arguments as for ancka_discretize. */
+ * device address (a runtime query, no allocation); make that first call
+ * before any stream capture.  Every call waits for `stream` before it
+ * returns, because it reads the inner-iteration count and an error flag back
+ * to the host.  Calls share the array: calls that overlap on the GPU race.
+ * Arguments as for ancka_discretize. */
 ancka_status ancka_discretize_noalloc(const float* Qk, int64_t n, int32_t k, int32_t ldq,
                                       int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
 

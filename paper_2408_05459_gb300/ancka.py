@@ -142,6 +142,8 @@ def load(path: str = LIB_PATH):
     L.ancka_discretize.restype = ctypes.c_int
     L.ancka_discretize_noalloc.argtypes = [vp, i64, i32, i32, i32, vp, ctypes.POINTER(i32), vp]
     L.ancka_discretize_noalloc.restype = ctypes.c_int
+    L.ancka_polar_factor.argtypes = [vp, i32, vp, ctypes.POINTER(i32), vp]
+    L.ancka_polar_factor.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -384,6 +386,15 @@ def cluster_host(g: dict, X: np.ndarray, params: Params | None = None, with_info
         s.m = len(hp) - 1
         s.he_ptr = hp.ctypes.data
         s.he_nodes = hn.ctypes.data
+    elif "row_ptr" in g:  # layers already in the ABI's layout (e.g. pinned host buffers)
+        rp = g["row_ptr"]
+        ci = g["col_idx"]
+        assert rp.dtype == np.int64 and ci.dtype == np.int32 and rp.flags.c_contiguous and ci.flags.c_contiguous
+        s.L = int(g["L"])
+        assert rp.size == s.L * (n + 1)
+        s.row_ptr = rp.ctypes.data
+        s.col_idx = ci.ctypes.data if ci.size else None
+        s.nnz = ci.size
     else:
         rps, cols, off = [], [], 0
         for rp, col in g["layers"]:
@@ -417,6 +428,21 @@ def discretize(Qk, max_iter: int = 20):
     st = load().ancka_discretize(_ptr(Qk), n, k, Qk.stride(0), max_iter, _ptr(labels), ctypes.byref(it), _stream())
     _check("ancka_discretize", st)
     return labels, it.value
+
+
+def polar_factor(M):
+    """ancka_polar_factor: R = V U^T of a k x k device matrix M = U Omega V^T
+    by Discretize's own device routines; returns (R, method) with method 0 =
+    Newton-Schulz, 1 = Jacobi."""
+    import torch
+    assert M.is_cuda and M.dtype == torch.float32 and M.dim() == 2 and M.shape[0] == M.shape[1]
+    M = M.contiguous()
+    k = M.shape[0]
+    R = torch.empty_like(M)
+    method = ctypes.c_int32(-1)
+    st = load().ancka_polar_factor(_ptr(M), k, _ptr(R), ctypes.byref(method), _stream())
+    _check("ancka_polar_factor", st)
+    return R, method.value
 
 
 def discretize_noalloc(Qk, labels, max_iter: int = 20):

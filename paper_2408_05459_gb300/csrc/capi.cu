@@ -811,6 +811,21 @@ ancka_status ancka_discretize(const float* Qk, int64_t n, int32_t k, int32_t ldq
   return st;
 }
 
+ancka_status ancka_polar_factor(const float* M, int32_t k, float* R, int32_t* method, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_REQUIRE(M && R, "M or R is NULL");
+  ANCKA_REQUIRE(k >= 1 && k <= 64, "k = %d out of range [1, 64]", k);
+  Workspace ws(s);
+  int32_t* md;
+  ANCKA_TRY(ws.zeros(&md, 1));
+  ANCKA_TRY(polar_factor(M, k, R, md, s));
+  if (method) {
+    ANCKA_CUDA(cudaMemcpyAsync(method, md, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ANCKA_CUDA(cudaStreamSynchronize(s));
+  }
+  return ANCKA_OK;
+}
 
 ancka_status ancka_warm_predict(const ancka_topology* topo, const float* X, int32_t d, const ancka_warm_model* model,
                                 float* W, void* stream) {

@@ -182,6 +182,7 @@ __device__ __forceinline__ void list_insert(float (&lv)[C], int32_t (&li)[C], fl
 
 // prep.cu: unit rows, low-precision copy, per-row quantisation error
 struct PrepOut {
+  int32_t d;           // feature dimension of X (unpadded)
   int32_t dp;          // padded feature dimension of the copy
   int64_t n_pad;       // padded row count of the copy
   float* xu32;         // FP32 unit rows (n_pad x dp) or null
@@ -335,6 +336,7 @@ ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, in
                         int32_t max_iter, int32_t* labels, int32_t* iters_dev, int32_t* flags_dev,
                         int32_t** err_dev, cudaStream_t s);
 size_t discretize_scratch_bytes(int64_t n, int32_t k);
+ancka_status polar_factor(const float* M, int32_t k, float* R, int32_t* method_dev, cudaStream_t s);
 ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, int64_t n, int32_t k, int32_t ldq,
                                 int32_t max_iter, int32_t* labels, int32_t** iters_dev, int32_t** err_dev,
                                 cudaStream_t s);

@@ -5,8 +5,10 @@
 //
 // Dense blocks are n x ld FP32 row-major with ld = round_up(width, 4) and
 // zero padding columns.  Every reduction has a fixed order, so a run is
-// bitwise reproducible.  FP64 is used only for k x k work (Gram matrices,
-// Cholesky, the Discretize SVD) and for cross-CTA sums.
+// bitwise reproducible.  FP64 is used only for k x k work (the CholeskyQR
+// Cholesky factor and inverse, Discretize's trace and objective); cross-CTA
+// sums are float-float.  Discretize's k x k polar factor is FP32
+// (Newton-Schulz, Jacobi SVD fallback).
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -1363,6 +1365,42 @@ k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_it
   }
 }
 
+// Diagnostic: R = V U^T for one k x k matrix M = U Omega V^T (row-major,
+// stride k) by the routines of k_discretize's phase B -- Newton-Schulz, or
+// the Jacobi SVD when a row of M is zero (an empty cluster) or the iteration
+// does not settle.  One CTA; method = 0 (Newton-Schulz) or 1 (Jacobi).
+__global__ void __launch_bounds__(kDiscThreads) k_polar_diag(const float* __restrict__ Min, int k,
+                                                             float* __restrict__ Rout, int32_t* __restrict__ method) {
+  extern __shared__ __align__(16) float dsm_f[];
+  __shared__ int rotated;
+  __shared__ int zero_row;
+  const int ldr = (k + 15) & ~15;
+  float* M = dsm_f;
+  float* X0 = M + kDiscLd * 64;
+  float* X1 = M + 2 * kDiscLd * 64;
+  float* P0 = M + 3 * kDiscLd * 64;
+  float* Rs = M + 4 * kDiscLd * 64;
+  if (threadIdx.x == 0) zero_row = 0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) M[(e / k) * kDiscLd + e % k] = Min[e];
+  for (int e = threadIdx.x; e < k * ldr; e += blockDim.x) Rs[e] = (e / ldr == e % ldr) ? 1.f : 0.f;
+  __syncthreads();
+  for (int l = threadIdx.x; l < k; l += blockDim.x) {
+    bool z = true;
+    for (int c = 0; c < k; ++c) z &= M[l * kDiscLd + c] == 0.f;
+    if (z) atomicOr(&zero_row, 1);
+  }
+  __syncthreads();
+  bool ok = false;
+  if (!zero_row)
+    ok = k <= 16   ? polar_newton_schulz<16>(M, k, X0, X1, P0, Rs, ldr)
+         : k <= 32 ? polar_newton_schulz<32>(M, k, X0, X1, P0, Rs, ldr)
+                   : polar_newton_schulz<64>(M, k, X0, X1, P0, Rs, ldr);
+  if (!ok) polar_jacobi(M, k, X0, X1, P0, Rs, ldr, &rotated);
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rout[e] = Rs[(e / k) * ldr + e % k];
+  if (threadIdx.x == 0) *method = ok ? 0 : 1;
+}
+
 // ---------------------------------------------------------------------------
 // labels -> counts, 1/sqrt(count), one-hot fills, trace, keep-best
 // ---------------------------------------------------------------------------
@@ -2283,6 +2321,15 @@ namespace ancka {
 namespace {
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 }  // namespace
+
+// The polar factor of one k x k matrix by Discretize's device routines.
+ancka_status polar_factor(const float* M, int32_t k, float* R, int32_t* method_dev, cudaStream_t s) {
+  const size_t smem = (size_t)(4 * kDiscLd * 64 + 64 * 64) * sizeof(float);
+  ANCKA_CUDA(cudaFuncSetAttribute(k_polar_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_polar_diag<<<1, kDiscThreads, smem, s>>>(M, k, R, method_dev);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
 
 // Bytes of caller-provided scratch Discretize needs for an n x k block.
 size_t discretize_scratch_bytes(int64_t n, int32_t k) {

@@ -111,20 +111,14 @@ __device__ __forceinline__ float pick32(const uint32_t (&r)[32], int e) {
   return v[0];
 }
 
-// Fold one 32-key chunk (scores in r, keys j0..j0+31) into the row's list.
+// Fold one 32-key chunk (scores in r, keys j0..j0+31, mx = their maximum
+// from the TMEM load) into the row's list.
 template <int C>
-__device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], int64_t j0, int64_t n, int64_t i,
+__device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], float mx, int64_t j0, int64_t n, int64_t i,
                                            float (&lv)[C], int32_t (&li)[C]) {
   // skip the chunk when no lane of the warp has a key above its threshold
-  float m[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) m[q] = fmaxf(__uint_as_float(r[q]), __uint_as_float(r[q + 16]));
-#pragma unroll
-  for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-    for (int q = 0; q < w; ++q) m[q] = fmaxf(m[q], m[q + w]);
   const float thr0 = lv[C - 1];
-  if (!__any_sync(0xffffffffu, m[0] > thr0)) return;
+  if (!__any_sync(0xffffffffu, mx > thr0)) return;
   // pass mask against the threshold at chunk start (it only rises, so the
   // mask is a superset); padding keys and the row itself removed
   uint32_t pm = 0;
@@ -146,12 +140,9 @@ __device__ __forceinline__ void fold_chunk(const uint32_t (&r)[32], int64_t j0, 
 // Collect mode: append every key whose score reaches the row's fixed
 // threshold t to the row's buffer (cap entries; the counter keeps counting
 // past cap so the caller can see an overflow).
-__device__ __forceinline__ void collect_chunk(const uint32_t (&r)[32], int64_t j0, int64_t n, int64_t i, float t,
-                                              int64_t ra, int32_t* __restrict__ cnt, int32_t* __restrict__ buf,
-                                              int cap) {
-  float mx = __uint_as_float(r[0]);
-#pragma unroll
-  for (int e = 1; e < 32; ++e) mx = fmaxf(mx, __uint_as_float(r[e]));
+__device__ __forceinline__ void collect_chunk(const uint32_t (&r)[32], float mx, int64_t j0, int64_t n, int64_t i,
+                                              float t, int64_t ra, int32_t* __restrict__ cnt,
+                                              int32_t* __restrict__ buf, int cap) {
   if (!__any_sync(0xffffffffu, mx >= t)) return;
   uint32_t pm = 0;
 #pragma unroll
@@ -200,11 +191,14 @@ __device__ __forceinline__ int key_rotation(int64_t qb, int n_tiles, int64_t wor
 // mode (two 16-entry lists per row); kE4M3: FP8 operands.  out_scale (list
 // mode, may be null) multiplies the scores written out.
 // key_stride > 1: only every key_stride-th key tile is swept (the sampled
-// pass of the symmetric contraction).
+// pass of the symmetric contraction).  k_last: MMAs issued for the last
+// 128-byte block of features (those past the last one holding a feature of
+// X are zero padding and are skipped).
 template <bool kCollect, bool kE4M3>
 __global__ void __launch_bounds__(kThreads, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-         int64_t n_pad, int64_t qblocks, int kb_count, int nstages, int key_stride, float* __restrict__ cand_val,
+         int64_t n_pad, int64_t qblocks, int kb_count, int k_last, int nstages, int key_stride,
+         float* __restrict__ cand_val,
          int32_t* __restrict__ cand_idx, const float* __restrict__ out_scale, float* __restrict__ part_val,
          int32_t* __restrict__ part_idx, CollectArgs ca, int* __restrict__ err) {
   constexpr int kTK = kE4M3 ? 128 : 64;  // features per stage
@@ -329,8 +323,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + kb * kABytes);
             const uint32_t b0 = smem_u32(sB + stage * kBBytes);
+            const int kmax = kb == kb_count - 1 ? k_last : kMmaPerStage;
 #pragma unroll
             for (int kk = 0; kk < kMmaPerStage; ++kk) {
+              if (kk >= kmax) break;
               if constexpr (kE4M3)
                 umma_e4m3(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0 ? 1u : 0u);
               else
@@ -397,13 +393,15 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
 #pragma unroll 1
         for (int c = 0; c < kSliceN / 32; ++c) {
           uint32_t rv[32];
-          tmem_ld32_issue(tb + (uint32_t)(c * 32), rv);
+          float mx;
+          tmem_ld32_max_issue(tb + (uint32_t)(c * 32), rv, mx);
           tmem_wait();
           pin(rv);
+          pin1(mx);
           if constexpr (kCollect) {
-            collect_chunk(rv, jb + c * 32, n, i, t_row, ra, ca.cnt, ca.buf, ca.cap);
+            collect_chunk(rv, mx, jb + c * 32, n, i, t_row, ra, ca.cnt, ca.buf, ca.cap);
           } else {
-            fold_chunk<C>(rv, jb + c * 32, n, i, lv, li);
+            fold_chunk<C>(rv, mx, jb + c * 32, n, i, lv, li);
           }
         }
         tc_fence_before();
@@ -925,8 +923,14 @@ __global__ void k_gather_rows(const uint8_t* __restrict__ x, int row_bytes, cons
 // partial-list area and the merge of split query blocks.
 template <bool kCollect, bool kE4M3>
 ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, int64_t n_pad,
-                       int64_t n_rows, int kb_count, float* cand_val, int32_t* cand_idx, const float* out_scale,
-                       const CollectArgs& ca, int32_t* err, cudaStream_t s, int key_stride = 1) {
+                       int64_t n_rows, int kb_count, int d, float* cand_val, int32_t* cand_idx,
+                       const float* out_scale, const CollectArgs& ca, int32_t* err, cudaStream_t s,
+                       int key_stride = 1) {
+  // MMAs over the last 128-byte feature block: K = 16 features (BF16) or 32
+  // (E4M3) each; the padding past d is zero and needs none
+  const int per_kb = kE4M3 ? 128 : 64, per_mma = kE4M3 ? 32 : 16;
+  const int rem = d - per_kb * (kb_count - 1);
+  const int k_last = (rem >= 1 && rem <= per_kb) ? (int)ceil_div(rem, per_mma) : kMmaPerStage;
   int nstages;
   size_t smem;
   ANCKA_TRY(tc_smem(kb_count, &nstages, &smem));
@@ -944,9 +948,9 @@ ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& 
     ANCKA_TRY(ws.alloc(&part_idx, (size_t)ctas * 2 * kTM * kCandC));
   }
   ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<kCollect, kE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_knn_tc<kCollect, kE4M3><<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, n_pad, qblocks, kb_count, nstages,
-                                                                   key_stride, cand_val, cand_idx, out_scale,
-                                                                   part_val, part_idx, ca, err);
+  k_knn_tc<kCollect, kE4M3><<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, n_pad, qblocks, kb_count, k_last,
+                                                                   nstages, key_stride, cand_val, cand_idx,
+                                                                   out_scale, part_val, part_idx, ca, err);
   ANCKA_LAUNCHED();
   if (!kCollect) {
     k_merge_lists<<<(unsigned)qblocks, kTM, 0, s>>>(n_tiles, work, ctas, part_val, part_idx, ca.a_rows, n_rows,
@@ -978,8 +982,8 @@ ancka_status knn_candidates_bf16_sym(Workspace& ws, const PrepOut& pr, int64_t n
   ANCKA_TRY(ws.alloc(&sv, (size_t)n * kCandC));
   ANCKA_TRY(ws.alloc(&si, (size_t)n * kCandC));
   CollectArgs none{};
-  const ancka_status st = launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n, kb_count, sv, si, nullptr, none, err,
-                                                  s, kSymStride);
+  const ancka_status st = launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n, kb_count, pr.d, sv, si, nullptr, none,
+                                                  err, s, kSymStride);
   if (st != ANCKA_OK) return st;
   // 2. thresholds
   const int64_t n_tiles = ceil_div(pr.n_pad, kTN);
@@ -1043,7 +1047,8 @@ ancka_status knn_candidates_bf16(Workspace& ws, const PrepOut& pr, int64_t n, fl
   if (n >= g_sym_min_rows.load(std::memory_order_relaxed))
     return knn_candidates_bf16_sym(ws, pr, n, ta, tb, kb_count, cand_val, cand_idx, err, s);
   CollectArgs none{};
-  return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n, kb_count, cand_val, cand_idx, nullptr, none, err, s);
+  return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n, kb_count, pr.d, cand_val, cand_idx, nullptr, none, err,
+                                 s);
 }
 
 void knn_set_symmetric_min_rows(int64_t n_min) { g_sym_min_rows.store(n_min, std::memory_order_relaxed); }
@@ -1059,7 +1064,8 @@ ancka_status knn_candidates_fp8(Workspace& ws, const PrepOut& pr, int64_t n, flo
   ANCKA_TRY(make_map(&ta, pr.x8, pr.dp8, pr.n_pad, kTM, 1));
   ANCKA_TRY(make_map(&tb, pr.x8, pr.dp8, pr.n_pad, kTN, 1));
   CollectArgs none{};
-  return launch_tc<false, true>(ws, ta, tb, n, pr.n_pad, n, kb_count, cand_val, cand_idx, pr.inv_s2, none, err, s);
+  return launch_tc<false, true>(ws, ta, tb, n, pr.n_pad, n, kb_count, pr.d, cand_val, cand_idx, pr.inv_s2, none, err,
+                                s);
 }
 
 int knn_tc_max_dp_fp8() { return 1024; }
@@ -1078,7 +1084,8 @@ ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n,
   ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM, 2));
   ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
   CollectArgs ca{rows, n_a, nullptr, nullptr, nullptr, 0};
-  return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n_a, kb_count, cand_val, cand_idx, nullptr, ca, err, s);
+  return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n_a, kb_count, pr.d, cand_val, cand_idx, nullptr, ca, err,
+                                 s);
 }
 
 ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
@@ -1094,7 +1101,7 @@ ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const
   ANCKA_TRY(make_map(&ta, af, pr.dp, n_a_pad, kTM, 2));
   ANCKA_TRY(make_map(&tb, pr.xb, pr.dp, pr.n_pad, kTN, 2));
   CollectArgs ca{rows, n_a, thr, cnt, buf, cap};
-  return launch_tc<true, false>(ws, ta, tb, n, pr.n_pad, n_a, kb_count, nullptr, nullptr, nullptr, ca, err, s);
+  return launch_tc<true, false>(ws, ta, tb, n, pr.n_pad, n_a, kb_count, pr.d, nullptr, nullptr, nullptr, ca, err, s);
 }
 
 }  // namespace ancka

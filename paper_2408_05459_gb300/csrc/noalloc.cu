@@ -14,7 +14,9 @@
 //
 // The first call on a device looks up the array's device address (a CUDA
 // runtime query, no allocation), so make that first call before any stream
-// capture.  All calls share the one array and leave their contents in it;
+// capture.  Every call waits for its stream before returning: it reads the
+// inner-iteration count and an error flag back to the host.  All calls
+// share the one array and leave their contents in it;
 // each call resets the state it needs, but two calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on it.
 #include <mutex>

@@ -130,6 +130,7 @@ ancka_status prep_rows(Workspace& ws, const float* X, int64_t n, int32_t d, int 
   // BF16 tiles consume 64 features (128 bytes) per pipeline stage; the FP32
   // SIMT tiles consume 8.  Rows are padded to the 128-row tile height.
   const bool tc = prec == ANCKA_PREC_BF16 || prec == ANCKA_PREC_FP8;
+  o.d = d;
   o.dp = (int32_t)(tc ? round_up(d, 64) : round_up(d, 8));
   o.n_pad = round_up(n, 128);
   if (tc) {
