@@ -446,19 +446,29 @@ def build_walk(topo_dict, X, K, beta, knn=None):
     return WalkOperator(topo, P_K, b), idx
 
 
-def ancka(topo_dict, X, params=None, knn=None, init_labels=None, warm=None, warm_bf16=True):
+def ancka(topo_dict, X, params=None, knn=None, init_labels=None, warm=None, warm_bf16=True, timings=None):
     """Algorithm 4 (ANCKA) in FP64 with the fixed schedule of reading R9.
 
     ``warm``: MLP weights (W1, b1, W2, b2) for the learned warm start of
-    readings W1-W6.  Returns a dict with the labels, the final Q
-    (n x (k+1)), the InitBCM labels, the phi trace and the Discretize
-    inner-iteration counts.
+    readings W1-W6.  ``timings``: an optional dict that receives the wall
+    time (s) of each phase -- "build" (P_K, beta, P_N), "init" (InitBCM,
+    Phi(Y0), Q0, the warm start), "iter" (the products and QR), "disc"
+    (Discretize), "mhc" (CalMHC in the loop); it does not change the
+    arithmetic.  Returns a dict with the labels, the final Q (n x (k+1)), the
+    InitBCM labels, the phi trace and the Discretize inner-iteration counts.
     """
+    from time import perf_counter
+    tm = {} if timings is None else timings
+    for key in ("build", "init", "iter", "disc", "mhc"):
+        tm.setdefault(key, 0.0)
     p = dict(DEFAULTS)
     if params:
         p.update(params)
     k, alpha, T, tau, gamma = p["k"], p["alpha"], p["T"], p["tau"], p["gamma"]
+    t0 = perf_counter()
     P, idx = build_walk(topo_dict, X, p["K"], p["beta"], knn)
+    tm["build"] += perf_counter() - t0
+    t0 = perf_counter()
     n = P.topo.n
     if init_labels is None:
         y0, Vc, _ = init_bcm(P.topo, k, alpha, p["T_i"])
@@ -475,19 +485,26 @@ def ancka(topo_dict, X, params=None, knn=None, init_labels=None, warm=None, warm
         phi_w = cal_mhc(P, y_w, k, alpha, gamma)
         if phi_w <= phi_best:
             Q, y0, Y_best, phi_best, warm_used = Q_w, y_w, y_w.copy(), phi_w, True
+    tm["init"] += perf_counter() - t0
     phis = [phi_best]
     disc_iters = []
     taken = []
     t_run = 0
     for t in range(1, T + 1):
         Q_prev = Q
+        t0 = perf_counter()
         Z = P.apply(Q)                                # Eq. (zt)
         Q, _ = qr_pos(Z)
+        tm["iter"] += perf_counter() - t0
         t_run = t
         if t % tau == 0 or t == T:
+            t0 = perf_counter()
             y_t, objs, _ = discretize(Q[:, 1:], p["disc_max_iter"], return_trace=True)
+            tm["disc"] += perf_counter() - t0
             disc_iters.append(len(objs))
+            t0 = perf_counter()
             phi_t = cal_mhc(P, y_t, k, alpha, gamma)
+            tm["mhc"] += perf_counter() - t0
             phis.append(phi_t)
             take = phi_t < phi_best
             taken.append(bool(take))
