@@ -148,7 +148,10 @@ def knn_adjacency(X, idx):
     lo, hi = np.minimum(src, dst), np.maximum(src, dst)
     key, count = np.unique(lo * n + hi, return_counts=True)
     a, b = key // n, key % n
-    f = np.einsum("ij,ij->i", Xn[a], Xn[b])
+    f = np.empty(a.size)
+    for s in range(0, a.size, 1 << 18):       # pairs in chunks; each dot product is unchanged
+        e = min(a.size, s + (1 << 18))
+        f[s:e] = np.einsum("ij,ij->i", Xn[a[s:e]], Xn[b[s:e]])
     w = count * f
     A = sp.coo_matrix((np.concatenate([w, w]), (np.concatenate([a, b]), np.concatenate([b, a]))),
                       shape=(n, n)).tocsr()
@@ -188,6 +191,23 @@ def incidence_from_csr(n, he_ptr, he_nodes):
     H = sp.coo_matrix((np.ones(rows.size), (rows, np.asarray(he_nodes, np.int64))), shape=(m, n)).tocsr()
     H.data[:] = 1.0
     return H
+
+
+def spmm_rows(M, Q, blocks=32):
+    """M @ Q for a CSR matrix M and a dense Q, by row blocks in a thread pool:
+    every row of the result is the same sum, in the same order, as in M @ Q
+    (scipy releases the GIL inside the product)."""
+    n = M.shape[0]
+    if n < 100_000:
+        return M @ Q
+    from concurrent.futures import ThreadPoolExecutor
+    b = np.linspace(0, n, blocks + 1).astype(np.int64)
+    out = np.empty((n,) + Q.shape[1:], dtype=np.result_type(M.dtype, Q.dtype))
+    def run(i):
+        out[b[i]:b[i + 1]] = M[b[i]:b[i + 1]] @ Q
+    with ThreadPoolExecutor(min(blocks, 16)) as ex:
+        list(ex.map(run, range(blocks)))
+    return out
 
 
 def _inv_or_zero(v):
@@ -235,8 +255,8 @@ class Topology:
 
     def apply(self, Q):
         if self.kind == "hypergraph":
-            return self.P_V @ (self.P_E @ Q)          # Eq. (zt): P_V (P_E Q)
-        return self.P_N @ Q
+            return spmm_rows(self.P_V, spmm_rows(self.P_E, Q))   # Eq. (zt): P_V (P_E Q)
+        return spmm_rows(self.P_N, Q)
 
     def apply_T(self, Q):
         if self.kind == "hypergraph":
@@ -267,7 +287,7 @@ class WalkOperator:
         self.topo, self.P_K, self.b = topo, P_K, b
 
     def apply(self, Q):
-        return (1.0 - self.b)[:, None] * self.topo.apply(Q) + self.b[:, None] * (self.P_K @ Q)
+        return (1.0 - self.b)[:, None] * self.topo.apply(Q) + self.b[:, None] * spmm_rows(self.P_K, Q)
 
     def dense(self):
         return (1.0 - self.b)[:, None] * self.topo.dense() + self.b[:, None] * self.P_K.toarray()

@@ -255,8 +255,10 @@ struct Walk {
   Csr topo;         // graph/multiplex: merged layers; hypergraph: node -> hyperedges (H^T)
   Csr edges;        // hypergraph: hyperedge -> nodes (H)
   Csr knn;          // KNN part with values beta_i A_K[i,j] / D_K[i]
-  float* rs_topo = nullptr;     // n: (1 - beta_i) [/ delta_i for hypergraphs]
-  float* inv_deg = nullptr;     // hypergraph: n, 1/delta_v (0 if delta = 0)
+  float* rs_topo = nullptr;     // n: (1 - beta_i) [/ delta_i for hypergraphs and one-layer graphs]
+  float* inv_deg = nullptr;     // hypergraph, one-layer graph: n, 1/delta_v (0 if delta = 0)
+  bool row_uniform = false;     // one-layer graph: P_N = D^-1 A, so topo.val / valT are not
+                                // stored (row scale inv_deg[i], column scale inv_deg[j])
   float* inv_size = nullptr;    // hypergraph: m, 1/|e|
   int32_t* degree = nullptr;    // n: delta(v) used for V_c
   float* beta = nullptr;        // n: beta_i

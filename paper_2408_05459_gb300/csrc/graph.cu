@@ -168,8 +168,8 @@ __global__ void k_merge_layers(int L, int64_t n, const int64_t* const* __restric
     for (int64_t p = lptr[l][i]; p < lptr[l][i + 1]; ++p, ++o) {
       int32_t j = lcol[l][p];
       mcol[o] = j;
-      val[o] = wi;
-      valT[o] = deg[j] > 0 ? invL / (float)deg[j] : 0.f;  // deg[j] >= 1 for a symmetric A_l
+      if (val) val[o] = wi;
+      if (valT) valT[o] = deg[j] > 0 ? invL / (float)deg[j] : 0.f;  // deg[j] >= 1 for a symmetric A_l
     }
   }
 }
@@ -414,8 +414,15 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     w->topo.nrows = n;
     w->topo.nnz = tot;
     ANCKA_TRY(ws.alloc(&w->topo.col, (size_t)tot));
-    ANCKA_TRY(ws.alloc(&w->topo.val, (size_t)tot));
-    ANCKA_TRY(ws.alloc(&w->topo.valT, (size_t)tot));
+    if (L == 1) {  // D^-1 A: a row scale and a column scale replace the per-entry values
+      w->row_uniform = true;
+      ANCKA_TRY(ws.alloc(&w->inv_deg, (size_t)n));
+      k_inv_count<<<grid_for(n, 256), 256, 0, s>>>(w->degree, w->inv_deg, n);
+      ANCKA_LAUNCHED();
+    } else {
+      ANCKA_TRY(ws.alloc(&w->topo.val, (size_t)tot));
+      ANCKA_TRY(ws.alloc(&w->topo.valT, (size_t)tot));
+    }
     k_merge_layers<<<grid_for(n, 256), 256, 0, s>>>(L, n, dlptr, dlcol, dldeg, w->topo.ptr,
                                                     w->topo.col, w->topo.val, w->topo.valT);
     ANCKA_LAUNCHED();
@@ -462,7 +469,9 @@ ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* 
                                               c.col, c.val, zero_row, w->degree, beta, nb, w->beta);
   ANCKA_LAUNCHED();
   ANCKA_TRY(ws.alloc(&w->rs_topo, (size_t)n));
-  k_topo_rowscale<<<grid_for(n, 256), 256, 0, s>>>(w->beta, w->kind == ANCKA_HYPERGRAPH ? w->inv_deg : nullptr,
+  k_topo_rowscale<<<grid_for(n, 256), 256, 0, s>>>(w->beta,
+                                                   (w->kind == ANCKA_HYPERGRAPH || w->row_uniform) ? w->inv_deg
+                                                                                                   : nullptr,
                                                    n, w->rs_topo);
   ANCKA_LAUNCHED();
   return ANCKA_OK;

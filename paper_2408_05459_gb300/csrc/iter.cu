@@ -1612,7 +1612,7 @@ ancka_status apply_walk(const Ctx& c, const float* Q, int ld, float* Z, float co
   } else {
     a.ptrA = w.topo.ptr;
     a.colA = w.topo.col;
-    a.valA = w.topo.val;
+    a.valA = w.row_uniform ? nullptr : w.topo.val;  // one layer: 1/delta_i is inside rs_topo
     a.rsA = w.rs_topo;
     a.srcA = Q;
     a.srcA_rows = c.n;
@@ -1703,7 +1703,10 @@ ancka_status apply_topology(Workspace& ws, const Walk& w, const float* U, int ld
       a.srcA = E + c0;
       a.srcA_rows = w.m;
     } else {
-      a.valA = w.topo.val;
+      if (w.row_uniform)
+        a.rsA = w.inv_deg;
+      else
+        a.valA = w.topo.val;
       a.srcA = U + c0;
       a.srcA_rows = w.n;
     }
@@ -1757,7 +1760,10 @@ ancka_status initbcm_hop(const Ctx& c, const float* Pi, float* out, const int32_
   } else {
     a.ptrA = w.topo.ptr;
     a.colA = w.topo.col;
-    a.valA = w.topo.valT;
+    if (w.row_uniform)
+      a.csA = w.inv_deg;  // P_N^T entry (i, j) = 1/delta_j
+    else
+      a.valA = w.topo.valT;
     a.srcA = Pi;
     a.srcA_rows = c.n;
     a.ldA = c.ldk;

@@ -64,6 +64,7 @@ struct __align__(8) Bars {
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
+  int rot[2];  // key rotation of the current and the previous segment (written by the producer)
 };
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accum) {
@@ -200,7 +201,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
          int64_t n_pad, int64_t qblocks, int kb_count, int k_last, int nstages, int key_stride,
          float* __restrict__ cand_val,
          int32_t* __restrict__ cand_idx, const float* __restrict__ out_scale, float* __restrict__ part_val,
-         int32_t* __restrict__ part_idx, CollectArgs ca, int* __restrict__ err) {
+         int32_t* __restrict__ part_idx, CollectArgs ca, unsigned long long* __restrict__ tick,
+         int* __restrict__ err) {
   constexpr int kTK = kE4M3 ? 128 : 64;  // features per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -250,17 +252,27 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       uint32_t phase = 0;
       bool ok = true;
       int seg = 0;
+      uint32_t tiles_issued = 0;
       for (int64_t w = w_begin; w < w_end && ok; ++seg) {
         const int64_t qb = w / n_tiles;
         const int t0 = (int)(w - qb * n_tiles);
         const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
-        const int rot = key_rotation(qb, n_tiles, work, gridDim.x);
+        int rot = key_rotation(qb, n_tiles, work, gridDim.x);
         w += t1 - t0;
         // the previous block of A stays in use until its last MMA completes
         if (seg > 0 && !mbar_wait(&bars->a_empty, (uint32_t)((seg - 1) & 1), abort, err, 6)) {
           ok = false;
           break;
         }
+        // A block this CTA sweeps whole starts at the key tile the CTAs are
+        // reading now (tiles issued by all CTAs / CTAs), so that CTAs whose
+        // rates drift apart re-align at every block and keep sharing the key
+        // tiles in L2; a split block keeps the static rotation both of its
+        // CTAs can compute.
+        if (tick && t0 == 0 && t1 == n_tiles)
+          rot = (int)((*reinterpret_cast<volatile unsigned long long*>(tick) / gridDim.x) % (uint64_t)n_tiles);
+        bars->rot[seg & 1] = rot;
+        __threadfence_block();
         mbar_expect_tx(&bars->a_full, (uint32_t)(kb_count * kABytes));
         for (int kb = 0; kb < kb_count; ++kb)
           tma_load_2d(smem_u32(sA + kb * kABytes), &tmA, kb * kTK, (int)(qb * kTM), &bars->a_full);
@@ -281,6 +293,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
               phase ^= 1;
             }
           }
+          if (tick && ((++tiles_issued) & 15) == 0) atomicAdd(tick, 16ull);
         }
       }
       if (!ok) {  // drain this warp's copies still in flight (bounded)
@@ -364,7 +377,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       const int64_t qb = w / n_tiles;
       const int t0 = (int)(w - qb * n_tiles);
       const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
-      const int rot = key_rotation(qb, n_tiles, work, gridDim.x);
+      int rot = 0;
       w += t1 - t0;
       // A row ra is query row ra, or compact row ra -> global row a_rows[ra]
       const int64_t ra = qb * kTM + r;
@@ -387,6 +400,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           break;
         }
         tc_fence_after();
+        // the producer wrote the segment's rotation before loading its block
+        // of A, which the first accumulator of the segment waited for
+        if (t == t0) rot = *reinterpret_cast<volatile int*>(&bars->rot[seg & 1]);
         const int kt = (t + rot < n_tiles ? t + rot : t + rot - n_tiles) * key_stride;
         const int64_t jb = (int64_t)kt * kTN + h * kSliceN;
         const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * kSliceN);
@@ -436,11 +452,13 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   }
 }
 
-// Lists of the query blocks split between CTAs: per row and column half, the
+// Lists of the query blocks split between runs: per row and column half, the
 // 16 best of the pieces' lists (each piece holds the best of its own key
-// tiles, so the result is the best of the whole half).  One CTA of kTM
-// threads per query block; blocks that one CTA covered return at once.
-__global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, int64_t ctas,
+// tiles, so the result is the best of the whole half).  One CTA of RB
+// threads per query block of RB rows (RB = 128: runs of single CTAs, 256:
+// runs of CTA pairs); blocks that one run covered return at once.
+template <int RB>
+__global__ void __launch_bounds__(RB) k_merge_lists(int n_tiles, int64_t work, int64_t ctas,
                                                      const float* __restrict__ part_val,
                                                      const int32_t* __restrict__ part_idx,
                                                      const int32_t* __restrict__ a_rows, int64_t n_rows,
@@ -450,7 +468,7 @@ __global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, 
   const int64_t c0 = ((x0 + 1) * ctas + work - 1) / work - 1;  // the CTA whose range holds x0
   if (range_begin(c0 + 1, work, ctas) >= x1) return;
   const int r = threadIdx.x;
-  const int64_t ra = qb * kTM + r;
+  const int64_t ra = qb * RB + r;
   if (ra >= n_rows) return;
   const int64_t i = a_rows ? (int64_t)a_rows[ra] : ra;
   constexpr int C = kListC;
@@ -465,7 +483,7 @@ __global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, 
     for (int64_t cc = c0; cc < ctas; ++cc) {
       const int64_t b = range_begin(cc, work, ctas);
       if (b >= x1) break;
-      const int64_t slot = (cc * 2 + (b / n_tiles == qb ? 0 : 1)) * kTM + r;
+      const int64_t slot = (cc * 2 + (b / n_tiles == qb ? 0 : 1)) * RB + r;
       for (int e = 0; e < C; ++e) {
         const int32_t j = part_idx[slot * kCandC + h * C + e];
         const float v = part_val[slot * kCandC + h * C + e];
@@ -947,14 +965,16 @@ ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& 
     ANCKA_TRY(ws.alloc(&part_val, (size_t)ctas * 2 * kTM * kCandC));
     ANCKA_TRY(ws.alloc(&part_idx, (size_t)ctas * 2 * kTM * kCandC));
   }
+  unsigned long long* tick = nullptr;  // tiles issued by all CTAs (re-aligns whole blocks' key order)
+  if (key_stride == 1) ANCKA_TRY(ws.zeros(&tick, 1));
   ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<kCollect, kE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_knn_tc<kCollect, kE4M3><<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, n_pad, qblocks, kb_count, k_last,
                                                                    nstages, key_stride, cand_val, cand_idx,
-                                                                   out_scale, part_val, part_idx, ca, err);
+                                                                   out_scale, part_val, part_idx, ca, tick, err);
   ANCKA_LAUNCHED();
   if (!kCollect) {
-    k_merge_lists<<<(unsigned)qblocks, kTM, 0, s>>>(n_tiles, work, ctas, part_val, part_idx, ca.a_rows, n_rows,
-                                                    cand_val, cand_idx);
+    k_merge_lists<kTM><<<(unsigned)qblocks, kTM, 0, s>>>(n_tiles, work, ctas, part_val, part_idx, ca.a_rows,
+                                                         n_rows, cand_val, cand_idx);
     ANCKA_LAUNCHED();
   }
   return ANCKA_OK;
