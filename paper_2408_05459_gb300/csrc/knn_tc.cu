@@ -160,12 +160,47 @@ __device__ __forceinline__ void collect_chunk(const uint32_t (&r)[32], float mx,
 
 struct CollectArgs {
   const int32_t* a_rows;  // global row of each compact query row (null: A holds rows 0..n-1)
-  int64_t n_a;            // compact query rows
+  int64_t n_a;            // compact query rows (0: as many as keys)
   const float* thr;       // collect mode: per compact row threshold
   int32_t* cnt;           // collect mode: per compact row counter
   int32_t* buf;           // collect mode: n_a x cap keys
   int cap;
+  // tile-list mode (null: every block sweeps every key tile): query block qb
+  // sweeps the key tiles blk_tiles[blk_ptr[qb] .. blk_ptr[qb + 1])
+  const int64_t* blk_ptr = nullptr;
+  const int32_t* blk_tiles = nullptr;
+  int64_t blk_work = 0;   // blk_ptr[qblocks]
+  int no_self = 0;        // the keys are another set (no row excludes "itself")
 };
+
+// The segment of query block qb that a run [w, w_end) covers from w:
+// positions [t0, t1) of the block's len key tiles.
+struct Seg {
+  int64_t qb;
+  int t0, t1, len;
+  int64_t base;  // tile-list mode: offset of the block's tiles
+};
+__device__ __forceinline__ Seg segment_at(int64_t w, int64_t w_end, int n_tiles, int64_t qblocks,
+                                          const CollectArgs& ca) {
+  Seg sg;
+  if (ca.blk_ptr) {
+    int64_t lo = 0, hi = qblocks;  // the last qb with blk_ptr[qb] <= w
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ca.blk_ptr[mid] <= w) lo = mid; else hi = mid;
+    }
+    sg.qb = lo;
+    sg.base = ca.blk_ptr[lo];
+    sg.len = (int)(ca.blk_ptr[lo + 1] - sg.base);
+  } else {
+    sg.qb = w / n_tiles;
+    sg.base = sg.qb * n_tiles;
+    sg.len = n_tiles;
+  }
+  sg.t0 = (int)(w - sg.base);
+  sg.t1 = (int)(w_end - w < (int64_t)(sg.len - sg.t0) ? sg.t0 + (w_end - w) : sg.len);
+  return sg;
+}
 
 // Work split (stream-K): the (query block, key tile) pairs, numbered
 // qb * n_tiles + t, are cut into gridDim.x equal contiguous ranges, one per
@@ -211,7 +246,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   Bars* bars = reinterpret_cast<Bars*>(sB + nstages * kBBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = (int)ceil_div(ceil_div(n_pad, kTN), key_stride);
-  const int64_t work = qblocks * n_tiles;
+  const int64_t work = ca.blk_ptr ? ca.blk_work : qblocks * n_tiles;
   const int64_t w_begin = range_begin(blockIdx.x, work, gridDim.x);
   const int64_t w_end = range_begin((int64_t)blockIdx.x + 1, work, gridDim.x);
   volatile int* abort = &bars->abort;
@@ -254,10 +289,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       int seg = 0;
       uint32_t tiles_issued = 0;
       for (int64_t w = w_begin; w < w_end && ok; ++seg) {
-        const int64_t qb = w / n_tiles;
-        const int t0 = (int)(w - qb * n_tiles);
-        const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
-        int rot = key_rotation(qb, n_tiles, work, gridDim.x);
+        const Seg sg = segment_at(w, w_end, n_tiles, qblocks, ca);
+        const int64_t qb = sg.qb;
+        const int t0 = sg.t0, t1 = sg.t1;
+        int rot = ca.blk_ptr ? 0 : key_rotation(qb, n_tiles, work, gridDim.x);
         w += t1 - t0;
         // the previous block of A stays in use until its last MMA completes
         if (seg > 0 && !mbar_wait(&bars->a_empty, (uint32_t)((seg - 1) & 1), abort, err, 6)) {
@@ -269,7 +304,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         // rates drift apart re-align at every block and keep sharing the key
         // tiles in L2; a split block keeps the static rotation both of its
         // CTAs can compute.
-        if (tick && t0 == 0 && t1 == n_tiles)
+        if (tick && !ca.blk_ptr && t0 == 0 && t1 == n_tiles)
           rot = (int)((*reinterpret_cast<volatile unsigned long long*>(tick) / gridDim.x) % (uint64_t)n_tiles);
         bars->rot[seg & 1] = rot;
         __threadfence_block();
@@ -284,7 +319,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             }
             pending[stage] = false;
             mbar_expect_tx(&bars->full[stage], (uint32_t)kBBytes);
-            const int kt = (t + rot < n_tiles ? t + rot : t + rot - n_tiles) * key_stride;
+            const int kt = ca.blk_ptr ? ca.blk_tiles[sg.base + t]
+                                      : (t + rot < n_tiles ? t + rot : t + rot - n_tiles) * key_stride;
             tma_load_2d(smem_u32(sB + stage * kBBytes), &tmB, kb * kTK, kt * kTN, &bars->full[stage]);
             pending[stage] = true;
             pend_par[stage] = phase;
@@ -311,9 +347,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       int64_t g = 0;  // accumulator tiles so far (ping-pong over two)
       int seg = 0;
       for (int64_t w = w_begin; w < w_end && ok; ++seg) {
-        const int64_t qb = w / n_tiles;
-        const int t0 = (int)(w - qb * n_tiles);
-        const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
+        const Seg sg = segment_at(w, w_end, n_tiles, qblocks, ca);
+        const int t0 = sg.t0, t1 = sg.t1;
         w += t1 - t0;
         if (!mbar_wait(&bars->a_full, (uint32_t)(seg & 1), abort, err, 2)) {
           ok = false;
@@ -374,15 +409,16 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     int seg = 0;
     bool ok = true;
     for (int64_t w = w_begin; w < w_end && ok; ++seg) {
-      const int64_t qb = w / n_tiles;
-      const int t0 = (int)(w - qb * n_tiles);
-      const int t1 = (int)(w_end - w < (int64_t)(n_tiles - t0) ? t0 + (w_end - w) : n_tiles);
+      const Seg sg = segment_at(w, w_end, n_tiles, qblocks, ca);
+      const int64_t qb = sg.qb;
+      const int t0 = sg.t0, t1 = sg.t1;
       int rot = 0;
       w += t1 - t0;
       // A row ra is query row ra, or compact row ra -> global row a_rows[ra]
       const int64_t ra = qb * kTM + r;
-      const bool row_ok = ca.a_rows ? (ra < ca.n_a) : (ra < n);
+      const bool row_ok = ra < (ca.n_a > 0 ? ca.n_a : n);
       const int64_t i = ca.a_rows ? (row_ok ? (int64_t)ca.a_rows[ra] : -1) : ra;
+      const int64_t i_self = ca.no_self ? -1 : i;  // the key index this row excludes
       const float t_row = kCollect && row_ok ? ca.thr[ra] : INFINITY;
       float lv[C];
       int32_t li[C];
@@ -403,9 +439,12 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         // the producer wrote the segment's rotation before loading its block
         // of A, which the first accumulator of the segment waited for
         if (t == t0) rot = *reinterpret_cast<volatile int*>(&bars->rot[seg & 1]);
-        const int kt = (t + rot < n_tiles ? t + rot : t + rot - n_tiles) * key_stride;
+        const int kt = ca.blk_ptr ? ca.blk_tiles[sg.base + t]
+                                  : (t + rot < n_tiles ? t + rot : t + rot - n_tiles) * key_stride;
         const int64_t jb = (int64_t)kt * kTN + h * kSliceN;
         const uint32_t tb = lane_base + (uint32_t)(b * kTN + h * kSliceN);
+        // the hardware's maximum over each 32-column load settles most
+        // chunks with one compare and one vote
 #pragma unroll 1
         for (int c = 0; c < kSliceN / 32; ++c) {
           uint32_t rv[32];
@@ -415,9 +454,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           pin(rv);
           pin1(mx);
           if constexpr (kCollect) {
-            collect_chunk(rv, mx, jb + c * 32, n, i, t_row, ra, ca.cnt, ca.buf, ca.cap);
+            collect_chunk(rv, mx, jb + c * 32, n, i_self, t_row, ra, ca.cnt, ca.buf, ca.cap);
           } else {
-            fold_chunk<C>(rv, mx, jb + c * 32, n, i, lv, li);
+            fold_chunk<C>(rv, mx, jb + c * 32, n, i_self, lv, li);
           }
         }
         tc_fence_before();
@@ -427,7 +466,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       if (!kCollect && ok) {
         float* ov;
         int32_t* oi;
-        if (t0 == 0 && t1 == n_tiles) {  // whole block: final lists
+        if (t0 == 0 && t1 == sg.len) {  // whole block: final lists
           if (!row_ok) continue;
           ov = cand_val + i * kCandC;
           oi = cand_idx + i * kCandC;
@@ -454,24 +493,34 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
 
 // Lists of the query blocks split between runs: per row and column half, the
 // 16 best of the pieces' lists (each piece holds the best of its own key
-// tiles, so the result is the best of the whole half).  One CTA of RB
-// threads per query block of RB rows (RB = 128: runs of single CTAs, 256:
-// runs of CTA pairs); blocks that one run covered return at once.
-template <int RB>
-__global__ void __launch_bounds__(RB) k_merge_lists(int n_tiles, int64_t work, int64_t ctas,
+// tiles, so the result is the best of the whole half).  One CTA of kTM
+// threads per query block; blocks that one run covered return at once.
+// Block qb's work items are [x0, x1) = [qb n_tiles, (qb + 1) n_tiles), or
+// [blk_ptr[qb], blk_ptr[qb + 1]) in tile-list mode (a block with no tiles
+// gets empty lists).
+__global__ void __launch_bounds__(kTM) k_merge_lists(int n_tiles, int64_t work, int64_t ctas,
+                                                     const int64_t* __restrict__ blk_ptr,
                                                      const float* __restrict__ part_val,
                                                      const int32_t* __restrict__ part_idx,
                                                      const int32_t* __restrict__ a_rows, int64_t n_rows,
                                                      float* __restrict__ cand_val, int32_t* __restrict__ cand_idx) {
   const int64_t qb = blockIdx.x;
-  const int64_t x0 = qb * n_tiles, x1 = x0 + n_tiles;
-  const int64_t c0 = ((x0 + 1) * ctas + work - 1) / work - 1;  // the CTA whose range holds x0
-  if (range_begin(c0 + 1, work, ctas) >= x1) return;
+  const int64_t x0 = blk_ptr ? blk_ptr[qb] : qb * n_tiles;
+  const int64_t x1 = blk_ptr ? blk_ptr[qb + 1] : x0 + n_tiles;
   const int r = threadIdx.x;
-  const int64_t ra = qb * RB + r;
+  const int64_t ra = qb * kTM + r;
   if (ra >= n_rows) return;
   const int64_t i = a_rows ? (int64_t)a_rows[ra] : ra;
   constexpr int C = kListC;
+  if (x0 == x1) {
+    for (int e = 0; e < kCandC; ++e) {
+      cand_val[i * kCandC + e] = -INFINITY;
+      cand_idx[i * kCandC + e] = -1;
+    }
+    return;
+  }
+  const int64_t c0 = ((x0 + 1) * ctas + work - 1) / work - 1;  // the CTA whose range holds x0
+  if (range_begin(c0 + 1, work, ctas) >= x1) return;
   for (int h = 0; h < kLists; ++h) {
     float lv[C];
     int32_t li[C];
@@ -483,7 +532,7 @@ __global__ void __launch_bounds__(RB) k_merge_lists(int n_tiles, int64_t work, i
     for (int64_t cc = c0; cc < ctas; ++cc) {
       const int64_t b = range_begin(cc, work, ctas);
       if (b >= x1) break;
-      const int64_t slot = (cc * 2 + (b / n_tiles == qb ? 0 : 1)) * RB + r;
+      const int64_t slot = (cc * 2 + (b >= x0 ? 0 : 1)) * kTM + r;  // run cc starts inside the block: its first segment
       for (int e = 0; e < C; ++e) {
         const int32_t j = part_idx[slot * kCandC + h * C + e];
         const float v = part_val[slot * kCandC + h * C + e];
@@ -957,8 +1006,8 @@ ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& 
   ANCKA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t qblocks = ceil_div(n_rows, kTM);
   const int n_tiles = (int)ceil_div(ceil_div(n_pad, kTN), key_stride);
-  const int64_t work = qblocks * n_tiles;
-  const int64_t ctas = std::min<int64_t>(sms, work);
+  const int64_t work = ca.blk_ptr ? ca.blk_work : qblocks * n_tiles;
+  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(sms, work));
   float* part_val = nullptr;
   int32_t* part_idx = nullptr;
   if (!kCollect) {
@@ -966,15 +1015,15 @@ ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& 
     ANCKA_TRY(ws.alloc(&part_idx, (size_t)ctas * 2 * kTM * kCandC));
   }
   unsigned long long* tick = nullptr;  // tiles issued by all CTAs (re-aligns whole blocks' key order)
-  if (key_stride == 1) ANCKA_TRY(ws.zeros(&tick, 1));
+  if (key_stride == 1 && !ca.blk_ptr) ANCKA_TRY(ws.zeros(&tick, 1));
   ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<kCollect, kE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_knn_tc<kCollect, kE4M3><<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, n_pad, qblocks, kb_count, k_last,
                                                                    nstages, key_stride, cand_val, cand_idx,
                                                                    out_scale, part_val, part_idx, ca, tick, err);
   ANCKA_LAUNCHED();
   if (!kCollect) {
-    k_merge_lists<kTM><<<(unsigned)qblocks, kTM, 0, s>>>(n_tiles, work, ctas, part_val, part_idx, ca.a_rows,
-                                                         n_rows, cand_val, cand_idx);
+    k_merge_lists<<<(unsigned)qblocks, kTM, 0, s>>>(n_tiles, work, ctas, ca.blk_ptr, part_val, part_idx, ca.a_rows,
+                                                    n_rows, cand_val, cand_idx);
     ANCKA_LAUNCHED();
   }
   return ANCKA_OK;
@@ -1106,6 +1155,37 @@ ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n,
   CollectArgs ca{rows, n_a, nullptr, nullptr, nullptr, 0};
   return launch_tc<false, false>(ws, ta, tb, n, pr.n_pad, n_a, kb_count, pr.d, cand_val, cand_idx, nullptr, ca, err,
                                  s);
+}
+
+ancka_status knn_lists_bf16(Workspace& ws, const __nv_bfloat16* a, int64_t a_rows_total, const int32_t* rows,
+                           int64_t n_rows, const __nv_bfloat16* keys, int64_t n_keys, int64_t keys_pad, int dp, int d,
+                           const int64_t* blk_ptr, const int32_t* blk_tiles, int64_t blk_work, bool no_self,
+                           float* cand_val, int32_t* cand_idx, int32_t* err, cudaStream_t s) {
+  const int kb_count = dp / 64;
+  if (dp % 64 != 0 || kb_count < 1 || dp > knn_tc_max_dp()) {
+    set_error("BF16 contraction supports up to %d features (got %d)", knn_tc_max_dp(), dp);
+    return ANCKA_ERR_UNSUPPORTED;
+  }
+  CUtensorMap ta, tb;
+  if (rows) {
+    const int64_t n_a_pad = round_up(n_rows, kTM);
+    __nv_bfloat16* af;
+    ANCKA_TRY(ws.alloc(&af, (size_t)n_a_pad * dp));
+    k_gather_rows<<<(unsigned)n_a_pad, 64, 0, s>>>(reinterpret_cast<const uint8_t*>(a), dp * 2, rows, n_rows,
+                                                   n_a_pad, reinterpret_cast<uint8_t*>(af));
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(make_map(&ta, af, dp, n_a_pad, kTM, 2));
+  } else {
+    ANCKA_TRY(make_map(&ta, a, dp, round_up(a_rows_total, kTM), kTM, 2));
+  }
+  ANCKA_TRY(make_map(&tb, keys, dp, keys_pad, kTN, 2));
+  CollectArgs ca{rows, n_rows, nullptr, nullptr, nullptr, 0};
+  ca.blk_ptr = blk_ptr;
+  ca.blk_tiles = blk_tiles;
+  ca.blk_work = blk_work;
+  ca.no_self = no_self ? 1 : 0;
+  return launch_tc<false, false>(ws, ta, tb, n_keys, keys_pad, n_rows, kb_count, d, cand_val, cand_idx, nullptr, ca,
+                                 err, s);
 }
 
 ancka_status knn_collect_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,

@@ -94,6 +94,32 @@ def test_odd_k_and_ragged_sizes(ak):
     _check(ak, g, "fp32", k=7, T=7, tau=3, gamma=2, T_i=9, K=5)
 
 
+def test_negative_knn_degree_nodes(ak):
+    """Reading R3 on the GPU: two nodes whose attributes point away from both
+    attribute clusters (and from each other) have negative cosines to all
+    their KNN entries, a negative KNN degree D_K, and so a zero P_K row and
+    beta_i = 0; the labels, the block and the phi trace must still match the
+    oracle's."""
+    rng = np.random.default_rng(31)
+    n, k = 400, 2
+    lab = rng.integers(0, k, n)
+    X = np.zeros((n, 6))
+    X[np.arange(n), lab] = 1.0
+    X += 0.15 * rng.standard_normal((n, 6))
+    out = np.array([n - 2, n - 1])
+    X[out] = np.array([[-1.0, -1.0, 2.0, 0, 0, 0], [-1.0, -1.0, -2.0, 0, 0, 0]]) + 0.02 * rng.standard_normal((2, 6))
+    src = rng.integers(0, n, 3000)                  # 80% of the edges inside a cluster
+    same = rng.random(3000) < 0.8
+    members = [np.nonzero(lab == c)[0] for c in range(k)]
+    dst = np.where(same, [rng.choice(members[lab[v]]) for v in src], rng.integers(0, n, 3000))
+    rp, col = synth.csr_from_edges(n, src, dst, symmetric=True)
+    g = dict(kind="graph", n=n, k=k, X=X.astype(np.float32), labels=lab, layers=[(rp, col)])
+    idx, _ = O.knn_cosine(g["X"], 10)
+    _, D = O.knn_transition(O.knn_adjacency(g["X"], idx))
+    assert np.all(D[out] < 0) and np.all(D[: n - 2] > 0)   # the case does exercise R3
+    _check(ak, g, "fp32", k=k)
+
+
 def test_cliques_closed_form_on_gpu(ak):
     k, c = 5, 24
     g = synth.cliques_closed_form(k, c, seed=7)
@@ -199,6 +225,45 @@ def test_multiplex_workload_with_verified_knn(ak):
     assert np.array_equal(ex["init_labels"], o["init_labels"])
     ari, ang = compare_iteration(o, labels, ex["Q"])
     assert ang <= ANGLE_MAX and ari >= ARI_MIN, (ari, ang)
+
+
+def _dcsbm_oracle_parity(ak, n, sample_rows):
+    """The DC-SBM generator with the large workload's settings (k = 47
+    Zipf-sized clusters, d = 100, 25 n edges, beta = 0.4, T_i = 1, T = 10,
+    BF16 KNN) at n nodes: the GPU's KNN exact on sampled rows, then the
+    oracle's Algorithm 4 on the same lists against the GPU's InitBCM labels,
+    final block (all k+1 columns), labels and phi trace."""
+    g = synth.config_large_dcsbm(0, n=n, m_edges=25 * n)
+    k = 47
+    labels, ex, info = _gpu_cluster(ak, g, "bf16", k=k, beta=0.4, T_i=1)
+    rows = np.random.default_rng(4).choice(n, sample_rows, replace=False)
+    compare_knn(g["X"], 10, rows, ex["knn_idx"], ex["knn_sim"])
+    p = _params(ak, k=k, beta=0.4, T_i=1)
+    o = O.ancka(g, g["X"], _oracle_params(p), knn=ex["knn_idx"])
+    assert np.array_equal(ex["init_labels"], o["init_labels"])
+    ari, ang = compare_iteration(o, labels, ex["Q"])
+    assert ang <= ANGLE_MAX and ari >= ARI_MIN, (ari, ang)
+    # phi(Y0) and the last Discretize's phi within 1e-4; the check point at
+    # t = 5, where the block is still far from converged, within 5e-3:
+    # there Discretize (k = 47) is ill-conditioned -- the oracle's own labels
+    # at t = 5 move to ARI 0.73 and its phi by 3e-3 when its FP64 block is
+    # merely rounded to FP32 (measured at n = 6e5)
+    ph = np.asarray(info["phi"][:info["n_phi"]])
+    assert ph.size == len(o["phi"])
+    assert abs(ph[0] - o["phi"][0]) <= 1e-4 and abs(ph[-1] - o["phi"][-1]) <= 1e-4, (ph, o["phi"])
+    assert np.all(np.abs(ph - o["phi"]) <= 5e-3), (ph, o["phi"])
+    return ari, ang
+
+
+def test_dcsbm_workload_oracle_parity_600k(ak):
+    """A quarter of the large workload (n = 6e5)."""
+    _dcsbm_oracle_parity(ak, 600_000, 64)
+
+
+def test_dcsbm_workload_oracle_parity_full_size(ak):
+    """The full large workload (n = 2.4e6, 6e7 edges; the oracle's iteration
+    takes about two minutes on the host cores)."""
+    _dcsbm_oracle_parity(ak, 2_400_000, 48)
 
 
 def test_large_dcsbm_workload_properties(ak):

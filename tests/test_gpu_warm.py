@@ -152,3 +152,64 @@ def test_warm_invalid_arguments(ak):
     with pytest.raises(ak.AnckaError) as e:             # k of the model != clusters
         ak.cluster(ak.topology_to_device(g), X, p, warm=_dev(synth.warm_init(0, 96, 256, g["k"])))
     assert e.value.status == 1
+
+
+def test_learned_start_gains_over_initbcm(ak):
+    """What the trained network gains over the method without it.  The MLP
+    is trained on ANCKA's own blocks of eight DC-SBM graphs (n = 2e4, k = 10,
+    d = 64, T_i = 1 and beta = 0.4 as for the large graphs, where InitBCM's
+    single hop from the k hubs leaves most nodes in one cluster), then four
+    held-out graphs of the same generator are clustered from InitBCM's start
+    and from the learned one:
+      - the learned start is taken (its Phi is lower than InitBCM's) on every
+        graph;
+      - with a budget of five hops (one Discretize) the kept Phi is never
+        higher and the labels agree better with the planted partition;
+      - in the paper's early-termination mode (Eq. tcond-1/2) the learned
+        start needs fewer hops in total, at a Phi no higher on any graph;
+      - on the first graph the oracle, given the same weights, takes the same
+        start and reaches the same labels and block."""
+    k, d = 10, 64
+    items = []
+    for seed in range(100, 108):
+        g = synth.dcsbm_graph(20000, k, 500000, d, 1.5, seed)
+        td = ak.topology_to_device(g)
+        X = torch.as_tensor(g["X"], device="cuda")
+        p = ak.default_params(k=k, K=10, T=10, T_i=1, beta=0.4, knn_prec="bf16")
+        _, ex, _ = ak.cluster(td, X, p, want_Q=True, with_info=False)
+        items.append((td, X, ex["Q"][:, 1:].contiguous()))
+    w = _dev(synth.warm_init(0, 2 * d, 256, k))
+    losses = ak.warm_train(items, w, 60, 1e-3, 1e-2)
+    torch.cuda.synchronize()
+    assert losses[-1] < 0.5 * losses[0]
+    hops = {"plain": 0, "learned": 0}
+    ari5 = {"plain": [], "learned": []}
+    for seed in (200, 201, 202, 203):
+        g = synth.dcsbm_graph(20000, k, 500000, d, 1.5, seed)
+        td = ak.topology_to_device(g)
+        X = torch.as_tensor(g["X"], device="cuda")
+        res = {}
+        for mode in ("plain", "learned"):
+            r = {}
+            for tag, kw in (("paper", dict(T=100, early_stop=1, eps_Q=0.005)), ("T5", dict(T=5))):
+                p = ak.default_params(k=k, K=10, T_i=1, beta=0.4, tau=5, knn_prec="bf16", **kw)
+                lab, _, info = ak.cluster(td, X, p, warm=w if mode == "learned" else None)
+                torch.cuda.synchronize()
+                r[tag] = (info["iters_run"], info["phi"][0], info["phi_best"],
+                          O.adjusted_rand_index(lab.cpu().numpy(), g["labels"]), info["warm_used"])
+            res[mode] = r
+            hops[mode] += r["paper"][0]
+            ari5[mode].append(r["T5"][3])
+        assert res["learned"]["T5"][4] == 1 and res["learned"]["T5"][1] < res["plain"]["T5"][1], res
+        assert res["learned"]["T5"][2] <= res["plain"]["T5"][2] + 1e-5, res
+        assert res["learned"]["paper"][2] <= res["plain"]["paper"][2] + 1e-4, res
+        if seed == 200:
+            p = ak.default_params(k=k, K=10, T=5, T_i=1, beta=0.4, tau=5, knn_prec="bf16")
+            labels, ex, info = ak.cluster(td, X, p, want_Q=True, want_knn=True, warm=w)
+            torch.cuda.synchronize()
+            o = O.ancka(g, g["X"], _oracle_params(p), knn=ex["knn_idx"].cpu().numpy(), warm=_host(w))
+            assert info["warm_used"] == 1 and bool(o["warm_used"])
+            ari, ang = compare_iteration(o, labels.cpu().numpy(), ex["Q"].cpu().numpy())
+            assert ari >= ARI_MIN and ang <= ANGLE_MAX, (ari, ang)
+    assert hops["learned"] < hops["plain"], hops
+    assert np.mean(ari5["learned"]) > np.mean(ari5["plain"]), ari5

@@ -177,6 +177,37 @@ def test_beta_rule_and_row_stochastic_P():
     assert np.allclose(rows, 1.0)
 
 
+def test_negative_knn_degree_reading_r3():
+    """Reading R3 worked by hand on six nodes (Eq. AK with negative cosines):
+    node 0 points away from everyone, so its K = 2 nearest are node 5
+    (cos = -0.2/sqrt(1.04)) and node 3 (cos = -1/sqrt(1.09), tied with node 4,
+    lowest index kept); no node lists node 0, so D_K[0] = -0.196 - 0.958 < 0
+    and node 0 gets a zero P_K row and beta_0 = 0, while every other row of
+    P_K still sums to 1 (its degree is positive)."""
+    X = np.array([[1.0, 0.0], [-1.0, 0.1], [-1.0, -0.1], [-1.0, 0.3], [-1.0, -0.3], [-0.2, 1.0]])
+    idx, _ = O.knn_cosine(X, 2)
+    assert idx[0].tolist() == [5, 3]
+    assert idx[5].tolist() == [3, 1] and 0 not in idx[1:].ravel()
+    A = O.knn_adjacency(X, idx).toarray()
+    f05, f03 = -0.2 / math.sqrt(1.04), -1.0 / math.sqrt(1.09)
+    assert A[0, 5] == pytest.approx(f05, abs=1e-15) and A[5, 0] == pytest.approx(f05, abs=1e-15)
+    assert A[0, 3] == pytest.approx(f03, abs=1e-15) and A[0, [1, 2, 4]].tolist() == [0.0, 0.0, 0.0]
+    P_K, D = O.knn_transition(O.knn_adjacency(X, idx))
+    assert D[0] == pytest.approx(f05 + f03, abs=1e-15) and D[0] < 0
+    P_K = P_K.toarray()
+    assert np.all(P_K[0] == 0.0)                      # not D_K^-1 A_K: that row would be positive
+    assert np.all(D[1:] > 0) and np.allclose(P_K[1:].sum(axis=1), 1.0)
+    b = O.beta_vector(X, np.ones(6), 0.5, D)
+    assert b[0] == 0.0 and np.all(b[1:] == 0.5)
+    # the walk of node 0 is then its topology walk alone
+    row_ptr = np.array([0, 1, 2, 3, 4, 5, 6], np.int64)
+    col = np.array([1, 0, 3, 2, 5, 4], np.int32)
+    P, _ = O.build_walk(dict(kind="graph", n=6, layers=[(row_ptr, col)]), X, K=2, beta=0.5, knn=idx)
+    Pd = P.dense()
+    assert Pd[0].tolist() == [0.0, 1.0, 0.0, 0.0, 0.0, 0.0]
+    assert np.allclose(Pd.sum(axis=1), 1.0)
+
+
 def test_knn_transition_row_stochastic():
     X = np.abs(np.random.default_rng(9).standard_normal((40, 6)))  # positive cosines
     idx, _ = O.knn_cosine(X, 5)
