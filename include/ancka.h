@@ -127,6 +127,9 @@ typedef struct {
                             points (the paper's mode, T = T_a up to 1000); 0: run T (0) */
   float eps_Q;           /* Eq. tcond-1 threshold on ||Q(t) - Q(t-1)||_F (0.005) */
   const ancka_warm_model* warm;  /* init = 2: the MLP (device weights) */
+  int32_t knn_nlist;     /* 0: exact KNN lists (default); > 0: approximate lists from
+                            nlist inverted-list cells, as ancka_knn_ivf (BF16 only) */
+  int32_t knn_nprobe;    /* cells probed per row when knn_nlist > 0 (1 <= nprobe <= min(32, nlist)) */
 } ancka_params;
 
 /* Optional device outputs (any field may be NULL). */
@@ -164,6 +167,8 @@ typedef struct {
   float ms_spmm;               /* the T products Z = P Q of the orthogonal iteration (inside ms_iter) */
   int32_t warm_used;           /* init = 2: 1 if the warm start replaced InitBCM's (lower or equal Phi) */
   int32_t pad2_;
+  int64_t knn_tiles;           /* approximate KNN: (query block, key tile) pairs multiplied */
+  int64_t knn_full_tiles;      /* approximate KNN: the same for the exact sweep */
 } ancka_info;
 
 /* Fill *p with the defaults above. */
@@ -206,6 +211,27 @@ void ancka_set_symmetric_knn_min_rows(int64_t n_min);
  * Requires 1 <= K <= 64, K < n, 1 <= d <= 4096, n < 2^31. */
 ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t prec,
                        int32_t* out_idx, float* out_sim, ancka_info* info, void* stream);
+
+/* Approximate KNN lists by inverted lists: the large-graph variant of the
+ * paper's KNN construction (Section 7 builds the KNN graph with Faiss IVFPQ
+ * when n >= 100k; here the codes are the BF16 unit rows themselves and the
+ * final ranking is exact).  The unit rows are partitioned into nlist cells by
+ * spherical k-means (8 rounds on min(n, 64 nlist) evenly spaced rows,
+ * assignment by the tcgen05 BF16 contraction against the centroids, seeded
+ * initial centroids), every row probes its nprobe nearest cells, the BF16
+ * contraction scores it against the rows of the probed cells only (plus its
+ * own 256-row key tile), and the 32 best candidates are re-ranked by their
+ * exact FP32 cosine.  The lists are valid KNN lists (K distinct other rows,
+ * ordered by cosine desc, index asc) but not necessarily the exact N_K: the
+ * recall against ancka_knn is the quality measure.  Deterministic for fixed
+ * inputs.
+ *   X        n x d FP32 (device); d <= 512
+ *   out_idx  n x K int32, out_sim n x K FP32 (device, caller-owned)
+ *   info     may be NULL; fills ms_knn, knn_tiles and knn_full_tiles
+ * Requires 1 <= K <= 16, K < n, 1 <= nlist <= min(n, 8192),
+ * 1 <= nprobe <= min(32, nlist), n <= 16.7e6. */
+ancka_status ancka_knn_ivf(const float* X, int64_t n, int32_t d, int32_t K, int32_t nlist, int32_t nprobe,
+                           int32_t* out_idx, float* out_sim, ancka_info* info, void* stream);
 
 /* Diagnostic, not part of the method: the candidate lists of the tensor-core
  * contraction before the exact re-rank, with the quantised copy and the error

@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("T_i", ctypes.c_int32), ("tau", ctypes.c_int32), ("disc_max_iter", ctypes.c_int32),
                 ("knn_prec", ctypes.c_int32), ("init", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("init_labels", ctypes.c_void_p), ("early_stop", ctypes.c_int32), ("eps_Q", ctypes.c_float),
-                ("warm", ctypes.POINTER(WarmModel))]
+                ("warm", ctypes.POINTER(WarmModel)), ("knn_nlist", ctypes.c_int32), ("knn_nprobe", ctypes.c_int32)]
 
 
 class Outputs(ctypes.Structure):
@@ -65,7 +65,8 @@ class Info(ctypes.Structure):
                 ("ms_iter", ctypes.c_float), ("ms_disc", ctypes.c_float), ("ms_mhc", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("ms_contract", ctypes.c_float),
                 ("ms_rerank", ctypes.c_float), ("ms_spmm", ctypes.c_float),
-                ("warm_used", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
+                ("warm_used", ctypes.c_int32), ("pad2_", ctypes.c_int32),
+                ("knn_tiles", ctypes.c_int64), ("knn_full_tiles", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         n = self.n_phi
@@ -76,7 +77,8 @@ class Info(ctypes.Structure):
                     ms_knn=self.ms_knn, ms_build=self.ms_build, ms_init=self.ms_init, ms_iter=self.ms_iter,
                     ms_disc=self.ms_disc, ms_mhc=self.ms_mhc, ms_total=self.ms_total,
                     ms_contract=self.ms_contract, ms_rerank=self.ms_rerank,
-                    ms_spmm=self.ms_spmm, warm_used=self.warm_used)
+                    ms_spmm=self.ms_spmm, warm_used=self.warm_used, knn_tiles=self.knn_tiles,
+                    knn_full_tiles=self.knn_full_tiles)
 
 
 class AnckaError(RuntimeError):
@@ -142,6 +144,8 @@ def load(path: str = LIB_PATH):
     L.ancka_discretize.restype = ctypes.c_int
     L.ancka_discretize_noalloc.argtypes = [vp, i64, i32, i32, i32, vp, ctypes.POINTER(i32), vp]
     L.ancka_discretize_noalloc.restype = ctypes.c_int
+    L.ancka_knn_ivf.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp, ctypes.POINTER(Info), vp]
+    L.ancka_knn_ivf.restype = ctypes.c_int
     L.ancka_polar_factor.argtypes = [vp, i32, vp, ctypes.POINTER(i32), vp]
     L.ancka_polar_factor.restype = ctypes.c_int
     _lib = L
@@ -198,6 +202,20 @@ def knn(X, K: int, prec: str = "bf16", with_info: bool = True):
     st = load().ancka_knn(_ptr(X), n, d, K, PREC[prec], _ptr(idx), _ptr(sim),
                           ctypes.byref(info) if with_info else None, _stream())
     _check("ancka_knn", st)
+    return idx, sim, (info.to_dict() if with_info else None)
+
+
+def knn_ivf(X, K: int, nlist: int, nprobe: int, with_info: bool = True):
+    """Approximate N_K lists by inverted lists (ancka_knn_ivf): (idx, sim, info)."""
+    import torch
+    assert X.is_cuda and X.dtype == torch.float32 and X.is_contiguous()
+    n, d = X.shape
+    idx = torch.empty((n, K), dtype=torch.int32, device=X.device)
+    sim = torch.empty((n, K), dtype=torch.float32, device=X.device)
+    info = Info()
+    st = load().ancka_knn_ivf(_ptr(X), n, d, K, nlist, nprobe, _ptr(idx), _ptr(sim),
+                              ctypes.byref(info) if with_info else None, _stream())
+    _check("ancka_knn_ivf", st)
     return idx, sim, (info.to_dict() if with_info else None)
 
 

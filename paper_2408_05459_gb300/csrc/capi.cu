@@ -271,6 +271,20 @@ ancka_status knn_impl(Workspace& ws, const float* X, int64_t n, int32_t d, int32
   return ANCKA_OK;
 }
 
+constexpr int kIvfIters = 8;  // spherical k-means rounds of the inverted-list KNN
+
+ancka_status validate_ivf_args(const float* X, int64_t n, int32_t d, int32_t K, int32_t nlist, int32_t nprobe) {
+  ANCKA_REQUIRE(X != nullptr, "X is NULL");
+  ANCKA_REQUIRE(n >= 2 && n < (int64_t(1) << 31) - 1, "n out of range");
+  ANCKA_REQUIRE(d >= 1 && round_up(d, 64) <= knn_tc_max_dp(), "inverted-list KNN: d must be in [1, %d]",
+                knn_tc_max_dp());
+  ANCKA_REQUIRE(K >= 1 && K <= 16 && K < n, "inverted-list KNN: need 1 <= K <= 16 and K < n");
+  ANCKA_REQUIRE(nlist >= 1 && nlist <= 8192 && nlist <= n, "inverted-list KNN: need 1 <= nlist <= min(n, 8192)");
+  ANCKA_REQUIRE(nprobe >= 1 && nprobe <= 32 && nprobe <= nlist, "inverted-list KNN: need 1 <= nprobe <= min(32, nlist)");
+  ANCKA_REQUIRE(ceil_div(round_up(n, 128), 256) <= ivf_max_tiles(), "inverted-list KNN: n too large");
+  return ANCKA_OK;
+}
+
 ancka_status validate_topology(const ancka_topology* t) {
   ANCKA_REQUIRE(t != nullptr, "topology is NULL");
   ANCKA_REQUIRE(t->n >= 2 && t->n < (int64_t(1) << 31) - 1, "topology n out of range");
@@ -299,6 +313,7 @@ ancka_status validate_params(const ancka_params* p, int64_t n) {
   ANCKA_REQUIRE(p->init == 0 || (p->init == 1 && p->init_labels) || (p->init == 2 && p->warm),
                 "init must be 0, 1 with init_labels, or 2 with a warm model");
   ANCKA_REQUIRE(p->early_stop == 0 || (p->early_stop == 1 && p->eps_Q >= 0.f), "early_stop must be 0 or 1, eps_Q >= 0");
+  ANCKA_REQUIRE(p->knn_nlist >= 0, "knn_nlist must be >= 0 (0: exact KNN)");
   return ANCKA_OK;
 }
 
@@ -345,7 +360,9 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
   const int64_t n = topo->n;
   ANCKA_TRY(validate_params(p, n));
   ANCKA_REQUIRE(labels != nullptr, "labels is NULL");
-  if (!knn_idx_in) {
+  if (!knn_idx_in && p->knn_nlist > 0) {
+    ANCKA_TRY(validate_ivf_args(X, n, d, p->K, p->knn_nlist, p->knn_nprobe));
+  } else if (!knn_idx_in) {
     ANCKA_TRY(validate_knn_args(X, n, d, p->K, p->knn_prec));
   } else {
     ANCKA_REQUIRE(X && knn_sim_in && d >= 1 && p->K >= 1 && p->K < n, "bad KNN inputs");
@@ -424,11 +441,21 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
       Phase ph(tp, s, 0);
       if (!idx) st = ws.alloc(&idx, (size_t)n * K);
       if (st == ANCKA_OK && !sim) st = ws.alloc(&sim, (size_t)n * K);
-      if (st == ANCKA_OK)
+      if (st == ANCKA_OK && p->knn_nlist > 0) {
+        IvfStats stats;
+        st = knn_ivf(ws, X, n, d, K, p->knn_nlist, p->knn_nprobe, kIvfIters, 0x5eed, idx, sim, &zero_row, &stats,
+                     s);
+        if (st == ANCKA_OK && !early_init) st = start_init();
+        if (info) {
+          info->knn_tiles = stats.key_tiles;
+          info->knn_full_tiles = stats.full_tiles;
+        }
+      } else if (st == ANCKA_OK) {
         st = knn_impl(ws, X, n, d, K, p->knn_prec, idx, sim, &zero_row, &ncand, &nfb, &nex, info != nullptr, s,
                       info && K <= max_candidate_K(p->knn_prec) ? cev : nullptr,
                       early_init ? std::function<ancka_status()>() : std::function<ancka_status()>(start_init));
-      contract_timed = info && K <= max_candidate_K(p->knn_prec);
+        contract_timed = info && K <= max_candidate_K(p->knn_prec);
+      }
     } else if (st == ANCKA_OK) {
       Phase ph(tp, s, 0);
       k_check_knn<<<(unsigned)ceil_div(n * K, 256), 256, 0, s>>>(knn_idx_in, n, K, bad);
@@ -594,6 +621,41 @@ ancka_status ancka_device_check(void) { return device_check(); }
 int64_t ancka_kernel_launches(void) { return g_launches.load(); }
 
 void ancka_set_symmetric_knn_min_rows(int64_t n_min) { knn_set_symmetric_min_rows(n_min); }
+
+ancka_status ancka_knn_ivf(const float* X, int64_t n, int32_t d, int32_t K, int32_t nlist, int32_t nprobe,
+                           int32_t* out_idx, float* out_sim, ancka_info* info, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ANCKA_TRY(device_check());
+  ANCKA_TRY(validate_ivf_args(X, n, d, K, nlist, nprobe));
+  ANCKA_REQUIRE(out_idx && out_sim, "output pointers are NULL");
+  if (info) memset(info, 0, sizeof(*info));
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (info) {
+    a = pooled_event();
+    b = pooled_event();
+    cudaEventRecord(a, s);
+  }
+  ancka_status st;
+  IvfStats stats;
+  {
+    Workspace ws(s);
+    st = knn_ivf(ws, X, n, d, K, nlist, nprobe, kIvfIters, 0x5eed, out_idx, out_sim, nullptr, &stats, s);
+  }
+  if (info) {
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && st == ANCKA_OK) st = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    info->ms_knn = ms;
+    info->ms_total = ms;
+    info->knn_tiles = stats.key_tiles;
+    info->knn_full_tiles = stats.full_tiles;
+    release_event(a);
+    release_event(b);
+  }
+  return st;
+}
 
 ancka_status ancka_knn(const float* X, int64_t n, int32_t d, int32_t K, int32_t prec, int32_t* out_idx,
                        float* out_sim, ancka_info* info, void* stream) {

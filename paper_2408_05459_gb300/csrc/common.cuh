@@ -213,6 +213,25 @@ ancka_status knn_candidates_bf16(Workspace& ws, const PrepOut& pr, int64_t n, fl
 ancka_status knn_candidates_fp8(Workspace& ws, const PrepOut& pr, int64_t n, float* cand_val, int32_t* cand_idx,
                                 int32_t* err, cudaStream_t s);
 int knn_tc_max_dp_fp8();
+// ivf.cu: approximate KNN by inverted lists (spherical k-means cells, nprobe
+// nearest cells per row, exact cosines of the candidates found there)
+struct IvfStats {
+  int64_t key_tiles = 0;   // (query block, key tile) pairs multiplied
+  int64_t full_tiles = 0;  // the same for the exact sweep
+};
+ancka_status knn_ivf(Workspace& ws, const float* X, int64_t n, int32_t d, int32_t K, int32_t nlist, int32_t nprobe,
+                     int32_t iters, uint64_t seed, int32_t* out_idx, float* out_sim, int32_t** zero_row,
+                     IvfStats* stats, cudaStream_t s);
+int ivf_max_tiles();
+// Two 16-entry candidate lists per query row of the BF16 matrix a (rows
+// 0..n_rows-1, or the rows listed in `rows`, written at their own row index)
+// against the keys (n_keys rows of keys, keys_pad rows addressable, zero
+// padded); optional key-tile lists per 128-row query block (blk_ptr /
+// blk_tiles, blk_work = blk_ptr[blocks]); no_self: the keys are another set.
+ancka_status knn_lists_bf16(Workspace& ws, const __nv_bfloat16* a, int64_t a_rows_total, const int32_t* rows,
+                           int64_t n_rows, const __nv_bfloat16* keys, int64_t n_keys, int64_t keys_pad, int dp, int d,
+                           const int64_t* blk_ptr, const int32_t* blk_tiles, int64_t blk_work, bool no_self,
+                           float* cand_val, int32_t* cand_idx, int32_t* err, cudaStream_t s);
 // BF16 list pass for the n_a rows listed in rows; lists written at their global rows
 ancka_status knn_list_gathered_bf16(Workspace& ws, const PrepOut& pr, int64_t n, const int32_t* rows, int64_t n_a,
                                     float* cand_val, int32_t* cand_idx, int32_t* err, cudaStream_t s);

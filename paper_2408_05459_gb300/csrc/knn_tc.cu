@@ -1015,7 +1015,10 @@ ancka_status launch_tc(Workspace& ws, const CUtensorMap& ta, const CUtensorMap& 
     ANCKA_TRY(ws.alloc(&part_idx, (size_t)ctas * 2 * kTM * kCandC));
   }
   unsigned long long* tick = nullptr;  // tiles issued by all CTAs (re-aligns whole blocks' key order)
-  if (key_stride == 1 && !ca.blk_ptr) ANCKA_TRY(ws.zeros(&tick, 1));
+  // (not for tile lists or foreign keys, whose callers want the same lists
+  // on every call: a key order that moves with timing resolves exact score
+  // ties differently)
+  if (key_stride == 1 && !ca.blk_ptr && !ca.no_self) ANCKA_TRY(ws.zeros(&tick, 1));
   ANCKA_CUDA(cudaFuncSetAttribute(k_knn_tc<kCollect, kE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_knn_tc<kCollect, kE4M3><<<(unsigned)ctas, kThreads, smem, s>>>(ta, tb, n, n_pad, qblocks, kb_count, k_last,
                                                                    nstages, key_stride, cand_val, cand_idx,
