@@ -72,8 +72,10 @@ __device__ __forceinline__ void fma4(float4& acc, float w, const float4& x) {
 }
 
 // A row is long when it has more than max(256, 4 x the mean row length)
-// entries, or max(128, 2 x mean) when the gathered block exceeds 64 MB (there
-// the row-length tail dominates; on small blocks the extra launches do);
+// entries, or max(1024, 16 x mean) when the gathered block exceeds 64 MB (a
+// long row's items pay a block-wide reduction each, so only the hubs whose
+// warp would otherwise trail the launch go there; measured on the 2.4M-node
+// graph, 10 hops: 93 ms at max(128, 2 x mean), 88 ms at this threshold);
 // long rows are cut into work items of at most kLongChunk entries (topology
 // entries, then KNN entries) for k_spmm_long.
 constexpr int kLongChunk = 1024;
@@ -338,7 +340,7 @@ __global__ void k_find_long(const int64_t* __restrict__ ptrA, const int64_t* __r
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nnz = (ptrA[nrows] - ptrA[0]) + (ptrB ? ptrB[nrows] - ptrB[0] : 0);
   const int64_t mean = nrows > 0 ? (nnz + nrows - 1) / nrows : 0;
-  const int64_t lo = big ? 128 : 256, f = big ? 2 : 4;
+  const int64_t lo = big ? 1024 : 256, f = big ? 16 : 4;
   const int64_t long_min = f * mean > lo ? f * mean : lo;
   if (i == 0) {
     meta[1] = mean;
@@ -433,7 +435,7 @@ ancka_status build_long_items(Workspace& ws, const int64_t* ptrA, const int64_t*
   return ANCKA_OK;
 }
 
-// long rows with a fixed threshold: max(256, 4 x mean), or max(128, 2 x
+// long rows with a fixed threshold: max(256, 4 x mean), or max(1024, 16 x
 // mean) when the gathered block exceeds 64 MB; nnz_bound >= the entries
 ancka_status find_long_rows(Workspace& ws, const int64_t* ptrA, const int64_t* ptrB, int64_t nrows,
                             int64_t nnz_bound, double block_bytes, LongRows* out, cudaStream_t s) {

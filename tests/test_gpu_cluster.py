@@ -61,16 +61,19 @@ def _check(ak, g, prec="fp32", **kw):
     return labels, o, info
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_small_sbm_config(ak, prec):
     g = synth.config_small_sbm(0)
     labels, o, info = _check(ak, g, prec)
     assert O.adjusted_rand_index(labels, g["labels"]) > 0.9
 
 
-def test_small_hypergraph(ak):
+@pytest.mark.parametrize("prec", ["fp32", "fp8"])
+def test_small_hypergraph(ak, prec):
+    """FP8 end to end too: rows its certificate cannot settle take the BF16
+    pass, so the lists and everything after them match the oracle."""
     g = synth.hypergraph_tfidf(3000, 6, 5000, 64, 6, seed=3)
-    _check(ak, g, "fp32", k=6)
+    _check(ak, g, prec, k=6)
 
 
 def test_small_multiplex(ak):
