@@ -130,6 +130,12 @@ typedef struct {
   int32_t knn_nlist;     /* 0: exact KNN lists (default); > 0: approximate lists from
                             nlist inverted-list cells, as ancka_knn_ivf (BF16 only) */
   int32_t knn_nprobe;    /* cells probed per row when knn_nlist > 0 (1 <= nprobe <= min(32, nlist)) */
+  int32_t node_order;    /* graphs and multiplex graphs: the order in which the iteration stores
+                            the nodes (results are always in the caller's order).  0 (default):
+                            descending degree when the n x (k+1) FP32 block exceeds 64 MiB,
+                            else as given; 1: as given; 2: descending degree.  Algorithm 4 is
+                            unchanged by the renaming (InitBCM's tie-break stays on the
+                            caller's indices); only FP32 summation orders differ. */
 } ancka_params;
 
 /* Optional device outputs (any field may be NULL). */

@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("T_i", ctypes.c_int32), ("tau", ctypes.c_int32), ("disc_max_iter", ctypes.c_int32),
                 ("knn_prec", ctypes.c_int32), ("init", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("init_labels", ctypes.c_void_p), ("early_stop", ctypes.c_int32), ("eps_Q", ctypes.c_float),
-                ("warm", ctypes.POINTER(WarmModel)), ("knn_nlist", ctypes.c_int32), ("knn_nprobe", ctypes.c_int32)]
+                ("warm", ctypes.POINTER(WarmModel)), ("knn_nlist", ctypes.c_int32), ("knn_nprobe", ctypes.c_int32),
+                ("node_order", ctypes.c_int32)]
 
 
 class Outputs(ctypes.Structure):

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libancka.so")
 SOURCES = ["capi.cu", "prep.cu", "knn_simt.cu", "knn_tc.cu", "rerank.cu", "graph.cu", "iter.cu", "noalloc.cu",
-           "gemm_tc.cu", "warm.cu", "ivf.cu"]
+           "gemm_tc.cu", "warm.cu", "ivf.cu", "sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -314,6 +314,7 @@ ancka_status validate_params(const ancka_params* p, int64_t n) {
                 "init must be 0, 1 with init_labels, or 2 with a warm model");
   ANCKA_REQUIRE(p->early_stop == 0 || (p->early_stop == 1 && p->eps_Q >= 0.f), "early_stop must be 0 or 1, eps_Q >= 0");
   ANCKA_REQUIRE(p->knn_nlist >= 0, "knn_nlist must be >= 0 (0: exact KNN)");
+  ANCKA_REQUIRE(p->node_order >= 0 && p->node_order <= 2, "node_order = %d must be 0, 1 or 2", p->node_order);
   return ANCKA_OK;
 }
 
@@ -418,7 +419,8 @@ ancka_status cluster_impl(const ancka_topology* topo, const float* X, int32_t d,
     } ij{s};
     Workspace wsi(is);  // InitBCM's scratch, used and released on its stream
     int32_t* y0_async = nullptr;
-    const IterCfg cfg{p->k, p->T, p->gamma, p->T_i, p->tau, p->disc_max_iter, p->alpha, p->early_stop, p->eps_Q};
+    const IterCfg cfg{p->k,     p->T,          p->gamma, p->T_i,  p->tau,
+                      p->disc_max_iter, p->alpha, p->early_stop, p->eps_Q, p->node_order};
     auto start_init = [&]() -> ancka_status {
       if (p->init == 1) return ANCKA_OK;  // labels given
       ANCKA_TRY(ws.alloc(&y0_async, (size_t)n));

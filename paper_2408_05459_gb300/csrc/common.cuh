@@ -223,6 +223,14 @@ ancka_status knn_ivf(Workspace& ws, const float* X, int64_t n, int32_t d, int32_
                      int32_t iters, uint64_t seed, int32_t* out_idx, float* out_sim, int32_t** zero_row,
                      IvfStats* stats, cudaStream_t s);
 int ivf_max_tiles();
+// sort.cu: keys sorted ascending on bits [0, end_bit) (in is left as it was;
+// in != out); out[i] = in[0] + ... + in[i-1] for i < count; the distinct
+// values of sorted keys, their count written to *count_dev
+ancka_status radix_sort_u64(Workspace& ws, const uint64_t* in, uint64_t* out, int64_t count, int end_bit,
+                            cudaStream_t s);
+ancka_status exclusive_scan(Workspace& ws, const int64_t* in, int64_t* out, int64_t count, cudaStream_t s);
+ancka_status unique_u64(Workspace& ws, const uint64_t* in, uint64_t* out, int64_t* count_dev, int64_t count,
+                        cudaStream_t s);
 // Two 16-entry candidate lists per query row of the BF16 matrix a (rows
 // 0..n_rows-1, or the rows listed in `rows`, written at their own row index)
 // against the keys (n_keys rows of keys, keys_pad rows addressable, zero
@@ -281,6 +289,7 @@ struct Walk {
   float* inv_size = nullptr;    // hypergraph: m, 1/|e|
   int32_t* degree = nullptr;    // n: delta(v) used for V_c
   float* beta = nullptr;        // n: beta_i
+  const int32_t* names = nullptr;  // n: the caller's index of each row when the nodes are renamed, else null
 };
 ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cudaStream_t s);
 ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* idx, const float* sim,
@@ -292,7 +301,12 @@ struct IterCfg {
   float alpha;
   int32_t early_stop;  // Eq. tcond-1 / tcond-2 checks (paper mode)
   float eps_Q;         // Eq. tcond-1 threshold
+  int32_t node_order = 0;  // 0: degree order when the block exceeds kDegreeOrderMinBytes, 1: as given, 2: degree order
 };
+// graphs whose n x (k+1) FP32 block is larger than this are iterated with the
+// nodes renamed by descending degree (the gathers of the walk products then
+// hit L2 more often); smaller blocks stay in L2 as they are
+constexpr double kDegreeOrderMinBytes = 64.0 * 1024 * 1024;
 struct IterTrace {
   double* phi_dev;         // device [ANCKA_MAX_TRACE]
   int32_t* disc_iters_dev; // device [ANCKA_MAX_TRACE]

@@ -12,8 +12,6 @@
 // KNN part: row i holds its K out-neighbours with A_K = 2f (mutual) or f,
 // then the nodes that list i but are not listed by i (weight f), in source
 // order; values are pre-scaled to beta_i A_K[i,j] / D_K[i] (Eq. p-mat-ancka).
-#include <cub/cub.cuh>
-
 #include "common.cuh"
 
 namespace ancka {
@@ -28,38 +26,6 @@ int bits_for(int64_t n) {
   int b = 1;
   while ((int64_t(1) << b) < n) ++b;
   return b;
-}
-
-// --- CUB wrappers (one-off preprocessing sorts / scans) ---------------------
-ancka_status sort_keys(Workspace& ws, uint64_t* keys_in, uint64_t* keys_out, int64_t count,
-                       int end_bit, cudaStream_t s) {
-  if (count == 0) return ANCKA_OK;
-  size_t tmp = 0;
-  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, keys_in, keys_out, count, 0, end_bit, s));
-  void* t = nullptr;
-  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp));
-  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, keys_in, keys_out, count, 0, end_bit, s));
-  return ANCKA_OK;
-}
-
-ancka_status unique_keys(Workspace& ws, const uint64_t* in, uint64_t* out, int64_t* count_dev,
-                         int64_t count, cudaStream_t s) {
-  size_t tmp = 0;
-  ANCKA_CUDA(cub::DeviceSelect::Unique(nullptr, tmp, in, out, count_dev, count, s));
-  void* t = nullptr;
-  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp));
-  ANCKA_CUDA(cub::DeviceSelect::Unique(t, tmp, in, out, count_dev, count, s));
-  return ANCKA_OK;
-}
-
-template <class T>
-ancka_status exclusive_scan(Workspace& ws, const T* in, T* out, int64_t count, cudaStream_t s) {
-  size_t tmp = 0;
-  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, count, s));
-  void* t = nullptr;
-  ANCKA_TRY(ws.alloc(reinterpret_cast<char**>(&t), tmp));
-  ANCKA_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, in, out, count, s));
-  return ANCKA_OK;
 }
 
 ancka_status check_bad(const int32_t* bad, cudaStream_t s, const char* fmt, int arg = 0) {
@@ -328,10 +294,10 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     k_hyper_to_keys<<<grid_for(m, 256), 256, 0, s>>>(t.he_ptr, t.he_nodes, m, n, nb, k0, bad);
     ANCKA_LAUNCHED();
     const int mb = bits_for(m);
-    ANCKA_TRY(sort_keys(ws, k0, k1, nnz, mb + nb, s));
+    ANCKA_TRY(radix_sort_u64(ws, k0, k1, nnz, mb + nb, s));
     int64_t* ucnt_dev;
     ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
-    if (nnz > 0) ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, nnz, s));
+    if (nnz > 0) ANCKA_TRY(unique_u64(ws, k1, k2, ucnt_dev, nnz, s));
     int64_t ucnt = 0;
     ANCKA_CUDA(cudaMemcpyAsync(&ucnt, ucnt_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     ANCKA_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -345,7 +311,7 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
     // node -> hyperedge incidence
     k_swap_halves<<<grid_for(ucnt, 256), 256, 0, s>>>(k2, ucnt_dev, nb, mb, k0);
     ANCKA_LAUNCHED();
-    ANCKA_TRY(sort_keys(ws, k0, k1, ucnt, nb + mb, s));
+    ANCKA_TRY(radix_sort_u64(ws, k0, k1, ucnt, nb + mb, s));
     int32_t* vdeg;
     ANCKA_TRY(keys_to_csr(ws, k1, ucnt_dev, ucnt, n, mb, &w->topo, &vdeg, s));
     w->degree = vdeg;
@@ -377,10 +343,10 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
       k_csr_to_keys<<<grid_for(n, 256), 256, 0, s>>>(rp, t.col_idx, n, t.directed, nb, k0, bad);
       ANCKA_LAUNCHED();
       ANCKA_TRY(check_bad(bad, s, "topology: node id out of range [0, n)"));
-      ANCKA_TRY(sort_keys(ws, k0, k1, cnt, 2 * nb, s));
+      ANCKA_TRY(radix_sort_u64(ws, k0, k1, cnt, 2 * nb, s));
       int64_t* ucnt_dev;
       ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
-      if (cnt > 0) ANCKA_TRY(unique_keys(ws, k1, k2, ucnt_dev, cnt, s));
+      if (cnt > 0) ANCKA_TRY(unique_u64(ws, k1, k2, ucnt_dev, cnt, s));
       int64_t ucnt = 0;
       ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
       Csr lay;
@@ -443,7 +409,7 @@ ancka_status build_knn_part(Workspace& ws, int64_t n, int32_t K, const int32_t* 
   const int nb = bits_for(n);
   k_knn_mutual<<<grid_for(nk, 256), 256, 0, s>>>(idx, n, K, nb, mutual, keys, in_cnt);
   ANCKA_LAUNCHED();
-  ANCKA_TRY(sort_keys(ws, keys, skeys, nk, 2 * nb + 1, s));
+  ANCKA_TRY(radix_sort_u64(ws, keys, skeys, nk, 2 * nb + 1, s));
   int64_t *len, *in_len, *in_start;
   ANCKA_TRY(ws.alloc(&len, (size_t)n + 1));
   ANCKA_TRY(ws.alloc(&in_len, (size_t)n + 1));

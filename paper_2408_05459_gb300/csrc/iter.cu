@@ -9,7 +9,6 @@
 // Cholesky factor and inverse, Discretize's trace and objective); cross-CTA
 // sums are float-float.  Discretize's k x k polar factor is FP32
 // (Newton-Schulz, Jacobi SVD fallback).
-#include <cub/cub.cuh>
 
 #include <algorithm>
 
@@ -1438,7 +1437,8 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // keeps span(h(Y)) and gives Q^(0) full rank.
 __global__ void k_fill_onehot(const int32_t* __restrict__ labels, const float* __restrict__ inv,
                               const int32_t* __restrict__ cnt, int k, int64_t n, int ld, int col_off,
-                              float first_col, float scale, float* __restrict__ out) {
+                              float first_col, float scale, float* __restrict__ out,
+                              const int32_t* __restrict__ names = nullptr) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * ld) return;
   const int64_t i = t / ld;
@@ -1452,7 +1452,7 @@ __global__ void k_fill_onehot(const int32_t* __restrict__ labels, const float* _
     for (int q = 0; q < k; ++q)
       if (cnt[q] > 0) last = q;
     if (cnt[c - 1] == 0 || c - 1 == last)
-      v = (splitmix64((uint64_t)i * 64u + (uint64_t)(c - 1)) >> 63) ? -first_col : first_col;
+      v = (splitmix64((uint64_t)(names ? names[i] : i) * 64u + (uint64_t)(c - 1)) >> 63) ? -first_col : first_col;
   }
   out[t] = v;
 }
@@ -2017,11 +2017,7 @@ ancka_status initbcm_labels(Workspace& ws, const Walk& w, const IterCfg& cfg, in
   ANCKA_CUDA(cudaMemsetAsync(seedcol, 0xff, sizeof(int32_t) * n, s));
   k_degree_keys<<<grid_for(n, 256), 256, 0, s>>>(w.degree, n, keys);
   ANCKA_LAUNCHED();
-  size_t tmp = 0;
-  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, keys, skeys, n, 0, 64, s));
-  char* t;
-  ANCKA_TRY(ws.alloc(&t, tmp));
-  ANCKA_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, keys, skeys, n, 0, 64, s));
+  ANCKA_TRY(radix_sort_u64(ws, keys, skeys, n, 64, s));
   k_seed_setup<<<1, 32, 0, s>>>(skeys, k, seedcol);
   ANCKA_LAUNCHED();
   k_fill_seed<<<grid_for(n * ldk, 256), 256, 0, s>>>(seedcol, n, ldk, cfg.alpha, Fa);
@@ -2039,10 +2035,147 @@ ancka_status initbcm_labels(Workspace& ws, const Walk& w, const IterCfg& cfg, in
   return ANCKA_OK;
 }
 
+namespace {
+
+// ---- degree order of the nodes (locality of the walk products) ----
+// Algorithm 4 is equivariant under a renaming of the nodes, except for
+// InitBCM's tie-break by index, which is therefore taken on the caller's
+// names.  Renaming the nodes by descending degree puts the rows of Q that
+// most entries gather (the hubs) next to each other, so more of the gathers
+// hit L2.
+
+// new row r holds old row order[r]; pos is the inverse
+__global__ void k_order_maps(const uint64_t* __restrict__ sorted, int64_t n, int32_t* __restrict__ order,
+                             int32_t* __restrict__ pos) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int32_t o = (int32_t)(sorted[r] & 0xffffffffull);
+  order[r] = o;
+  pos[o] = (int32_t)r;
+}
+
+// entries of new row r (and len[n] = 0, for the scan into row pointers)
+__global__ void k_permuted_lens(const int64_t* __restrict__ ptr, const int32_t* __restrict__ order, int64_t n,
+                                int64_t* __restrict__ len) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) len[r] = ptr[order[r] + 1] - ptr[order[r]];
+  if (r == n) len[r] = 0;
+}
+
+constexpr int kPermPerLane = 16;  // entries per lane of k_permute_csr
+
+// the renamed CSR: entry q of new row r is entry q - nptr[r] of old row
+// order[r] (the row's entry order is kept), its column renamed by pos.  A
+// warp covers 32 x kPermPerLane consecutive entries (lane-interleaved, so
+// the copies coalesce); each lane finds its first row by binary search and
+// then walks forward.
+__global__ void k_permute_csr(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, const float* __restrict__ valT,
+                              const int32_t* __restrict__ order, const int32_t* __restrict__ pos, int64_t n,
+                              const int64_t* __restrict__ nptr, int32_t* __restrict__ ncol,
+                              float* __restrict__ nval, float* __restrict__ nvalT) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = nptr[n];
+  const int64_t q0 = warp * 32 * kPermPerLane + lane;
+  if (q0 >= total) return;
+  int64_t lo = 0, hi = n - 1;  // last row r with nptr[r] <= q0
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (nptr[mid] <= q0) lo = mid;
+    else hi = mid - 1;
+  }
+  int64_t r = lo;
+  for (int j = 0; j < kPermPerLane; ++j) {
+    const int64_t q = q0 + 32 * j;
+    if (q >= total) break;
+    while (nptr[r + 1] <= q) ++r;
+    const int64_t src = ptr[order[r]] + (q - nptr[r]);
+    ncol[q] = pos[col[src]];
+    if (nval) nval[q] = val[src];
+    if (nvalT) nvalT[q] = valT[src];
+  }
+}
+
+template <class T>
+__global__ void k_gather_vec(const T* __restrict__ in, const int32_t* __restrict__ order, int64_t n,
+                             T* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) out[r] = in[order[r]];
+}
+
+template <class T>
+__global__ void k_scatter_vec(const T* __restrict__ in, const int32_t* __restrict__ order, int64_t n,
+                              T* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) out[order[r]] = in[r];
+}
+
+// out row r = in row order[r] (gather) or out row order[r] = in row r
+template <bool Gather>
+__global__ void k_permute_rows(const float* __restrict__ in, int ldi, const int32_t* __restrict__ order, int64_t n,
+                               int width, float* __restrict__ out, int ldo) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * width) return;
+  const int64_t r = t / width;
+  const int c = (int)(t % width);
+  if (Gather) out[r * ldo + c] = in[(int64_t)order[r] * ldi + c];
+  else out[(int64_t)order[r] * ldo + c] = in[r * ldi + c];
+}
+
+ancka_status permute_csr(Workspace& ws, const Csr& a, int64_t n, const int32_t* order, const int32_t* pos, Csr* b,
+                         cudaStream_t s) {
+  *b = a;
+  int64_t* len;
+  ANCKA_TRY(ws.alloc(&len, (size_t)n + 1));
+  ANCKA_TRY(ws.alloc(&b->ptr, (size_t)n + 1));
+  k_permuted_lens<<<grid_for(n + 1, 256), 256, 0, s>>>(a.ptr, order, n, len);
+  ANCKA_LAUNCHED();
+  ANCKA_TRY(exclusive_scan(ws, len, b->ptr, n + 1, s));
+  // nnz may be an upper bound (the KNN part): the kernel stops at ptr[n]
+  ANCKA_TRY(ws.alloc(&b->col, (size_t)a.nnz));
+  b->val = b->valT = nullptr;
+  if (a.val) ANCKA_TRY(ws.alloc(&b->val, (size_t)a.nnz));
+  if (a.valT) ANCKA_TRY(ws.alloc(&b->valT, (size_t)a.nnz));
+  const int64_t warps = ceil_div(a.nnz, 32 * kPermPerLane);
+  k_permute_csr<<<grid_for(warps * 32, 256), 256, 0, s>>>(a.ptr, a.col, a.val, a.valT, order, pos, n, b->ptr,
+                                                          b->col, b->val, b->valT);
+  ANCKA_LAUNCHED();
+  return ANCKA_OK;
+}
+
+template <class T>
+ancka_status gather_vec(Workspace& ws, const T* in, const int32_t* order, int64_t n, T** out, cudaStream_t s) {
+  *out = nullptr;
+  if (!in) return ANCKA_OK;
+  T* o;
+  ANCKA_TRY(ws.alloc(&o, (size_t)n));
+  k_gather_vec<T><<<grid_for(n, 256), 256, 0, s>>>(in, order, n, o);
+  ANCKA_LAUNCHED();
+  *out = o;
+  return ANCKA_OK;
+}
+
+// the walk with its nodes renamed: graphs and multiplex graphs only
+ancka_status permute_walk(Workspace& ws, const Walk& w, const int32_t* order, const int32_t* pos, Walk* v,
+                          cudaStream_t s) {
+  const int64_t n = w.n;
+  *v = w;
+  ANCKA_TRY(permute_csr(ws, w.topo, n, order, pos, &v->topo, s));
+  ANCKA_TRY(permute_csr(ws, w.knn, n, order, pos, &v->knn, s));
+  ANCKA_TRY(gather_vec(ws, w.rs_topo, order, n, &v->rs_topo, s));
+  ANCKA_TRY(gather_vec(ws, w.inv_deg, order, n, &v->inv_deg, s));
+  ANCKA_TRY(gather_vec(ws, w.degree, order, n, &v->degree, s));
+  ANCKA_TRY(gather_vec(ws, w.beta, order, n, &v->beta, s));
+  return ANCKA_OK;
+}
+
+}  // namespace
+
 // phases: 2 = init, 3 = iteration, 4 = discretize, 5 = mhc, 6 = the walk products inside 3
-ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const int32_t* init_labels,
-                       const float* warm_W, int ldw, int32_t* labels_out, float* Q_out, int32_t* init_out,
-                       IterTrace* tr, cudaStream_t s) {
+static ancka_status run_ancka_rows(Workspace& ws, const Walk& w, const IterCfg& cfg, const int32_t* init_labels,
+                                   const float* warm_W, int ldw, int32_t* labels_out, float* Q_out,
+                                   int32_t* init_out, IterTrace* tr, cudaStream_t s) {
   const int64_t n = w.n;
   const int k = cfg.k;
   const int wq = k + 1;
@@ -2119,7 +2252,7 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     k_inv_sqrt_counts<<<1, 64, 0, s>>>(sc.cnt, k, sc.inv);
     ANCKA_LAUNCHED();
     k_fill_onehot<<<grid_for(n * ld, 256), 256, 0, s>>>(y0, sc.inv, sc.cnt, k, n, ld, 1,
-                                                        (float)(1.0 / sqrt((double)n)), 1.f, Qa);
+                                                        (float)(1.0 / sqrt((double)n)), 1.f, Qa, w.names);
     ANCKA_LAUNCHED();
   }
   tr->warm_used = 0;
@@ -2306,6 +2439,74 @@ ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const i
     return ANCKA_ERR_NUMERIC;
   }
   return ANCKA_OK;
+}
+
+bool degree_order_applies(const Walk& w, const IterCfg& cfg) {
+  if (w.kind == ANCKA_HYPERGRAPH || cfg.node_order == 1 || w.n < 2) return false;
+  if (cfg.node_order == 2) return true;
+  return (double)w.n * round_up(cfg.k + 1, 4) * 4.0 > kDegreeOrderMinBytes;
+}
+
+ancka_status run_ancka(Workspace& ws, const Walk& w, const IterCfg& cfg, const int32_t* init_labels,
+                       const float* warm_W, int ldw, int32_t* labels_out, float* Q_out, int32_t* init_out,
+                       IterTrace* tr, cudaStream_t s) {
+  if (!degree_order_applies(w, cfg))
+    return run_ancka_rows(ws, w, cfg, init_labels, warm_W, ldw, labels_out, Q_out, init_out, tr, s);
+  const int64_t n = w.n;
+  const int k = cfg.k;
+  const int wq = k + 1;
+  int32_t *y0 = nullptr, *order, *pos;
+  {
+    PhaseTimer pt(tr, s, 2);
+    if (!init_labels) {  // InitBCM breaks degree ties by the caller's node index
+      ANCKA_TRY(ws.alloc(&y0, (size_t)n));
+      ANCKA_TRY(initbcm_labels(ws, w, cfg, y0, s));
+      init_labels = y0;
+    }
+  }
+  Walk v;
+  int32_t *y_in, *lab, *init_v = nullptr;
+  float *W_v = nullptr, *Q_v = nullptr;
+  {
+    PhaseTimer pt(tr, s, 1);
+    uint64_t *keys, *skeys;
+    ANCKA_TRY(ws.alloc(&keys, (size_t)n));
+    ANCKA_TRY(ws.alloc(&skeys, (size_t)n));
+    ANCKA_TRY(ws.alloc(&order, (size_t)n));
+    ANCKA_TRY(ws.alloc(&pos, (size_t)n));
+    k_degree_keys<<<grid_for(n, 256), 256, 0, s>>>(w.degree, n, keys);
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(radix_sort_u64(ws, keys, skeys, n, 64, s));
+    k_order_maps<<<grid_for(n, 256), 256, 0, s>>>(skeys, n, order, pos);
+    ANCKA_LAUNCHED();
+    ANCKA_TRY(permute_walk(ws, w, order, pos, &v, s));
+    v.names = order;  // R13's sign vectors follow the caller's node index
+    ANCKA_TRY(ws.alloc(&y_in, (size_t)n));
+    ANCKA_TRY(ws.alloc(&lab, (size_t)n));
+    if (init_out) ANCKA_TRY(ws.alloc(&init_v, (size_t)n));
+    k_gather_vec<int32_t><<<grid_for(n, 256), 256, 0, s>>>(init_labels, order, n, y_in);
+    ANCKA_LAUNCHED();
+    if (warm_W) {
+      ANCKA_TRY(ws.alloc(&W_v, (size_t)n * ldw));
+      k_permute_rows<true><<<grid_for(n * k, 256), 256, 0, s>>>(warm_W, ldw, order, n, k, W_v, ldw);
+      ANCKA_LAUNCHED();
+    }
+    if (Q_out) ANCKA_TRY(ws.alloc(&Q_v, (size_t)n * wq));
+  }
+  const ancka_status st = run_ancka_rows(ws, v, cfg, y_in, W_v, ldw, lab, Q_v, init_v, tr, s);
+  if (st != ANCKA_OK && st != ANCKA_ERR_NUMERIC) return st;
+  PhaseTimer pt(tr, s, 1);
+  k_scatter_vec<int32_t><<<grid_for(n, 256), 256, 0, s>>>(lab, order, n, labels_out);
+  ANCKA_LAUNCHED();
+  if (init_out) {
+    k_scatter_vec<int32_t><<<grid_for(n, 256), 256, 0, s>>>(init_v, order, n, init_out);
+    ANCKA_LAUNCHED();
+  }
+  if (Q_out) {
+    k_permute_rows<false><<<grid_for(n * wq, 256), 256, 0, s>>>(Q_v, wq, order, n, wq, Q_out, wq);
+    ANCKA_LAUNCHED();
+  }
+  return st;
 }
 
 ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, int32_t ldq, int32_t max_iter,

@@ -123,6 +123,39 @@ def test_negative_knn_degree_nodes(ak):
     _check(ak, g, "fp32", k=k)
 
 
+@pytest.mark.parametrize("case", ["sbm", "multiplex", "directed"])
+def test_degree_order_matches_oracle(ak, case):
+    """The iteration on nodes renamed by descending degree (node_order = 2,
+    forced at sizes where the default keeps the caller's order): results come
+    back in the caller's order and match the oracle's Algorithm 4."""
+    if case == "sbm":
+        g, k = synth.config_small_sbm(3), None
+    elif case == "multiplex":
+        g, k = synth.multiplex_sbm(2500, 4, 12.0, (6.0, 3.0), 32, 2.0, seed=14), 4
+    else:
+        rng = np.random.default_rng(15)
+        n = 1500
+        src = rng.integers(0, n, 9000)
+        dst = (src + rng.integers(1, 40, 9000)) % n
+        rp, col = synth.csr_from_edges(n, src, dst, symmetric=False)
+        X = synth.gaussian_mixture(rng, rng.integers(0, 3, n), 3, 16, 1.0)
+        g, k = dict(kind="graph", n=n, k=3, X=X, layers=[(rp, col)], directed=1), 3
+    kw = {} if k is None else {"k": k}
+    _check(ak, g, "fp32", node_order=2, **kw)
+
+
+def test_degree_order_same_result_as_given_order(ak):
+    """Renaming the nodes changes only FP32 summation orders: the same labels,
+    the same subspace and the same phi trace as the caller's order."""
+    g = synth.sbm_graph(6000, 8, 0.01, 0.001, 48, 1.5, seed=16)
+    a = _gpu_cluster(ak, g, "fp32", k=8, node_order=1)
+    b = _gpu_cluster(ak, g, "fp32", k=8, node_order=2)
+    assert np.array_equal(a[1]["init_labels"], b[1]["init_labels"])
+    assert O.adjusted_rand_index(a[0], b[0]) >= 0.999
+    assert O.max_principal_angle(a[1]["Q"].astype(np.float64), b[1]["Q"].astype(np.float64)) <= 1e-4
+    assert np.allclose(a[2]["phi"], b[2]["phi"], atol=1e-5)
+
+
 def test_cliques_closed_form_on_gpu(ak):
     k, c = 5, 24
     g = synth.cliques_closed_form(k, c, seed=7)
@@ -187,6 +220,9 @@ def test_invalid_arguments(ak):
     with pytest.raises(ak.AnckaError) as e:
         _gpu_cluster(ak, g, "fp32", alpha=0.0)
     assert e.value.status == 1
+    with pytest.raises(ak.AnckaError) as e:
+        _gpu_cluster(ak, g, "fp32", node_order=3)
+    assert e.value.status == 1
     bad = dict(g)
     rp, col = g["layers"][0]
     col = col.copy()
@@ -230,15 +266,16 @@ def test_multiplex_workload_with_verified_knn(ak):
     assert ang <= ANGLE_MAX and ari >= ARI_MIN, (ari, ang)
 
 
-def _dcsbm_oracle_parity(ak, n, sample_rows):
+def _dcsbm_oracle_parity(ak, n, sample_rows, node_order=0):
     """The DC-SBM generator with the large workload's settings (k = 47
     Zipf-sized clusters, d = 100, 25 n edges, beta = 0.4, T_i = 1, T = 10,
     BF16 KNN) at n nodes: the GPU's KNN exact on sampled rows, then the
     oracle's Algorithm 4 on the same lists against the GPU's InitBCM labels,
-    final block (all k+1 columns), labels and phi trace."""
+    final block (all k+1 columns), labels and phi trace.  node_order 0 (the
+    default) renames the nodes by degree at these sizes; 1 keeps them."""
     g = synth.config_large_dcsbm(0, n=n, m_edges=25 * n)
     k = 47
-    labels, ex, info = _gpu_cluster(ak, g, "bf16", k=k, beta=0.4, T_i=1)
+    labels, ex, info = _gpu_cluster(ak, g, "bf16", k=k, beta=0.4, T_i=1, node_order=node_order)
     rows = np.random.default_rng(4).choice(n, sample_rows, replace=False)
     compare_knn(g["X"], 10, rows, ex["knn_idx"], ex["knn_sim"])
     p = _params(ak, k=k, beta=0.4, T_i=1)
@@ -258,9 +295,11 @@ def _dcsbm_oracle_parity(ak, n, sample_rows):
     return ari, ang
 
 
-def test_dcsbm_workload_oracle_parity_600k(ak):
-    """A quarter of the large workload (n = 6e5)."""
-    _dcsbm_oracle_parity(ak, 600_000, 64)
+@pytest.mark.parametrize("node_order", [0, 1])
+def test_dcsbm_workload_oracle_parity_600k(ak, node_order):
+    """A quarter of the large workload (n = 6e5), with the nodes renamed by
+    degree (the default at this size) and in the generator's order."""
+    _dcsbm_oracle_parity(ak, 600_000, 64, node_order)
 
 
 def test_dcsbm_workload_oracle_parity_full_size(ak):

@@ -94,9 +94,11 @@ def _oracle_params(p):
                 disc_max_iter=p.disc_max_iter, early_stop=bool(p.early_stop), eps_Q=p.eps_Q)
 
 
-def test_warm_start_cluster(ak):
+@pytest.mark.parametrize("node_order", [1, 2])
+def test_warm_start_cluster(ak, node_order):
     """Targets are ANCKA's own blocks on two training graphs; on a fresh graph
-    the GPU and the oracle take the same start (warm or InitBCM) and agree."""
+    the GPU and the oracle take the same start (warm or InitBCM) and agree,
+    with the iteration on the caller's node order and on the degree order."""
     k = 4
     items = []
     for seed in (20, 21):
@@ -109,7 +111,7 @@ def test_warm_start_cluster(ak):
     ak.warm_train(items, w, 40, 3e-3, 1e-2)
     torch.cuda.synchronize()
     g = GRAPHS["sbm"](22)
-    p = ak.default_params(k=k, knn_prec="fp32")
+    p = ak.default_params(k=k, knn_prec="fp32", node_order=node_order)
     td = ak.topology_to_device(g)
     labels, ex, info = ak.cluster(td, torch.as_tensor(g["X"], device="cuda"), p, want_Q=True, want_knn=True,
                                   warm=w)
