@@ -2,7 +2,8 @@
 //
 // Topology (built once per call, deterministic):
 //   graph / multiplex  each layer's (row, col) pairs (plus reversed pairs for
-//     directed input) are sorted and de-duplicated, giving the binary A_l of
+//     directed input) are sorted and de-duplicated (skipped for undirected
+//     input whose rows are already strictly increasing), giving the binary A_l of
 //     Eq. rw-ag / rw-mg; the layers are then concatenated row by row into one
 //     CSR whose values are P_N[i,j] = 1/(L deg_l(i)) and, on the same
 //     pattern, P_N^T[i,j] = 1/(L deg_l(j)) (A_l is symmetric).
@@ -56,22 +57,51 @@ __global__ void k_check_ptr(const int64_t* __restrict__ ptr, int64_t rows, int64
   if (i < rows && ptr[i] > ptr[i + 1]) atomicExch(bad, 1);
 }
 
+// Entry-parallel kernels: a warp covers 32 x kPerLane consecutive entries,
+// lane-interleaved (so loads and stores coalesce); each lane finds the row of
+// its first entry by binary search and walks forward.  Rows of any length
+// (hubs of skewed degree distributions) cost the same per entry.
+constexpr int kPerLane = 16;
+
+// the last row r in [0, nrows) with ptr[r] <= p (the row holding entry p
+// when ptr[0] <= p < ptr[nrows])
+__device__ __forceinline__ int64_t row_of(const int64_t* __restrict__ ptr, int64_t nrows, int64_t p) {
+  int64_t lo = 0, hi = nrows - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (ptr[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// (row, col) keys of one layer (and the reversed pairs for directed input);
+// *unsorted is set if some row's columns are not strictly increasing
 __global__ void k_csr_to_keys(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                               int64_t n, int directed, int cb, uint64_t* __restrict__ keys,
-                              int32_t* __restrict__ bad) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t b = ptr[i], e = ptr[i + 1], base = ptr[0];
-  for (int64_t p = b; p < e; ++p) {
+                              int32_t* __restrict__ bad, int32_t* __restrict__ unsorted) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t base = ptr[0], total = ptr[n] - base;
+  const int64_t q0 = warp * 32 * kPerLane + lane;
+  if (q0 >= total) return;
+  int64_t i = row_of(ptr, n, base + q0);
+  bool out_of_order = false;
+  for (int t = 0; t < kPerLane; ++t) {
+    const int64_t q = q0 + 32 * t;
+    if (q >= total) break;
+    const int64_t p = base + q;
+    while (ptr[i + 1] <= p) ++i;
     int32_t j = col[p];
+    if (p > ptr[i] && col[p - 1] >= j) out_of_order = true;
     if (j < 0 || j >= n) {
       atomicExch(bad, 1);
       j = 0;
     }
-    int64_t q = p - base;
     keys[directed ? 2 * q : q] = ((uint64_t)i << cb) | (uint32_t)j;
     if (directed) keys[2 * q + 1] = ((uint64_t)j << cb) | (uint32_t)i;
   }
+  if (out_of_order) *unsorted = 1;
 }
 
 __global__ void k_hyper_to_keys(const int64_t* __restrict__ he_ptr, const int32_t* __restrict__ nodes,
@@ -90,13 +120,28 @@ __global__ void k_hyper_to_keys(const int64_t* __restrict__ he_ptr, const int32_
 }
 
 // counts per row (key >> cb); col = low cb bits
-__global__ void k_keys_to_rows(const uint64_t* __restrict__ keys, const int64_t* __restrict__ cnt_dev, int cb,
-                               int32_t* __restrict__ rowcnt, int32_t* __restrict__ col) {
-  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= *cnt_dev) return;
-  uint64_t k = keys[q];
-  atomicAdd(&rowcnt[k >> cb], 1);
-  if (col) col[q] = (int32_t)(k & col_mask(cb));
+__global__ void k_keys_to_cols(const uint64_t* __restrict__ keys, int64_t cnt, int cb, int32_t* __restrict__ col) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < cnt) col[q] = (int32_t)(keys[q] & col_mask(cb));
+}
+
+// ptr[r] = the first key position whose row is >= r (r = 0..nrows)
+__global__ void k_row_bounds(const uint64_t* __restrict__ keys, int64_t cnt, int cb, int64_t nrows,
+                             int64_t* __restrict__ ptr) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > nrows) return;
+  int64_t lo = 0, hi = cnt;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)(keys[mid] >> cb) < r) lo = mid + 1;
+    else hi = mid;
+  }
+  ptr[r] = lo;
+}
+
+__global__ void k_row_counts(const int64_t* __restrict__ ptr, int64_t nrows, int32_t* __restrict__ cnt) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrows) cnt[r] = (int32_t)(ptr[r + 1] - ptr[r]);
 }
 
 // (row << cb_in | col) -> (col << cb_out | row); cb_out covers the old rows
@@ -108,35 +153,41 @@ __global__ void k_swap_halves(const uint64_t* __restrict__ in, const int64_t* __
   out[q] = ((k & col_mask(cb_in)) << cb_out) | (k >> cb_in);
 }
 
-__global__ void k_int_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = a[i];
-}
-
 __global__ void k_inv_count(const int32_t* __restrict__ c, float* __restrict__ inv, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) inv[i] = c[i] > 0 ? 1.f / (float)c[i] : 0.f;
 }
 
 // merged multiplex / graph CSR: row i = layer 0 row i, layer 1 row i, ...
+// merged entry o of row i: the layers' rows in layer order
 __global__ void k_merge_layers(int L, int64_t n, const int64_t* const* __restrict__ lptr,
                                const int32_t* const* __restrict__ lcol,
                                const int32_t* const* __restrict__ ldeg,
                                const int64_t* __restrict__ mptr, int32_t* __restrict__ mcol,
                                float* __restrict__ val, float* __restrict__ valT) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t o = mptr[i];
-  float invL = 1.f / (float)L;
-  for (int l = 0; l < L; ++l) {
-    const int32_t* deg = ldeg[l];
-    float wi = deg[i] > 0 ? invL / (float)deg[i] : 0.f;
-    for (int64_t p = lptr[l][i]; p < lptr[l][i + 1]; ++p, ++o) {
-      int32_t j = lcol[l][p];
-      mcol[o] = j;
-      if (val) val[o] = wi;
-      if (valT) valT[o] = deg[j] > 0 ? invL / (float)deg[j] : 0.f;  // deg[j] >= 1 for a symmetric A_l
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = mptr[n];
+  const int64_t o0 = warp * 32 * kPerLane + lane;
+  if (o0 >= total) return;
+  const float invL = 1.f / (float)L;
+  int64_t i = row_of(mptr, n, o0);
+  for (int t = 0; t < kPerLane; ++t) {
+    const int64_t o = o0 + 32 * t;
+    if (o >= total) break;
+    while (mptr[i + 1] <= o) ++i;
+    int64_t d = o - mptr[i];
+    int l = 0;
+    for (; l < L - 1; ++l) {
+      const int64_t len = lptr[l][i + 1] - lptr[l][i];
+      if (d < len) break;
+      d -= len;
     }
+    const int32_t j = lcol[l][lptr[l][i] + d];
+    mcol[o] = j;
+    const int32_t* deg = ldeg[l];
+    if (val) val[o] = deg[i] > 0 ? invL / (float)deg[i] : 0.f;
+    if (valT) valT[o] = deg[j] > 0 ? invL / (float)deg[j] : 0.f;  // deg[j] >= 1 for a symmetric A_l
   }
 }
 
@@ -240,19 +291,18 @@ __global__ void k_topo_rowscale(const float* __restrict__ beta, const float* __r
 inline unsigned grid_for(int64_t n, int b) { return (unsigned)ceil_div(n > 0 ? n : 1, b); }
 
 // sorted unique keys -> CSR over the high halves (rows 0..nrows-1)
-ancka_status keys_to_csr(Workspace& ws, const uint64_t* ukeys, const int64_t* ucnt_dev, int64_t ucnt,
+ancka_status keys_to_csr(Workspace& ws, const uint64_t* ukeys, int64_t ucnt,
                          int64_t nrows, int cb, Csr* out, int32_t** rowcnt_out, cudaStream_t s) {
   int32_t* rowcnt;
-  ANCKA_TRY(ws.zeros(&rowcnt, (size_t)nrows + 1));
+  ANCKA_TRY(ws.alloc(&rowcnt, (size_t)nrows + 1));
   ANCKA_TRY(ws.alloc(&out->col, (size_t)ucnt));
-  k_keys_to_rows<<<grid_for(ucnt, 256), 256, 0, s>>>(ukeys, ucnt_dev, cb, rowcnt, out->col);
-  ANCKA_LAUNCHED();
-  int64_t* len;
-  ANCKA_TRY(ws.alloc(&len, (size_t)nrows + 1));
-  k_int_to_i64<<<grid_for(nrows + 1, 256), 256, 0, s>>>(rowcnt, len, nrows + 1);
+  k_keys_to_cols<<<grid_for(ucnt, 256), 256, 0, s>>>(ukeys, ucnt, cb, out->col);
   ANCKA_LAUNCHED();
   ANCKA_TRY(ws.alloc(&out->ptr, (size_t)nrows + 1));
-  ANCKA_TRY(exclusive_scan(ws, len, out->ptr, nrows + 1, s));
+  k_row_bounds<<<grid_for(nrows + 1, 256), 256, 0, s>>>(ukeys, ucnt, cb, nrows, out->ptr);
+  ANCKA_LAUNCHED();
+  k_row_counts<<<grid_for(nrows, 256), 256, 0, s>>>(out->ptr, nrows, rowcnt);
+  ANCKA_LAUNCHED();
   out->nrows = nrows;
   out->nnz = ucnt;
   *rowcnt_out = rowcnt;
@@ -307,13 +357,13 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
       return ANCKA_ERR_INVALID_ARG;
     }
     int32_t* esize;
-    ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, m, nb, &w->edges, &esize, s));
+    ANCKA_TRY(keys_to_csr(ws, k2, ucnt, m, nb, &w->edges, &esize, s));
     // node -> hyperedge incidence
     k_swap_halves<<<grid_for(ucnt, 256), 256, 0, s>>>(k2, ucnt_dev, nb, mb, k0);
     ANCKA_LAUNCHED();
     ANCKA_TRY(radix_sort_u64(ws, k0, k1, ucnt, nb + mb, s));
     int32_t* vdeg;
-    ANCKA_TRY(keys_to_csr(ws, k1, ucnt_dev, ucnt, n, mb, &w->topo, &vdeg, s));
+    ANCKA_TRY(keys_to_csr(ws, k1, ucnt, n, mb, &w->topo, &vdeg, s));
     w->degree = vdeg;
     ANCKA_TRY(ws.alloc(&w->inv_size, (size_t)m));
     ANCKA_TRY(ws.alloc(&w->inv_deg, (size_t)n));
@@ -340,18 +390,28 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
       ANCKA_TRY(ws.alloc(&k0, (size_t)cnt));
       ANCKA_TRY(ws.alloc(&k1, (size_t)cnt));
       ANCKA_TRY(ws.alloc(&k2, (size_t)cnt));
-      k_csr_to_keys<<<grid_for(n, 256), 256, 0, s>>>(rp, t.col_idx, n, t.directed, nb, k0, bad);
+      int32_t* unsorted;
+      ANCKA_TRY(ws.zeros(&unsorted, 1));
+      k_csr_to_keys<<<grid_for(ceil_div(e - b, 32 * kPerLane) * 32, 256), 256, 0, s>>>(rp, t.col_idx, n, t.directed,
+                                                                                      nb, k0, bad, unsorted);
       ANCKA_LAUNCHED();
+      int32_t hu = 0;
+      ANCKA_CUDA(cudaMemcpyAsync(&hu, unsorted, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       ANCKA_TRY(check_bad(bad, s, "topology: node id out of range [0, n)"));
-      ANCKA_TRY(radix_sort_u64(ws, k0, k1, cnt, 2 * nb, s));
       int64_t* ucnt_dev;
       ANCKA_TRY(ws.zeros(&ucnt_dev, 1));
-      if (cnt > 0) ANCKA_TRY(unique_u64(ws, k1, k2, ucnt_dev, cnt, s));
       int64_t ucnt = 0;
-      ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
+      if (!t.directed && !hu) {  // rows already strictly increasing: the keys are sorted and unique
+        k2 = k0;
+        ucnt = cnt;
+      } else {
+        ANCKA_TRY(radix_sort_u64(ws, k0, k1, cnt, 2 * nb, s));
+        if (cnt > 0) ANCKA_TRY(unique_u64(ws, k1, k2, ucnt_dev, cnt, s));
+        ANCKA_TRY(read_count(ucnt_dev, &ucnt, s));
+      }
       Csr lay;
       int32_t* deg;
-      ANCKA_TRY(keys_to_csr(ws, k2, ucnt_dev, ucnt, n, nb, &lay, &deg, s));
+      ANCKA_TRY(keys_to_csr(ws, k2, ucnt, n, nb, &lay, &deg, s));
       lptr[l] = lay.ptr;
       lcol[l] = lay.col;
       ldeg[l] = deg;
@@ -389,7 +449,7 @@ ancka_status build_topology(Workspace& ws, const ancka_topology& t, Walk* w, cud
       ANCKA_TRY(ws.alloc(&w->topo.val, (size_t)tot));
       ANCKA_TRY(ws.alloc(&w->topo.valT, (size_t)tot));
     }
-    k_merge_layers<<<grid_for(n, 256), 256, 0, s>>>(L, n, dlptr, dlcol, dldeg, w->topo.ptr,
+    k_merge_layers<<<grid_for(ceil_div(tot, 32 * kPerLane) * 32, 256), 256, 0, s>>>(L, n, dlptr, dlcol, dldeg, w->topo.ptr,
                                                     w->topo.col, w->topo.val, w->topo.valT);
     ANCKA_LAUNCHED();
   }

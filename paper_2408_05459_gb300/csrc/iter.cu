@@ -862,9 +862,9 @@ ancka_status apply_rinv(const float* Z, int ld, int64_t n, int w, const float* R
 // Discretize (Def. 2, Alg. 5)
 // ---------------------------------------------------------------------------
 struct DiscState {
-  float* part;          // kDiscMaxGrid x k x k: per-CTA sums of Q~ rows per cluster
+  long long* part;      // kDiscMaxGrid x k x k: per-CTA sums of Q~ rows per cluster (fixed point)
   int32_t* partc;       // kDiscMaxGrid x k: per-CTA cluster sizes
-  float2* S;            // k x k: float-float totals of part
+  long long* S;         // k x k: totals of part
   int32_t* cnt;         // k: cluster sizes of the current Y
   unsigned int* bar;    // 2: grid barrier count and generation
   int32_t* err;         // 1: grid barrier expired
@@ -872,13 +872,13 @@ struct DiscState {
 
 constexpr int kDiscThreads = 512;
 constexpr int kDiscMaxGrid = 320;
-// dynamic shared memory, in floats: a region of 4 x 64 x 65 (the row tile
-// in phase A; M, X, X', P or Jacobi's A and V in phase B), the tile's
+// dynamic shared memory, in floats: a region of 256 x 68 (the row tile
+// in phase A; M, X, X', P (4 x 64 x 65) or Jacobi's A and V in phase B), the tile's
 // labels, the slice sums, R with rows padded to a multiple of 16 columns
 constexpr int kDiscLd = 65;
-constexpr int kDiscRegion = 4 * 64 * kDiscLd;
+constexpr int kDiscRegion = 256 * 68;  // >= 4 x 64 x kDiscLd (phase B) and the staged tile of phase A
 constexpr int kDiscLabels = 512;
-constexpr int kDiscSlices = 16384;
+constexpr int kDiscSlices = 8192;  // the int64 cluster sums, k x k <= 4096 of them
 constexpr int kDiscR = 64 * 64;
 constexpr int kNsMaxIter = 60;
 
@@ -1170,13 +1170,96 @@ __device__ bool polar_newton_schulz(const float* M, int k, float* X, float* Xn, 
   return conv_s != 0;
 }
 
+// Fixed-point scale of the cluster sums in Discretize: |q| <= 1 for a
+// row-normalised Q~, so n < 2^31 rows of 2^31-scaled entries cannot overflow
+// an int64, and integer sums are exact in any order (the totals do not
+// depend on how the rows are split between CTAs).  Rounding each entry costs
+// at most 2^-32, far below FP32's resolution of M.
+constexpr float kDiscFix = 2147483648.0f;
+constexpr double kDiscFixInv = 1.0 / 2147483648.0;
+
+// Y = argmax(Q~ R) for the rows of one staged tile, a register-blocked
+// product.  The tile is staged row-major (row stride kDiscLds, 16-byte
+// aligned); lane (row group g, column group cg) of warp w computes rows
+// 16 w + g + 4 i (i = 0..3) x columns cg CPC .. cg CPC + CPC - 1 (CPC =
+// ldr / 8: eight lanes span the padded columns of R), four features a at a
+// time: four 16-byte loads of Q~ and 4 CPC / 2 8-byte loads of R feed
+// 16 CPC FMAs.  Per lane the columns are visited in ascending order with
+// strict ">", and across the eight lanes the lower column wins equal
+// scores: ties go to the lowest column.  Features past k are zero in Q~
+// and rows past k of R are zero.
+constexpr int kDiscTR = 256;  // rows per tile
+constexpr int kDiscLds = 68;  // row stride of the staged tile: 64 features + 4 (bank offset 4 rows apart)
+template <int CPC>
+__device__ __forceinline__ void disc_argmax_tile(const float* __restrict__ tile, int rows, const float* __restrict__ Rs,
+                                                 int ldr, int k4, int k, int64_t tb, int32_t* __restrict__ labels,
+                                                 int32_t* __restrict__ labt) {
+  const int lane = threadIdx.x & 31, cg = lane & 7;
+  const int rbase = 16 * (threadIdx.x >> 5) + (lane >> 3);  // rows rbase + 4 i
+  const int c0 = cg * CPC;
+  float acc[4][CPC];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < CPC; ++j) acc[i][j] = 0.f;
+  for (int a = 0; a < k4; a += 4) {
+    float4 q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = *reinterpret_cast<const float4*>(tile + (rbase + 4 * i) * kDiscLds + a);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float rv[CPC];
+#pragma unroll
+      for (int j = 0; j < CPC; j += 2) {
+        const float2 t = *reinterpret_cast<const float2*>(Rs + (a + u) * ldr + c0 + j);
+        rv[j] = t.x;
+        rv[j + 1] = t.y;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float x = u == 0 ? q[i].x : u == 1 ? q[i].y : u == 2 ? q[i].z : q[i].w;
+#pragma unroll
+        for (int j = 0; j < CPC; ++j) acc[i][j] = fmaf(x, rv[j], acc[i][j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float best = -INFINITY;
+    int bc = 0x7fffffff;
+#pragma unroll
+    for (int j = 0; j < CPC; ++j)
+      if (c0 + j < k && acc[i][j] > best) {
+        best = acc[i][j];
+        bc = c0 + j;
+      }
+#pragma unroll
+    for (int off = 1; off <= 4; off <<= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+      if (ob > best || (ob == best && oc < bc)) {
+        best = ob;
+        bc = oc;
+      }
+    }
+    const int r = rbase + 4 * i;
+    if (cg == 0 && r < rows) {
+      if (bc == 0x7fffffff) bc = 0;  // a NaN row
+      labels[tb + r] = bc;
+      labt[r] = bc;
+    }
+  }
+}
+
 // Discretize (Def. 2, Alg. 5) as one persistent cooperative kernel.  Per
 // iteration:
 //  A. every CTA takes a contiguous row range in tiles staged in shared
-//     memory, sets Y = argmax(Q~ R) (ties to the lowest column), and sums
-//     its Q~ rows per cluster (fixed order) with its cluster sizes;
+//     memory (the next tile prefetched to L2), sets Y = argmax(Q~ R) (ties
+//     to the lowest column), orders the tile's rows by cluster (stable) and
+//     adds each cluster's rows (FP32, in order) to its sums in fixed point
+//     (exact int64), with its cluster sizes;
 //  R. after a grid barrier the CTAs total the per-CTA sums, one warp per
-//     entry (float-float, fixed order);
+//     entry (exact int64);
 //  B. after a second barrier every CTA forms M = Y~^T Q~ (the totals over
 //     the cluster sizes), takes R = V U^T for M = U Omega V^T (Newton-Schulz,
 //     or Jacobi for rank-deficient M) and obj = n - 2 tr(Omega), and stops
@@ -1193,101 +1276,137 @@ k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_it
   __shared__ int done_s;
   const int tid = threadIdx.x;
   const int kk = k * k;
-  const int nsl = max(1, min((int)blockDim.x / k, kDiscSlices / kk));
   const int ldr = (k + 15) & ~15;
-  const int lds = ldt + 1;
-  const int TPR = k > 16 ? 2 : 1;          // threads per row in the argmax
-  const int TR = (int)blockDim.x / TPR;    // rows per tile
+  constexpr int TR = kDiscTR;
+  static_assert(2 * TR <= kDiscLabels, "tile labels and order");
+  static_assert(kDiscThreads * 4 == TR * 8, "four rows x eight column lanes per tile row group");
+  static_assert(TR * kDiscLds <= kDiscRegion && 4 * 64 * kDiscLd <= kDiscRegion, "staged tile, phase B");
+  __shared__ int32_t wcnt[TR / 32][64];
+  __shared__ int32_t seg0[64], segn[64];
   float* region = dsm_f;
   int32_t* labt = reinterpret_cast<int32_t*>(dsm_f + kDiscRegion);
-  float* sM = dsm_f + kDiscRegion + kDiscLabels;
-  float* Rs = sM + kDiscSlices;
+  int32_t* ordt = labt + TR;
+  unsigned long long* sMi = reinterpret_cast<unsigned long long*>(dsm_f + kDiscRegion + kDiscLabels);
+  float* Rs = dsm_f + kDiscRegion + kDiscLabels + kDiscSlices;
   const int64_t per = ceil_div(n, (int64_t)gridDim.x);
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = (r0 + per < n) ? r0 + per : n;
   const int nv4 = ldt / 4;
-  for (int e = tid; e < k * ldr; e += blockDim.x) Rs[e] = (e / ldr == e % ldr) ? 1.f : 0.f;  // R = I
+  const int cpc = ldr >> 3;  // columns per lane in the argmax: 2, 4, 6 or 8
+  const int wid = tid >> 5, lane = tid & 31;
+  // R = I; rows k .. ldt - 1 stay zero (the argmax reads R four rows at a time)
+  for (int e = tid; e < ldt * ldr; e += blockDim.x) Rs[e] = (e / ldr == e % ldr && e / ldr < k) ? 1.f : 0.f;
   double obj_prev = 0.0;
   for (int it = 0; it < max_iter; ++it) {
     // ---------------- phase A ----------------------------------------------
     for (int e = tid; e < 64; e += blockDim.x) hist[e] = 0;
-    for (int e = tid; e < nsl * kk; e += blockDim.x) sM[e] = 0.f;
+    for (int e = tid; e < kk; e += blockDim.x) sMi[e] = 0ull;
     __syncthreads();
     for (int64_t tb = r0; tb < r1; tb += TR) {
       const int rows = (int)((r1 - tb) < TR ? (r1 - tb) : TR);
-      {
+      {  // row-major, coalesced: float4 j of row r; all of a thread's loads
+         // (at most 8: nv4 <= 16) are issued first; rows past the range are zero
+        constexpr int kLd = kDiscTR * 16 / kDiscThreads;
         const float4* src = reinterpret_cast<const float4*>(Qt + tb * ldt);
-        for (int e = tid; e < rows * nv4; e += blockDim.x) {
-          const float4 v = src[e];
-          float* d = region + (e / nv4) * lds + 4 * (e % nv4);
-          d[0] = v.x;
-          d[1] = v.y;
-          d[2] = v.z;
-          d[3] = v.w;
+        float4 v[kLd];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+          const int e = tid + u * kDiscThreads;
+          const int r = e / nv4;
+          v[u] = (r < rows) ? src[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+          const int e = tid + u * kDiscThreads;
+          const int r = e / nv4, j = e - r * nv4;
+          if (r < TR) *reinterpret_cast<float4*>(region + r * kDiscLds + 4 * j) = v[u];
+        }
+      }
+      for (int e = tid; e < (TR / 32) * 64; e += blockDim.x) (&wcnt[0][0])[e] = 0;
+      {  // the next tile of this CTA's rows towards L2 while this one is scored
+        const int64_t nb = tb + TR;
+        const int64_t nrows = nb < r1 ? ((r1 - nb) < TR ? (r1 - nb) : TR) : 0;
+        const int64_t lines = (nrows * ldt * 4 + 127) / 128;
+        if (tid < lines) {
+          const char* pf = reinterpret_cast<const char*>(Qt + nb * ldt) + 128 * tid;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
         }
       }
       __syncthreads();
-      const int r = tid / TPR, h = tid % TPR;
-      float best = -INFINITY;
-      int bc = 0x7fffffff;
-      if (r < rows) {
-        const float* q = region + r * lds;
-        for (int cb = 16 * h; cb < k; cb += 16 * TPR) {
-          float acc[16];
+      if (cpc <= 2) disc_argmax_tile<2>(region, rows, Rs, ldr, ldt, k, tb, labels, labt);
+      else if (cpc == 4) disc_argmax_tile<4>(region, rows, Rs, ldr, ldt, k, tb, labels, labt);
+      else if (cpc == 6) disc_argmax_tile<6>(region, rows, Rs, ldr, ldt, k, tb, labels, labt);
+      else disc_argmax_tile<8>(region, rows, Rs, ldr, ldt, k, tb, labels, labt);
+      __syncthreads();
+      // the tile's rows in a stable order by cluster: warp ranks (a match on
+      // the label), per-cluster prefixes over the warps, cluster offsets
+      int lr = 64, rk = 0;
+      if (tid < TR) {
+        const bool v = tid < rows;
+        lr = v ? labt[tid] : 64;
+        const unsigned peers = __match_any_sync(0xffffffffu, lr);
+        rk = __popc(peers & ((1u << lane) - 1u));
+        if (v && rk == 0) wcnt[wid][lr] = __popc(peers);
+      }
+      __syncthreads();
+      if (wid == 0) {  // lane owns clusters lane and lane + 32: prefixes over the warps, then a scan
+        int tot[2];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-          for (int a = 0; a < k; ++a) {
-            const float qa = q[a];
-            const float4* rr = reinterpret_cast<const float4*>(Rs + a * ldr + cb);
+        for (int h = 0; h < 2; ++h) {
+          const int l = lane + 32 * h;
+          int acc = 0;
+          if (l < k) {
 #pragma unroll
-            for (int j4 = 0; j4 < 4; ++j4) {
-              const float4 rv = rr[j4];
-              acc[4 * j4 + 0] = fmaf(qa, rv.x, acc[4 * j4 + 0]);
-              acc[4 * j4 + 1] = fmaf(qa, rv.y, acc[4 * j4 + 1]);
-              acc[4 * j4 + 2] = fmaf(qa, rv.z, acc[4 * j4 + 2]);
-              acc[4 * j4 + 3] = fmaf(qa, rv.w, acc[4 * j4 + 3]);
+            for (int w = 0; w < TR / 32; ++w) {
+              const int c = wcnt[w][l];
+              wcnt[w][l] = acc;
+              acc += c;
             }
+            segn[l] = acc;
+            hist[l] += acc;
           }
+          tot[h] = acc;
+        }
+        int base = 0;
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (cb + j < k && acc[j] > best) {
-              best = acc[j];
-              bc = cb + j;
-            }
-        }
-      }
-      if (TPR == 2) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, 1);
-        const int oc = __shfl_xor_sync(0xffffffffu, bc, 1);
-        if (ob > best || (ob == best && oc < bc)) {
-          best = ob;
-          bc = oc;
-        }
-      }
-      if (r < rows && h == 0) {
-        if (bc == 0x7fffffff) bc = 0;
-        labels[tb + r] = bc;
-        labt[r] = bc;
-        atomicAdd(&hist[bc], 1);
-      }
-      __syncthreads();
-      {
-        const int sl = tid / k, c = tid % k;
-        if (sl < nsl) {
-          const int sper = (rows + nsl - 1) / nsl;
-          const int s0 = sl * sper;
-          const int s1 = (s0 + sper < rows) ? s0 + sper : rows;
-          float* my = sM + sl * kk;
-          for (int t = s0; t < s1; ++t) my[labt[t] * k + c] += region[t * lds + c];
+        for (int h = 0; h < 2; ++h) {
+          int inc = tot[h];
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+          }
+          if (lane + 32 * h < k) seg0[lane + 32 * h] = base + inc - tot[h];
+          base += __shfl_sync(0xffffffffu, inc, 31);
         }
       }
       __syncthreads();
+      if (tid < rows) ordt[seg0[lr] + wcnt[wid][lr] + rk] = tid;
+      __syncthreads();
+      // cluster sums: thread e owns entry (l, c) = (e / k, e % k) of the k x k
+      // sums for the whole call; a tile adds its rows of cluster l in order
+      // (FP32), then the tile's sum in fixed point (exact int64)
+      for (int e = tid; e < kk; e += blockDim.x) {
+        const int l = e / k, c = e - l * k;
+        const int b = seg0[l], m = segn[l];
+        if (m == 0) continue;
+        const float* col = region + c;
+        float s4[4] = {0.f, 0.f, 0.f, 0.f};  // four interleaved partial sums, combined in a fixed order
+        int q = 0;
+        for (; q + 4 <= m; q += 4) {
+          const int i0 = ordt[b + q], i1 = ordt[b + q + 1], i2 = ordt[b + q + 2], i3 = ordt[b + q + 3];
+          s4[0] += col[i0 * kDiscLds];
+          s4[1] += col[i1 * kDiscLds];
+          s4[2] += col[i2 * kDiscLds];
+          s4[3] += col[i3 * kDiscLds];
+        }
+        for (; q < m; ++q) s4[q & 3] += col[ordt[b + q] * kDiscLds];
+        const float sum = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+        sMi[e] += (unsigned long long)__float2ll_rn(sum * kDiscFix);
+      }
+      __syncthreads();
     }
-    for (int e = tid; e < kk; e += blockDim.x) {
-      float t = 0.f;
-      for (int q = 0; q < nsl; ++q) t += sM[q * kk + e];
-      st.part[(int64_t)blockIdx.x * kk + e] = t;
-    }
+    for (int e = tid; e < kk; e += blockDim.x) st.part[(int64_t)blockIdx.x * kk + e] = (long long)sMi[e];
     for (int e = tid; e < k; e += blockDim.x) st.partc[(int64_t)blockIdx.x * k + e] = hist[e];
     if (!grid_barrier(st.bar, st.err)) return;
     // ---------------- phase R: totals, one warp per entry ------------------
@@ -1295,13 +1414,10 @@ k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_it
       const int nw = blockDim.x >> 5, wid = tid >> 5, lane = tid & 31;
       for (int e = blockIdx.x * nw + wid; e < kk + k; e += gridDim.x * nw) {
         if (e < kk) {
-          float h = 0.f, l = 0.f;
-          for (int b = lane; b < (int)gridDim.x; b += 32) ff_add(h, l, __ldcg(st.part + (int64_t)b * kk + e), 0.f);
-          for (int off = 16; off >= 1; off >>= 1) {  // ff_add is symmetric: every lane ends equal
-            const float oh = __shfl_xor_sync(0xffffffffu, h, off), ol = __shfl_xor_sync(0xffffffffu, l, off);
-            ff_add(h, l, oh, ol);
-          }
-          if (lane == 0) st.S[e] = make_float2(h, l);
+          long long t = 0;
+          for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(st.part + (int64_t)b * kk + e);
+          for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+          if (lane == 0) st.S[e] = t;
         } else {
           int c = 0;
           for (int b = lane; b < (int)gridDim.x; b += 32) c += __ldcg(st.partc + (int64_t)b * k + (e - kk));
@@ -1317,9 +1433,9 @@ k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_it
     __syncthreads();
     for (int e = tid; e < kk; e += blockDim.x) {
       const int l = e / k, c = e % k;
-      const float2 v = __ldcg(st.S + e);
+      const long long v = __ldcg(st.S + e);
       const int cl = cnt_s[l];
-      M[l * kDiscLd + c] = cl > 0 ? (float)(((double)v.x + (double)v.y) / (double)cl) : 0.f;
+      M[l * kDiscLd + c] = cl > 0 ? (float)((double)v * kDiscFixInv / (double)cl) : 0.f;
     }
     __syncthreads();
     bool empty = false;
@@ -1332,6 +1448,7 @@ k_discretize(const float* __restrict__ Qt, int ldt, int64_t n, int k, int max_it
       float* P0 = region + 3 * kDiscLd * 64;
       ok = k <= 16   ? polar_newton_schulz<16>(M, k, X0, X1, P0, Rs, ldr)
            : k <= 32 ? polar_newton_schulz<32>(M, k, X0, X1, P0, Rs, ldr)
+           : k <= 48 ? polar_newton_schulz<48>(M, k, X0, X1, P0, Rs, ldr)
                      : polar_newton_schulz<64>(M, k, X0, X1, P0, Rs, ldr);
     }
     if (!ok)
@@ -1395,6 +1512,7 @@ __global__ void __launch_bounds__(kDiscThreads) k_polar_diag(const float* __rest
   if (!zero_row)
     ok = k <= 16   ? polar_newton_schulz<16>(M, k, X0, X1, P0, Rs, ldr)
          : k <= 32 ? polar_newton_schulz<32>(M, k, X0, X1, P0, Rs, ldr)
+         : k <= 48 ? polar_newton_schulz<48>(M, k, X0, X1, P0, Rs, ldr)
                    : polar_newton_schulz<64>(M, k, X0, X1, P0, Rs, ldr);
   if (!ok) polar_jacobi(M, k, X0, X1, P0, Rs, ldr, &rotated);
   __syncthreads();
@@ -2543,8 +2661,8 @@ ancka_status polar_factor(const float* M, int32_t k, float* R, int32_t* method_d
 // Bytes of caller-provided scratch Discretize needs for an n x k block.
 size_t discretize_scratch_bytes(int64_t n, int32_t k) {
   const size_t ldk = (size_t)round_up(k, 4);
-  return align256((size_t)n * ldk * sizeof(float)) + align256((size_t)kDiscMaxGrid * k * k * sizeof(float)) +
-         align256((size_t)kDiscMaxGrid * k * sizeof(int32_t)) + align256((size_t)k * k * sizeof(float2)) +
+  return align256((size_t)n * ldk * sizeof(float)) + align256((size_t)kDiscMaxGrid * k * k * sizeof(long long)) +
+         align256((size_t)kDiscMaxGrid * k * sizeof(int32_t)) + align256((size_t)k * k * sizeof(long long)) +
          align256((size_t)k * sizeof(int32_t)) + 256;
 }
 
@@ -2564,12 +2682,12 @@ ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, in
   float* Qt = reinterpret_cast<float*>(p);
   p += align256((size_t)n * ldk * sizeof(float));
   DiscState st;
-  st.part = reinterpret_cast<float*>(p);
-  p += align256((size_t)kDiscMaxGrid * k * k * sizeof(float));
+  st.part = reinterpret_cast<long long*>(p);
+  p += align256((size_t)kDiscMaxGrid * k * k * sizeof(long long));
   st.partc = reinterpret_cast<int32_t*>(p);
   p += align256((size_t)kDiscMaxGrid * k * sizeof(int32_t));
-  st.S = reinterpret_cast<float2*>(p);
-  p += align256((size_t)k * k * sizeof(float2));
+  st.S = reinterpret_cast<long long*>(p);
+  p += align256((size_t)k * k * sizeof(long long));
   st.cnt = reinterpret_cast<int32_t*>(p);
   p += align256((size_t)k * sizeof(int32_t));
   st.bar = reinterpret_cast<unsigned int*>(p);

@@ -33,51 +33,73 @@ __global__ void __launch_bounds__(kThreads) k_rs_hist(const uint64_t* __restrict
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kTile;
   const unsigned lane_lt = (1u << (t & 31)) - 1u;
-#pragma unroll 4
+  unsigned dg[kItems];  // all loads in flight before the first vote
+#pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t i = base + r * kThreads + t;
-    const unsigned d = i < count ? (unsigned)(keys[i] >> shift) & 255u : 256u;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (d < 256u && (peers & lane_lt) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    dg[r] = i < count ? (unsigned)(keys[i] >> shift) & 255u : 256u;
+  }
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+    if (dg[r] < 256u && (peers & lane_lt) == 0) atomicAdd(&h[dg[r]], (uint32_t)__popc(peers));
   }
   __syncthreads();
   hist[(int64_t)t * tiles + blockIdx.x] = h[t];
 }
 
-// stable scatter of one tile: keys keep their index order within a digit
+// stable scatter of one tile: keys keep their index order within a digit.
+// Warp w ranks the 512 consecutive keys [w 512, (w + 1) 512) of the tile in
+// 16 rounds of 32 (a match on the digit, the group's leader advancing the
+// warp's counter for that digit); one block-wide prefix over the warps'
+// counters then places warp w's keys of a digit after those of warps < w.
 __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                          int64_t count, int shift, int64_t tiles,
                                                          const int64_t* __restrict__ off) {
   __shared__ int64_t run[256];
   __shared__ uint32_t wc[kWarps][256];
-  const int t = threadIdx.x, warp = t >> 5;
-  const unsigned lane_lt = (1u << (t & 31)) - 1u;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const unsigned lane_lt = (1u << lane) - 1u;
   run[t] = off[(int64_t)t * tiles + blockIdx.x];
-  const int64_t base = (int64_t)blockIdx.x * kTile;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) wc[w][t] = 0;
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)warp * (32 * kItems) + lane;
+  uint64_t keys[kItems];  // all loads in flight before the first rank
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) keys[r] = base + 32 * r < count ? in[base + 32 * r] : 0ull;
+  __syncthreads();
+  uint32_t rank[kItems];
+#pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    const int64_t i = base + r * kThreads + t;
-    const bool valid = i < count;
-    const uint64_t key = valid ? in[i] : 0ull;
-    const unsigned d = valid ? (unsigned)(key >> shift) & 255u : 256u;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) wc[w][t] = 0;
-    __syncthreads();
+    const bool valid = base + 32 * r < count;
+    const unsigned d = valid ? (unsigned)(keys[r] >> shift) & 255u : 256u;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & lane_lt);
-    if (valid && rank == 0) wc[warp][d] = (uint32_t)__popc(peers);
-    __syncthreads();
-    // thread t owns digit t: counts of the warps before each warp
-    uint32_t acc = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t c = wc[w][t];
-      wc[w][t] = acc;
-      acc += c;
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (valid && lane == leader) {
+      before = wc[warp][d];
+      wc[warp][d] = before + (uint32_t)__popc(peers);
     }
-    __syncthreads();
-    if (valid) out[run[d] + wc[warp][d] + rank] = key;
-    __syncthreads();
-    run[t] += acc;
+    before = __shfl_sync(0xffffffffu, before, leader);
+    rank[r] = before + (uint32_t)__popc(peers & lane_lt);
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread t owns digit t: counts of the warps before each warp
+  uint32_t acc = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = wc[w][t];
+    wc[w][t] = acc;
+    acc += c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    if (base + 32 * r < count) {
+      const unsigned d = (unsigned)(keys[r] >> shift) & 255u;
+      out[run[d] + wc[warp][d] + rank[r]] = keys[r];
+    }
   }
 }
 

@@ -156,6 +156,31 @@ def test_degree_order_same_result_as_given_order(ak):
     assert np.allclose(a[2]["phi"], b[2]["phi"], atol=1e-5)
 
 
+def test_unsorted_duplicated_rows_same_result(ak):
+    """Rows given with their columns shuffled and some entries repeated (the
+    build then sorts and de-duplicates) give the same walk, so bit-identical
+    labels and block, as the sorted rows (which skip the sort)."""
+    g = synth.config_small_sbm(4)
+    rp, col = g["layers"][0]
+    rng = np.random.default_rng(17)
+    rows = []
+    for i in range(g["n"]):
+        r = col[rp[i]:rp[i + 1]].copy()
+        rng.shuffle(r)
+        if r.size and rng.random() < 0.3:
+            r = np.concatenate([r, r[: 1 + r.size // 3]])
+        rows.append(r)
+    rp2 = np.concatenate([[0], np.cumsum([r.size for r in rows])]).astype(rp.dtype)
+    col2 = np.concatenate(rows).astype(col.dtype)
+    g2 = dict(g)
+    g2["layers"] = [(rp2, col2)]
+    a = _gpu_cluster(ak, g, "fp32")
+    b = _gpu_cluster(ak, g2, "fp32")
+    assert col2.size > col.size
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1]["Q"], b[1]["Q"])
+
+
 def test_cliques_closed_form_on_gpu(ak):
     k, c = 5, 24
     g = synth.cliques_closed_form(k, c, seed=7)
