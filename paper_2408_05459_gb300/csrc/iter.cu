@@ -621,13 +621,26 @@ k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, const float*
   for (int64_t rb = r0; rb < r1; rb += trows) {
     const int rows = (int)((r1 - rb) < trows ? (r1 - rb) : trows);
     __syncthreads();
-    for (int e = t; e < rows * nb; e += kGramThreads) {
-      const int r = e / nb, c = 4 * (e % nb);
-      float4 v = *reinterpret_cast<const float4*>(Z + (rb + r) * ldz + c);
-      if (c + 1 >= w) v.y = 0.f;  // columns >= w read as zero
-      if (c + 2 >= w) v.z = 0.f;
-      if (c + 3 >= w) v.w = 0.f;
-      *reinterpret_cast<float4*>(&T[r * tld + c]) = v;
+    {  // a tile is trows x nb <= kGramRows kGramLd / 4 float4, all of a thread's loads issued first
+      constexpr int kLd = (kGramRows * kGramLd / 4 + kGramThreads - 1) / kGramThreads;
+      float4 v[kLd];
+#pragma unroll
+      for (int u = 0; u < kLd; ++u) {
+        const int e = t + u * kGramThreads;
+        const int r = e / nb, c = 4 * (e - r * nb);
+        v[u] = r < rows ? *reinterpret_cast<const float4*>(Z + (rb + r) * ldz + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kLd; ++u) {
+        const int e = t + u * kGramThreads;
+        const int r = e / nb, c = 4 * (e - r * nb);
+        if (r < rows) {
+          if (c + 1 >= w) v[u].y = 0.f;  // columns >= w read as zero
+          if (c + 2 >= w) v[u].z = 0.f;
+          if (c + 3 >= w) v[u].w = 0.f;
+          *reinterpret_cast<float4*>(&T[r * tld + c]) = v[u];
+        }
+      }
     }
     __syncthreads();
     if (Rin) {  // Q rows of the tile: q[c] = sum_{a <= c} z[a] R^-1[a, c]
@@ -811,49 +824,65 @@ __device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int
   }
 }
 
-// out[i, c] = sum_{a <= c} Z[i, a] Rinv[a, c]  (padding columns -> 0)
-template <int G>
-__global__ void __launch_bounds__(256)
+// out[i, c] = sum_{a <= c} Z[i, a] Rinv[a, c]  (padding columns -> 0).
+// CTAs take tiles of rows grid-stride: a tile is staged in shared memory by
+// coalesced 16-byte loads (all of a thread's loads issued first), then each
+// thread forms one float4 of an output row from the staged row and R^-1.
+__global__ void __launch_bounds__(kGramThreads)
 k_apply_rinv(const float* __restrict__ Z, int ld, int64_t n, int w, const float* __restrict__ Rinv,
              float* __restrict__ out) {
+  constexpr int kApplyRows = 64;  // tile buffer rows at the widest block (static shared memory <= 48 KB)
   __shared__ __align__(16) float Rs[kMaxW * kMaxW];
+  __shared__ __align__(16) float T[kApplyRows * kGramLd];
   const int nv4 = ld / 4;
-  for (int e = threadIdx.x; e < w * ld; e += blockDim.x) {
+  const int t = threadIdx.x;
+  for (int e = t; e < w * ld; e += blockDim.x) {
     const int a = e / ld, c = e % ld;
     Rs[a * ld + c] = (c < w && a <= c) ? Rinv[a * w + c] : 0.f;
   }
-  __syncthreads();
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = t / G;
-  const int g = (int)(t % G);
-  if (i >= n || g >= nv4) return;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float* z = Z + i * ld;
-  const int amax = (4 * g + 3 < w - 1) ? 4 * g + 3 : w - 1;
-  for (int a = 0; a <= amax; ++a) {
-    const float za = z[a];
-    const float4 r = *reinterpret_cast<const float4*>(&Rs[a * ld + 4 * g]);
-    acc.x = fmaf(za, r.x, acc.x);
-    acc.y = fmaf(za, r.y, acc.y);
-    acc.z = fmaf(za, r.z, acc.z);
-    acc.w = fmaf(za, r.w, acc.w);
+  const int trows = (kApplyRows * kGramLd) / ld;
+  for (int64_t rb = (int64_t)blockIdx.x * trows; rb < n; rb += (int64_t)gridDim.x * trows) {
+    const int rows = (int)((n - rb) < trows ? (n - rb) : trows);
+    __syncthreads();
+    {
+      constexpr int kLd = (kApplyRows * kGramLd / 4 + kGramThreads - 1) / kGramThreads;
+      const float4* src = reinterpret_cast<const float4*>(Z + rb * ld);
+      float4 v[kLd];
+#pragma unroll
+      for (int u = 0; u < kLd; ++u) {
+        const int e = t + u * kGramThreads;
+        v[u] = e < rows * nv4 ? src[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kLd; ++u) {
+        const int e = t + u * kGramThreads;
+        if (e < rows * nv4) *reinterpret_cast<float4*>(&T[4 * e]) = v[u];
+      }
+    }
+    __syncthreads();
+    for (int e = t; e < rows * nv4; e += blockDim.x) {
+      const int r = e / nv4, g = e - r * nv4;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* z = T + r * ld;
+      const int amax = (4 * g + 3 < w - 1) ? 4 * g + 3 : w - 1;
+      for (int a = 0; a <= amax; ++a) {
+        const float za = z[a];
+        const float4 rv = *reinterpret_cast<const float4*>(&Rs[a * ld + 4 * g]);
+        acc.x = fmaf(za, rv.x, acc.x);
+        acc.y = fmaf(za, rv.y, acc.y);
+        acc.z = fmaf(za, rv.z, acc.z);
+        acc.w = fmaf(za, rv.w, acc.w);
+      }
+      *reinterpret_cast<float4*>(out + (rb + r) * ld + 4 * g) = acc;
+    }
   }
-  *reinterpret_cast<float4*>(out + i * ld + 4 * g) = acc;
 }
-
-int pick_g(int nv4) { return nv4 <= 1 ? 1 : nv4 <= 2 ? 2 : nv4 <= 4 ? 4 : nv4 <= 8 ? 8 : 16; }
 
 ancka_status apply_rinv(const float* Z, int ld, int64_t n, int w, const float* Rinv, float* out,
                         cudaStream_t s) {
-  const int G = pick_g(ld / 4);
-  const unsigned grid = grid_for(n * G, 256);
-  switch (G) {
-    case 1: k_apply_rinv<1><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
-    case 2: k_apply_rinv<2><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
-    case 4: k_apply_rinv<4><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
-    case 8: k_apply_rinv<8><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
-    default: k_apply_rinv<16><<<grid, 256, 0, s>>>(Z, ld, n, w, Rinv, out); break;
-  }
+  const int64_t tiles = ceil_div(n, (int64_t)((64 * kGramLd) / ld));  // kApplyRows rows of kGramLd floats
+  const unsigned grid = (unsigned)(tiles < 4 * 152 ? tiles : 4 * 152);
+  k_apply_rinv<<<grid > 0 ? grid : 1, kGramThreads, 0, s>>>(Z, ld, n, w, Rinv, out);
   ANCKA_LAUNCHED();
   return ANCKA_OK;
 }
@@ -2326,7 +2355,7 @@ static ancka_status run_ancka_rows(Workspace& ws, const Walk& w, const IterCfg& 
   sc.tblk = (int)(ceil_div(n, 4096) < 304 ? ceil_div(n, 4096) : 304);
   ANCKA_TRY(ws.alloc(&sc.tpart, (size_t)sc.tblk));
   ANCKA_TRY(ws.alloc(&sc.take, 1));
-  const int gblk = (int)(ceil_div(n, 512) < 152 ? ceil_div(n, 512) : 152);
+  const int gblk = (int)(ceil_div(n, 512) < 2 * 152 ? ceil_div(n, 512) : 2 * 152);  // two CTAs per SM
   float2* gpart;
   unsigned int* gticket;
   ANCKA_TRY(ws.alloc(&gpart, (size_t)gblk * wq * (wq + 1) / 2));
