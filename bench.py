@@ -28,6 +28,7 @@ import multiprocessing as mp
 import os
 import re
 import statistics
+import select
 import subprocess
 import sys
 import tempfile
@@ -131,12 +132,17 @@ class Clocks:
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.first = ""
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
                                        "-lms", "20", "-i", str(index)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+        # wait (at most 5 s) for the first sample, so that the sampler's start-up
+        # is not inside the timed region
+        if self.p is not None and select.select([self.p.stdout], [], [], 5.0)[0]:
+            self.first = self.p.stdout.readline()
 
     def stop(self):
         if self.p is None:
@@ -149,7 +155,7 @@ class Clocks:
             out, _ = self.p.communicate()
         sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in (self.first + out).strip().splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
