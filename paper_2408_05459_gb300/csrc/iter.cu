@@ -1942,6 +1942,133 @@ struct Scratch {
 };
 
 // CalMHC(Y) (Alg. 2): phi into phi_slot, keep-best into best_labels
+// The first CalMHC hop, Z = coef P F0 + oh_coef h(Y) with F0 = f0 h(Y)
+// (h(Y)[j, c] = inv[c] for c = y_j, else 0), of a graph or multiplex walk:
+// row i of P F0 is f0 inv[c] times the sum of P[i, j] over the j with
+// y_j = c, so the hop gathers 4-byte labels instead of rows of F0.  A warp
+// per row takes 32 entries a round; the lanes holding the same label add
+// their weights in lane order (every lane walks the 32 lanes), the lowest of
+// them adds the sum to the row's per-cluster total (rounds in order), first
+// for the topology part (scaled by the row scale), then for the KNN part.
+__global__ void __launch_bounds__(256)
+k_walk_onehot(const int64_t* __restrict__ ptrA, const int32_t* __restrict__ colA, const float* __restrict__ valA,
+              const float* __restrict__ rsA, const int64_t* __restrict__ ptrB, const int32_t* __restrict__ colB,
+              const float* __restrict__ valB, const int32_t* __restrict__ labels, const float* __restrict__ inv,
+              int k, int ld, float f0, float coef, float oh_coef, int64_t n, int64_t long_min,
+              float* __restrict__ out) {
+  __shared__ float acc[8][2][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
+    if (long_min > 0 && (ptrA[i + 1] - ptrA[i]) + (ptrB ? ptrB[i + 1] - ptrB[i] : 0) > long_min)
+      continue;  // a long row: k_walk_onehot_long
+    for (int c = lane; c < 64; c += 32) acc[w][0][c] = acc[w][1][c] = 0.f;
+    __syncwarp();
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const int64_t* ptr = part == 0 ? ptrA : ptrB;
+      const int32_t* col = part == 0 ? colA : colB;
+      const float* val = part == 0 ? valA : valB;
+      if (!ptr) continue;
+      const int64_t b = ptr[i], e = ptr[i + 1];
+      for (int64_t p0 = b; p0 < e; p0 += 32) {
+        const int64_t p = p0 + lane;
+        int l = 64;
+        float wv = 0.f;
+        if (p < e) {
+          l = labels[col[p]];
+          wv = val ? val[p] : 1.f;
+        }
+        float sum = 0.f;
+        bool first = true;  // no lower lane holds this label
+#pragma unroll
+        for (int src = 0; src < 32; ++src) {
+          const int ls = __shfl_sync(0xffffffffu, l, src);
+          const float vs = __shfl_sync(0xffffffffu, wv, src);
+          if (ls == l) {
+            sum += vs;
+            if (src < lane) first = false;
+          }
+        }
+        if (l < 64 && first) acc[w][part][l] += sum;
+        __syncwarp();
+      }
+    }
+    const int yi = labels[i];
+    const float rs = rsA ? rsA[i] : 1.f;
+    for (int c = lane; c < ld; c += 32) {
+      float z = 0.f;
+      if (c < k) {
+        z = coef * (f0 * inv[c] * (acc[w][0][c] * rs + acc[w][1][c]));
+        if (c == yi) z += oh_coef * inv[c];
+      }
+      out[i * ld + c] = z;
+    }
+    __syncwarp();
+  }
+}
+
+// The same hop for the long rows (more than long_min entries): a CTA per
+// row, warp w taking the rounds w, w + 8, ... of each part; the warps'
+// per-cluster totals are added in warp order.
+__global__ void __launch_bounds__(256)
+k_walk_onehot_long(const int32_t* __restrict__ rows, const int64_t* __restrict__ ptrA,
+                   const int32_t* __restrict__ colA, const float* __restrict__ valA, const float* __restrict__ rsA,
+                   const int64_t* __restrict__ ptrB, const int32_t* __restrict__ colB,
+                   const float* __restrict__ valB, const int32_t* __restrict__ labels, const float* __restrict__ inv,
+                   int k, int ld, float f0, float coef, float oh_coef, float* __restrict__ out) {
+  __shared__ float acc[8][2][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = rows[blockIdx.x];
+  for (int c = lane; c < 64; c += 32) acc[w][0][c] = acc[w][1][c] = 0.f;
+  __syncwarp();
+#pragma unroll 1
+  for (int part = 0; part < 2; ++part) {
+    const int64_t* ptr = part == 0 ? ptrA : ptrB;
+    const int32_t* col = part == 0 ? colA : colB;
+    const float* val = part == 0 ? valA : valB;
+    if (!ptr) continue;
+    const int64_t b = ptr[i], e = ptr[i + 1];
+    for (int64_t p0 = b + 32 * w; p0 < e; p0 += 32 * 8) {
+      const int64_t p = p0 + lane;
+      int l = 64;
+      float wv = 0.f;
+      if (p < e) {
+        l = labels[col[p]];
+        wv = val ? val[p] : 1.f;
+      }
+      float sum = 0.f;
+      bool first = true;
+#pragma unroll
+      for (int src = 0; src < 32; ++src) {
+        const int ls = __shfl_sync(0xffffffffu, l, src);
+        const float vs = __shfl_sync(0xffffffffu, wv, src);
+        if (ls == l) {
+          sum += vs;
+          if (src < lane) first = false;
+        }
+      }
+      if (l < 64 && first) acc[w][part][l] += sum;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const int yi = labels[i];
+  const float rs = rsA ? rsA[i] : 1.f;
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    float z = 0.f;
+    if (c < k) {
+      float a0 = 0.f, a1 = 0.f;
+      for (int q = 0; q < 8; ++q) {
+        a0 += acc[q][0][c];
+        a1 += acc[q][1][c];
+      }
+      z = coef * (f0 * inv[c] * (a0 * rs + a1));
+      if (c == yi) z += oh_coef * inv[c];
+    }
+    out[i * ld + c] = z;
+  }
+}
+
 ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma, double* phi_slot,
                      double* phi_best, int32_t* taken_slot, int32_t* best_labels, bool first) {
   cudaStream_t s = c.s;
@@ -1950,12 +2077,36 @@ ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma
   ANCKA_LAUNCHED();
   k_inv_sqrt_counts<<<1, 64, 0, s>>>(sc.cnt, c.k, sc.inv);
   ANCKA_LAUNCHED();
-  k_fill_onehot<<<grid_for(c.n * c.ldk, 256), 256, 0, s>>>(labels, sc.inv, sc.cnt, c.k, c.n, c.ldk, 0, 0.f,
-                                                           c.alpha, sc.Fa);
-  ANCKA_LAUNCHED();
   float* cur = sc.Fa;
   float* nxt = sc.Fb;
+  // graphs and multiplex graphs: the first hop from F0 = alpha h(Y) gathers labels
+  const bool onehot_hop = c.w.kind != ANCKA_HYPERGRAPH && gamma > 0;
+  if (!onehot_hop || gamma == 0) {
+    k_fill_onehot<<<grid_for(c.n * c.ldk, 256), 256, 0, s>>>(labels, sc.inv, sc.cnt, c.k, c.n, c.ldk, 0, 0.f,
+                                                             c.alpha, sc.Fa);
+    ANCKA_LAUNCHED();
+  }
   for (int l = 0; l < gamma; ++l) {  // F <- (1 - alpha) P F + alpha h(Y)
+    if (l == 0 && onehot_hop) {
+      const int64_t blocks = ceil_div(c.n, (int64_t)8);
+      const Walk& w = c.w;
+      const LongRows& lr = c.lr_walk;  // the walk's long rows (found before the iteration)
+      const bool longs = lr.rows && lr.count_host > 0;
+      k_walk_onehot<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(
+          w.topo.ptr, w.topo.col, w.row_uniform ? nullptr : w.topo.val, w.rs_topo, w.knn.ptr, w.knn.col, w.knn.val,
+          labels, sc.inv, c.k, c.ldk, c.alpha, 1.f - c.alpha, c.alpha, c.n, longs ? lr.min_entries : 0, nxt);
+      ANCKA_LAUNCHED();
+      if (longs) {
+        k_walk_onehot_long<<<(unsigned)lr.count_host, 256, 0, s>>>(
+            lr.rows, w.topo.ptr, w.topo.col, w.row_uniform ? nullptr : w.topo.val, w.rs_topo, w.knn.ptr, w.knn.col,
+            w.knn.val, labels, sc.inv, c.k, c.ldk, c.alpha, 1.f - c.alpha, c.alpha, nxt);
+        ANCKA_LAUNCHED();
+      }
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+      continue;
+    }
     ANCKA_TRY(apply_walk(c, cur, c.ldk, nxt, 1.f - c.alpha, labels, sc.inv, c.alpha));
     float* t = cur;
     cur = nxt;
