@@ -579,6 +579,67 @@ __device__ __forceinline__ void block_pair(int q, int nb, int& A, int& B) {
 __device__ void chol_inv_block(const float2* __restrict__ partial, int nblk, int w, float* __restrict__ Rinv_out,
                                int32_t* __restrict__ status, double* csm, float2* scratch);
 
+// Rows of a staged tile times an upper-triangular R^-1 (rows of T and of Rs
+// at stride ld; Rs zero below the diagonal and past w): out[r, c] =
+// sum_{a <= c} T[r, a] Rs[a, c], each element's terms in ascending a (fmaf).
+// A thread takes two rows x two float4 column groups, so each load of T or
+// Rs serves two outputs.  Results go to the tile buffer Tout (may be null,
+// stride ld) and to global rows (stride ldo).
+__device__ __forceinline__ void rinv_tile(const float* __restrict__ T, int ld, int rows, int nb, int w,
+                                          const float* __restrict__ Rs, float* __restrict__ Tout,
+                                          float* __restrict__ gout, int64_t ldo) {
+  const int ngp = (nb + 1) >> 1, nrp = (rows + 1) >> 1;
+  for (int e = threadIdx.x; e < nrp * ngp; e += blockDim.x) {
+    const int rp = e / ngp, gp = e - rp * ngp;
+    const int r0 = 2 * rp, g0 = 2 * gp;
+    const bool r1ok = r0 + 1 < rows, g1ok = g0 + 1 < nb;
+    const float* z0 = T + r0 * ld;
+    const float* z1 = T + (r1ok ? r0 + 1 : r0) * ld;
+    const int am0 = (4 * g0 + 3 < w - 1) ? 4 * g0 + 3 : w - 1;
+    const int am1 = g1ok ? ((4 * g0 + 7 < w - 1) ? 4 * g0 + 7 : w - 1) : am0;
+    float4 c00 = make_float4(0.f, 0.f, 0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;  // [row][group]
+    int a = 0;
+#pragma unroll 4
+    for (; a <= am0; ++a) {
+      const float za0 = z0[a], za1 = z1[a];
+      const float4 r0v = *reinterpret_cast<const float4*>(&Rs[a * ld + 4 * g0]);
+      c00.x = fmaf(za0, r0v.x, c00.x); c00.y = fmaf(za0, r0v.y, c00.y);
+      c00.z = fmaf(za0, r0v.z, c00.z); c00.w = fmaf(za0, r0v.w, c00.w);
+      c10.x = fmaf(za1, r0v.x, c10.x); c10.y = fmaf(za1, r0v.y, c10.y);
+      c10.z = fmaf(za1, r0v.z, c10.z); c10.w = fmaf(za1, r0v.w, c10.w);
+      if (g1ok) {
+        const float4 r1v = *reinterpret_cast<const float4*>(&Rs[a * ld + 4 * g0 + 4]);
+        c01.x = fmaf(za0, r1v.x, c01.x); c01.y = fmaf(za0, r1v.y, c01.y);
+        c01.z = fmaf(za0, r1v.z, c01.z); c01.w = fmaf(za0, r1v.w, c01.w);
+        c11.x = fmaf(za1, r1v.x, c11.x); c11.y = fmaf(za1, r1v.y, c11.y);
+        c11.z = fmaf(za1, r1v.z, c11.z); c11.w = fmaf(za1, r1v.w, c11.w);
+      }
+    }
+    for (; a <= am1; ++a) {  // the second group's remaining terms
+      const float za0 = z0[a], za1 = z1[a];
+      const float4 r1v = *reinterpret_cast<const float4*>(&Rs[a * ld + 4 * g0 + 4]);
+      c01.x = fmaf(za0, r1v.x, c01.x); c01.y = fmaf(za0, r1v.y, c01.y);
+      c01.z = fmaf(za0, r1v.z, c01.z); c01.w = fmaf(za0, r1v.w, c01.w);
+      c11.x = fmaf(za1, r1v.x, c11.x); c11.y = fmaf(za1, r1v.y, c11.y);
+      c11.z = fmaf(za1, r1v.z, c11.z); c11.w = fmaf(za1, r1v.w, c11.w);
+    }
+    if (Tout) *reinterpret_cast<float4*>(&Tout[r0 * ld + 4 * g0]) = c00;
+    *reinterpret_cast<float4*>(gout + r0 * ldo + 4 * g0) = c00;
+    if (g1ok) {
+      if (Tout) *reinterpret_cast<float4*>(&Tout[r0 * ld + 4 * g0 + 4]) = c01;
+      *reinterpret_cast<float4*>(gout + r0 * ldo + 4 * g0 + 4) = c01;
+    }
+    if (r1ok) {
+      if (Tout) *reinterpret_cast<float4*>(&Tout[(r0 + 1) * ld + 4 * g0]) = c10;
+      *reinterpret_cast<float4*>(gout + (r0 + 1) * ldo + 4 * g0) = c10;
+      if (g1ok) {
+        if (Tout) *reinterpret_cast<float4*>(&Tout[(r0 + 1) * ld + 4 * g0 + 4]) = c11;
+        *reinterpret_cast<float4*>(gout + (r0 + 1) * ldo + 4 * g0 + 4) = c11;
+      }
+    }
+  }
+}
+
 // Gram partials of Z; the CTA that finishes last (atomic ticket) sums the
 // partials and factors them (chol_inv_block), so one launch does both.  With
 // Rin (an R^-1 of the previous pass) the launch first forms each tile's rows
@@ -644,28 +705,15 @@ k_gram_chol(const float* __restrict__ Z, int ldz, int64_t n, int w, const float*
     }
     __syncthreads();
     if (Rin) {  // Q rows of the tile: q[c] = sum_{a <= c} z[a] R^-1[a, c]
-      for (int e = t; e < rows * nb; e += kGramThreads) {
-        const int r = e / nb, g = e % nb;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int amax = (4 * g + 3 < w - 1) ? 4 * g + 3 : w - 1;
-        for (int a = 0; a <= amax; ++a) {
-          const float za = T[r * tld + a];
-          const float4 rv = *reinterpret_cast<const float4*>(&Rs[a * tld + 4 * g]);
-          acc.x = fmaf(za, rv.x, acc.x);
-          acc.y = fmaf(za, rv.y, acc.y);
-          acc.z = fmaf(za, rv.z, acc.z);
-          acc.w = fmaf(za, rv.w, acc.w);
-        }
-        *reinterpret_cast<float4*>(&TQ[r * tld + 4 * g]) = acc;
-        *reinterpret_cast<float4*>(Qout + (rb + r) * ldz + 4 * g) = acc;
-      }
+      rinv_tile(T, tld, rows, nb, w, Rs, TQ, Qout + rb * ldz, ldz);
       __syncthreads();
     }
     if (active) {
       float acc[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-      for (int r = sub; r < rows; r += S) {
+#pragma unroll 4
+      for (int r = sub; r < rows; r += S) {  // four rows' loads in flight
         const float4 xa = *reinterpret_cast<const float4*>(&src[r * tld + 4 * A]);
         const float4 xb = *reinterpret_cast<const float4*>(&src[r * tld + 4 * B]);
         const float a4[4] = {xa.x, xa.y, xa.z, xa.w}, b4[4] = {xb.x, xb.y, xb.z, xb.w};
@@ -860,21 +908,7 @@ k_apply_rinv(const float* __restrict__ Z, int ld, int64_t n, int w, const float*
       }
     }
     __syncthreads();
-    for (int e = t; e < rows * nv4; e += blockDim.x) {
-      const int r = e / nv4, g = e - r * nv4;
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float* z = T + r * ld;
-      const int amax = (4 * g + 3 < w - 1) ? 4 * g + 3 : w - 1;
-      for (int a = 0; a <= amax; ++a) {
-        const float za = z[a];
-        const float4 rv = *reinterpret_cast<const float4*>(&Rs[a * ld + 4 * g]);
-        acc.x = fmaf(za, rv.x, acc.x);
-        acc.y = fmaf(za, rv.y, acc.y);
-        acc.z = fmaf(za, rv.z, acc.z);
-        acc.w = fmaf(za, rv.w, acc.w);
-      }
-      *reinterpret_cast<float4*>(out + (rb + r) * ld + 4 * g) = acc;
-    }
+    rinv_tile(T, ld, rows, nv4, w, Rs, nullptr, out + rb * ld, ld);
   }
 }
 
