@@ -22,13 +22,13 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import multiprocessing as mp
 import os
 import re
 import statistics
-import select
 import subprocess
 import sys
 import tempfile
@@ -126,25 +126,30 @@ def recorded_traffic(path, key, src_file):
 
 
 class Clocks:
-    """nvidia-smi samples (20 ms) while the timed region runs."""
+    """nvidia-smi samples (20 ms, time-stamped). The sampler starts before the
+    warm-up calls, so that its start-up (and the idle gap it would leave) is
+    outside the timed region; stop(t0, t1) keeps the samples taken between
+    the wall-clock times t0 and t1 (all of them if none falls there)."""
 
     def __init__(self, index):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        self.first = ""
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
                                        "-lms", "20", "-i", str(index)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
-        # wait (at most 5 s) for the first sample, so that the sampler's start-up
-        # is not inside the timed region
-        if self.p is not None and select.select([self.p.stdout], [], [], 5.0)[0]:
-            self.first = self.p.stdout.readline()
 
-    def stop(self):
+    @staticmethod
+    def _when(stamp):
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t0=None, t1=None):
         if self.p is None:
             return None
         self.p.terminate()
@@ -153,25 +158,26 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
             out, _ = self.p.communicate()
-        sm, mx, pw, reasons = [], [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (self.first + out).strip().splitlines():
+        rows = []
+        for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-                pw.append(float(f[3]))
+                rows.append((self._when(f[0]), float(f[2]), float(f[3]), float(f[4]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+            if inside:
+                rows = inside
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "power_w_max": round(max(pw), 1) if pw else None, "reasons": sorted(reasons)}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {nm for r in rows for nm, v in zip(names, r[4]) if v.lower().startswith("active")}
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "samples": len(rows), "power_w_max": round(max(r[3] for r in rows), 1),
+                "reasons": sorted(reasons)}
 
 
 def max_over_ranks(value, dist, device):
@@ -494,6 +500,7 @@ def main():
         """steps timed calls (L2 flushed before each); info=True asks every
         call for its diagnostics (phase events, counters), which adds host
         work to the step."""
+        clk = Clocks(local)
         for _ in range(warmup):
             step(pr, info=info, **kw)
         torch.cuda.synchronize()
@@ -501,7 +508,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         l0 = ancka.kernel_launches()
-        clk = Clocks(local)
+        t_wall0 = time.time()
         durs, infos = [], []
         for _ in range(steps):
             flush.zero_()
@@ -514,7 +521,7 @@ def main():
             durs.append(a.elapsed_time(b))
             if info:
                 infos.append(inf)
-        clocks = clk.stop()
+        clocks = clk.stop(t_wall0, time.time())
         launches = ancka.kernel_launches() - l0
         torch.cuda.synchronize()
         ms = max_over_ranks(float(np.mean(durs)), dist, "cuda")

@@ -33,17 +33,23 @@ def _fake_smi(tmp_path, lines):
 
 
 @pytest.mark.parametrize("power_cap", [False, True])
-def test_clock_sampler_parses_every_sample(tmp_path, monkeypatch, power_cap):
+def test_clock_sampler_keeps_the_timed_window(tmp_path, monkeypatch, power_cap):
+    import datetime
+    import time
     cap = "Active" if power_cap else "Not Active"
-    lines = [f"0, {mhz}, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, {cap}"
-             for mhz in (2070, 2055, 2070, 1980, 2070)]
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+    stamps = [base + datetime.timedelta(seconds=s_) for s_ in range(6)]
+    mhz = [1400, 2070, 2055, 2070, 1980, 1500]     # the first and last samples lie outside the window
+    lines = [f"{t.strftime('%Y/%m/%d %H:%M:%S')}.000, 0, {m}, 2070, 1200.5, 0x0, Not Active, Not Active, "
+             f"Not Active, {cap}" for t, m in zip(stamps, mhz)]
     monkeypatch.setenv("PATH", _fake_smi(tmp_path, lines) + os.pathsep + os.environ["PATH"])
     c = bench.Clocks(0)
-    assert c.first.startswith("0, 2070")        # the first sample is read before timing starts
-    import time
-    time.sleep(0.3)
-    out = c.stop()
-    assert out["samples"] == 5                  # the first sample is counted with the rest
-    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    time.sleep(0.4)
+    out = c.stop(stamps[1].timestamp(), stamps[4].timestamp())
+    assert out["samples"] == 4
+    assert out["sm_mhz"] == 2062.5 and out["sm_max_mhz"] == 2070.0
     assert out["power_w_max"] == 1200.5
     assert out["reasons"] == (["sw_power_cap"] if power_cap else [])
+    c = bench.Clocks(0)
+    time.sleep(0.4)
+    assert c.stop()["samples"] == 6                 # no window: every sample
