@@ -58,7 +58,10 @@ k_prep_rows(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp, int p
     dot2_warp_reduce(s, cc);
     any = __any_sync(0xffffffffu, any);
     double n2 = (double)s + (double)cc;
-    float inv = any ? (float)(1.0 / sqrt(n2)) : 0.f;
+    // 1/||x|| in FP64 on one lane (GB300's FP64 pipe is narrow), then broadcast
+    float inv = 0.f;
+    if (lane == 0) inv = any ? (float)(1.0 / sqrt(n2)) : 0.f;
+    inv = __shfl_sync(0xffffffffu, inv, 0);
     float e2 = 0.f, um = 0.f;
     for (int c = lane; c < dp; c += 32) {
       float u = c < d ? x[c] * inv : 0.f;
@@ -128,7 +131,9 @@ k_prep_fp8(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp8, const
     }
     const float* x = X + row * (int64_t)d;
     const bool zero = zero_row[row] != 0;
-    const float inv = zero ? 0.f : (float)(1.0 / sqrt(nrm2[row]));
+    float inv = 0.f;  // FP64 on one lane, then broadcast (as in k_prep_rows)
+    if (lane == 0) inv = zero ? 0.f : (float)(1.0 / sqrt(nrm2[row]));
+    inv = __shfl_sync(0xffffffffu, inv, 0);
     float e2 = 0.f;
     for (int c = lane; c < dp8; c += 32) {
       const float u = c < d ? x[c] * inv : 0.f;
