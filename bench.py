@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--knn-probe", default=None, metavar="N,D[,tfidf]",
                     help="only run the BF16 KNN twice on a seeded N x D Gaussian matrix, or on the hypergraph "
                          "generator's TF-IDF attributes at N nodes (D = 500) with ',tfidf' (profiling aid)")
+    ap.add_argument("--disc-probe", type=int, default=None, metavar="N",
+                    help="Discretize alone on an N x 47 block with Zipf-sized clusters (profiling)")
     ap.add_argument("--spmm-probe", type=int, default=None, metavar="N",
                     help="Algorithm 4 on the DC-SBM generator (k=47, d=100, 25 N edges) at N nodes: the walk "
                          "products' time against their compulsory bytes (one JSON line; profiling aid)")
@@ -405,6 +407,37 @@ def knn_probe(args):
                       "knn_fallback_rows": info["knn_fallback_rows"]}), flush=True)
 
 
+def disc_probe(args):
+    """Kernel-focused run for profiling: ancka_discretize on a seeded N x 47
+    block (scaled one-hot rows of Zipf(1)-sized clusters plus Gaussian noise,
+    the shape of the large workload's block), one and two inner iterations
+    after a warm-up call; prints the time per inner iteration."""
+    import torch
+    from paper_2408_05459_gb300 import ancka, build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    ancka.load()
+    n, k = args.disc_probe, 47
+    rng = np.random.default_rng(0)
+    w = 1.0 / np.arange(1, k + 1)
+    y = rng.choice(k, n, p=w / w.sum())
+    Q = np.eye(k, dtype=np.float32)[y] * 0.3 + 0.05 * rng.standard_normal((n, k)).astype(np.float32)
+    Qd = torch.as_tensor(Q, device="cuda")
+    ms = {}
+    for it in (1, 2):
+        ancka.discretize(Qd, it)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ancka.discretize(Qd, it)
+        b.record()
+        torch.cuda.synchronize()
+        ms[it] = a.elapsed_time(b)
+    print(json.dumps({"probe": "discretize", "n": n, "k": k, "ms_1_iter": round(ms[1], 3),
+                      "ms_2_iter": round(ms[2], 3), "ms_per_inner_iteration": round(ms[2] - ms[1], 3)}), flush=True)
+
+
 def spmm_probe(args):
     """SpMM in the HBM regime: a degree-corrected SBM graph at N nodes (25 N
     edges, k = 47, d = 100, beta = 0.4, T_i = 1, T = 10), where the block Q
@@ -439,6 +472,8 @@ def main():
         return cpu_worker(args.cpu_worker)
     if args.spmm_probe:
         return spmm_probe(args)
+    if args.disc_probe:
+        return disc_probe(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
