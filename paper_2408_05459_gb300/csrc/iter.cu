@@ -956,6 +956,50 @@ __global__ void k_rownorm(const float* __restrict__ Q, int ldq, int off, int64_t
   for (int c = 0; c < ldt; ++c) Qt[i * ldt + c] = c < k ? q[c] * inv : 0.f;
 }
 
+// The same rows through shared memory (block strides up to 68 and 64): the
+// tile is loaded and stored coalesced, and each thread takes its row from the
+// tile with the same operations in the same order as k_rownorm.
+constexpr int kRnRows = 64;
+__global__ void __launch_bounds__(kRnRows)
+k_rownorm_tiled(const float* __restrict__ Q, int ldq, int off, int64_t n, int k, float* __restrict__ Qt, int ldt) {
+  __shared__ float T[kRnRows * 69];
+  __shared__ float O[kRnRows * 65];
+  const int64_t r0 = (int64_t)blockIdx.x * kRnRows;
+  const int rows = (int)((n - r0) < kRnRows ? (n - r0) : kRnRows);
+  const int tq = ldq + 1, to = ldt + 1;
+  const float* src = Q + r0 * ldq;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < rows * ldq; e += kRnRows) {
+    const int r = e / ldq;
+    T[r * tq + (e - r * ldq)] = src[e];
+  }
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < rows) {
+    const float* q = T + r * tq + off;
+    float s = 0.f;
+    for (int c = 0; c < k; ++c) s = fmaf(q[c], q[c], s);
+    const float inv = s > 0.f ? 1.f / sqrtf(s) : 0.f;  // a zero row stays zero
+    for (int c = 0; c < ldt; ++c) O[r * to + c] = c < k ? q[c] * inv : 0.f;
+  }
+  __syncthreads();
+  float* dst = Qt + r0 * ldt;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < rows * ldt; e += kRnRows) {
+    const int rr = e / ldt;
+    dst[e] = O[rr * to + (e - rr * ldt)];
+  }
+}
+
+// row-normalised copy: tiled for the library's own blocks, a thread per row
+// for a caller's block of any stride
+void rownorm(const float* Q, int ldq, int off, int64_t n, int k, float* Qt, int ldt, cudaStream_t s) {
+  if (ldq <= 68 && ldt <= 64)
+    k_rownorm_tiled<<<(unsigned)ceil_div(n > 0 ? n : 1, (int64_t)kRnRows), kRnRows, 0, s>>>(Q, ldq, off, n, k, Qt, ldt);
+  else
+    k_rownorm<<<(unsigned)ceil_div(n > 0 ? n : 1, (int64_t)256), 256, 0, s>>>(Q, ldq, off, n, k, Qt, ldt);
+}
+
 __global__ void k_disc_init(unsigned int* bar, int32_t* err) {
   if (threadIdx.x == 0) {
     bar[0] = 0;
@@ -2607,7 +2651,7 @@ static ancka_status run_ancka_rows(Workspace& ws, const Walk& w, const IterCfg& 
     k_warm_block<<<grid_for(n * ld, 256), 256, 0, s>>>(warm_W, ldw, n, k, ld, (float)(1.0 / sqrt((double)n)), Qb);
     ANCKA_LAUNCHED();
     ANCKA_TRY(cholqr2(ws, c, Qb, Qs, wq, gpart, gblk, gticket, Rinv, wstatus));  // result in Qb
-    k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qb, ld, 1, n, k, Qt, ldk);
+    rownorm(Qb, ld, 1, n, k, Qt, ldk, s);
     ANCKA_LAUNCHED();
     ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, cfg.disc_max_iter, yw, nullptr, tr->flags_dev, s));
     ANCKA_TRY(cal_mhc(c, sc, yw, cfg.gamma, phw, phw + 1, nullptr, ywb, true));
@@ -2702,7 +2746,7 @@ static ancka_status run_ancka_rows(Workspace& ws, const Walk& w, const IterCfg& 
       double* phi_slot = rec ? tr->phi_dev + slot : phi_spare;
       const int b = side ? slot & 1 : 0;
       if (side && qt_used[b]) ANCKA_CUDA(cudaStreamWaitEvent(s, disc_done[b], 0));  // its last reader is done
-      k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Q, ld, 1, n, k, Qt2[b], ldk);  // the snapshot of Q^(t)
+      rownorm(Q, ld, 1, n, k, Qt2[b], ldk, s);  // the snapshot of Q^(t)
       ANCKA_LAUNCHED();
       if (side) {
         ANCKA_CUDA(cudaEventRecord(q_ev, s));
@@ -2847,7 +2891,7 @@ ancka_status discretize(Workspace& ws, const float* Qk, int64_t n, int32_t k, in
   const int ldk = (int)round_up(k, 4);
   float* Qt;
   ANCKA_TRY(ws.alloc(&Qt, (size_t)n * ldk));
-  k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qk, ldq, 0, n, k, Qt, ldk);
+  rownorm(Qk, ldq, 0, n, k, Qt, ldk, s);
   ANCKA_LAUNCHED();
   DiscState st;
   ANCKA_TRY(make_disc_state(ws, n, k, &st));
@@ -2908,7 +2952,7 @@ ancka_status discretize_scratch(void* scratch, size_t bytes, const float* Qk, in
   st.err = reinterpret_cast<int32_t*>(p + 8);
   int32_t* it = reinterpret_cast<int32_t*>(p + 12);
   ANCKA_CUDA(cudaMemsetAsync(it, 0, sizeof(int32_t), s));
-  k_rownorm<<<grid_for(n, 256), 256, 0, s>>>(Qk, ldq, 0, n, k, Qt, ldk);
+  rownorm(Qk, ldq, 0, n, k, Qt, ldk, s);
   ANCKA_LAUNCHED();
   ANCKA_TRY(run_discretize(st, Qt, ldk, n, k, max_iter, labels, it, nullptr, s));
   *iters_dev = it;
