@@ -190,8 +190,8 @@ const char* ancka_last_error(void);
 ancka_status ancka_device_check(void);
 
 /* Number of this library's own CUDA kernels launched by the calling process
- * so far (a diagnostics counter; the kernels inside the one-off CUB sorts and
- * scans of the graph build are not counted). */
+ * so far (a diagnostics counter; every kernel is the library's own, the sorts
+ * and scans of the graph build included). */
 int64_t ancka_kernel_launches(void);
 
 /* Tuning (process-wide, thread-safe): BF16 KNN lists of inputs with at least
