@@ -2147,6 +2147,182 @@ k_walk_onehot_long(const int32_t* __restrict__ rows, const int64_t* __restrict__
   }
 }
 
+// The first orthogonal-iteration hop Z = P Q^(0) of a graph or multiplex
+// walk when Q^(0) comes from labels (Alg. 4 line 12 with reading R13):
+// column 0 of Q^(0) is n^-1/2, column 1 + c is inv[c] on the rows labelled c
+// -- or, for a dependent column (the highest-index non-empty cluster and every
+// empty one), the sign vector +-n^-1/2 from the top bit of
+// splitmix64(64 name_j + c).  Row i of P Q^(0) needs, per part (topology,
+// then KNN): the total of P[i, j], the per-label totals and, per dependent
+// column, the signed total -- 4-byte gathers instead of rows of Q^(0).  The
+// label totals as in k_walk_onehot; the row and signed totals by a fixed
+// xor butterfly per round, added round by round.
+struct Q0Cols {
+  int ndep;
+  int8_t depidx[64];   // index among the dependent columns, or -1
+  int32_t dep[64];     // the dependent columns
+};
+
+__device__ void q0_columns(const int32_t* __restrict__ cnt, int k, Q0Cols& qc) {
+  if (threadIdx.x == 0) {
+    int last = 0;
+    for (int c = 0; c < k; ++c)
+      if (cnt[c] > 0) last = c;
+    int nd = 0;
+    for (int c = 0; c < k; ++c) {
+      if (cnt[c] == 0 || c == last) {
+        qc.depidx[c] = (int8_t)nd;
+        qc.dep[nd++] = c;
+      } else {
+        qc.depidx[c] = -1;
+      }
+    }
+    qc.ndep = nd;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float q0_sign(int64_t name, int c) {
+  return (splitmix64((uint64_t)name * 64u + (uint64_t)c) >> 63) ? -1.f : 1.f;
+}
+
+// one round of 32 entries [p0, p0 + 32) of row part `part` for warp slot w
+__device__ __forceinline__ void q0_round(int64_t p0, int64_t e, const int32_t* __restrict__ col,
+                                         const float* __restrict__ val, const int32_t* __restrict__ labels,
+                                         const int32_t* __restrict__ names, const Q0Cols& qc,
+                                         float (&acc)[64], float (&sgn)[64], float& tot) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = p0 + lane;
+  int l = 64;
+  float wv = 0.f;
+  int64_t j = 0;
+  if (p < e) {
+    j = col[p];
+    l = labels[j];
+    wv = val ? val[p] : 1.f;
+  }
+  float sum = 0.f;
+  bool first = true;
+#pragma unroll
+  for (int src = 0; src < 32; ++src) {
+    const int ls = __shfl_sync(0xffffffffu, l, src);
+    const float vs = __shfl_sync(0xffffffffu, wv, src);
+    if (ls == l) {
+      sum += vs;
+      if (src < lane) first = false;
+    }
+  }
+  if (l < 64 && first) acc[l] += sum;
+  float t = wv;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  tot += t;
+  const int64_t name = names ? (int64_t)names[j] : j;
+  for (int d = 0; d < qc.ndep; ++d) {
+    float sv = p < e ? wv * q0_sign(name, qc.dep[d]) : 0.f;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+    if (lane == 0) sgn[d] += sv;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void q0_write_row(int64_t i, int k, int ld, float c0, float rs, const float* __restrict__ inv,
+                                             const Q0Cols& qc, const float* A0, const float* A1, const float* S0,
+                                             const float* S1, float T0, float T1, float* __restrict__ out) {
+  for (int col = threadIdx.x & 31; col < ld; col += 32) {
+    float z = 0.f;
+    if (col == 0) {
+      z = c0 * (T0 * rs + T1);
+    } else if (col <= k) {
+      const int c = col - 1, d = qc.depidx[c];
+      z = d >= 0 ? c0 * (S0[d] * rs + S1[d]) : inv[c] * (A0[c] * rs + A1[c]);
+    }
+    out[i * ld + col] = z;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_walk_q0(const int64_t* __restrict__ ptrA, const int32_t* __restrict__ colA, const float* __restrict__ valA,
+          const float* __restrict__ rsA, const int64_t* __restrict__ ptrB, const int32_t* __restrict__ colB,
+          const float* __restrict__ valB, const int32_t* __restrict__ labels, const float* __restrict__ inv,
+          const int32_t* __restrict__ cnt, const int32_t* __restrict__ names, int k, int ld, float c0, int64_t n,
+          int64_t long_min, float* __restrict__ out) {
+  __shared__ Q0Cols qc;
+  __shared__ float acc[8][2][64], sgn[8][2][64];
+  q0_columns(cnt, k, qc);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
+    if (long_min > 0 && (ptrA[i + 1] - ptrA[i]) + (ptrB ? ptrB[i + 1] - ptrB[i] : 0) > long_min)
+      continue;  // a long row: k_walk_q0_long
+    for (int c = lane; c < 64; c += 32) acc[w][0][c] = acc[w][1][c] = sgn[w][0][c] = sgn[w][1][c] = 0.f;
+    __syncwarp();
+    float tot[2] = {0.f, 0.f};
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const int64_t* ptr = part == 0 ? ptrA : ptrB;
+      if (!ptr) continue;
+      const int64_t e = ptr[i + 1];
+      for (int64_t p0 = ptr[i]; p0 < e; p0 += 32)
+        q0_round(p0, e, part == 0 ? colA : colB, part == 0 ? valA : valB, labels, names, qc, acc[w][part],
+                 sgn[w][part], tot[part]);
+    }
+    q0_write_row(i, k, ld, c0, rsA ? rsA[i] : 1.f, inv, qc, acc[w][0], acc[w][1], sgn[w][0], sgn[w][1], tot[0],
+                 tot[1], out);
+    __syncwarp();
+  }
+}
+
+// the long rows: a CTA per row, warp w taking rounds w, w + 8, ...; the
+// warps' totals added in warp order
+__global__ void __launch_bounds__(256)
+k_walk_q0_long(const int32_t* __restrict__ rows, const int64_t* __restrict__ ptrA, const int32_t* __restrict__ colA,
+               const float* __restrict__ valA, const float* __restrict__ rsA, const int64_t* __restrict__ ptrB,
+               const int32_t* __restrict__ colB, const float* __restrict__ valB, const int32_t* __restrict__ labels,
+               const float* __restrict__ inv, const int32_t* __restrict__ cnt, const int32_t* __restrict__ names,
+               int k, int ld, float c0, float* __restrict__ out) {
+  __shared__ Q0Cols qc;
+  __shared__ float acc[8][2][64], sgn[8][2][64], tots[8][2];
+  __shared__ float A[2][64], S[2][64], T[2];
+  q0_columns(cnt, k, qc);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = rows[blockIdx.x];
+  for (int c = lane; c < 64; c += 32) acc[w][0][c] = acc[w][1][c] = sgn[w][0][c] = sgn[w][1][c] = 0.f;
+  __syncwarp();
+  float tot[2] = {0.f, 0.f};
+#pragma unroll 1
+  for (int part = 0; part < 2; ++part) {
+    const int64_t* ptr = part == 0 ? ptrA : ptrB;
+    if (!ptr) continue;
+    const int64_t e = ptr[i + 1];
+    for (int64_t p0 = ptr[i] + 32 * w; p0 < e; p0 += 32 * 8)
+      q0_round(p0, e, part == 0 ? colA : colB, part == 0 ? valA : valB, labels, names, qc, acc[w][part],
+               sgn[w][part], tot[part]);
+  }
+  if (lane == 0) {
+    tots[w][0] = tot[0];
+    tots[w][1] = tot[1];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * 64; e += blockDim.x) {
+    const int part = e >> 6, c = e & 63;
+    float a = 0.f, sg = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      a += acc[q][part][c];
+      sg += sgn[q][part][c];
+    }
+    A[part][c] = a;
+    S[part][c] = sg;
+  }
+  if (threadIdx.x < 2) {
+    float t = 0.f;
+    for (int q = 0; q < 8; ++q) t += tots[q][threadIdx.x];
+    T[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (w == 0) q0_write_row(i, k, ld, c0, rsA ? rsA[i] : 1.f, inv, qc, A[0], A[1], S[0], S[1], T[0], T[1], out);
+}
+
 ancka_status cal_mhc(const Ctx& c, Scratch& sc, const int32_t* labels, int gamma, double* phi_slot,
                      double* phi_best, int32_t* taken_slot, int32_t* best_labels, bool first) {
   cudaStream_t s = c.s;
@@ -2676,6 +2852,18 @@ static ancka_status run_ancka_rows(Workspace& ws, const Walk& w, const IterCfg& 
     }
   }
   if (init_out) ANCKA_CUDA(cudaMemcpyAsync(init_out, y0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  // the first hop from the labels (graphs, multiplex graphs, Q^(0) from InitBCM
+  // or given labels): its own copies of the cluster sizes and 1/sqrt(size),
+  // since the keep-best chain recomputes the scratch ones beside the hops
+  const bool q0_labels = w.kind != ANCKA_HYPERGRAPH && !tr->warm_used;
+  int32_t* q0cnt = nullptr;
+  float* q0inv = nullptr;
+  if (q0_labels) {
+    ANCKA_TRY(ws.alloc(&q0cnt, 64));
+    ANCKA_TRY(ws.alloc(&q0inv, 64));
+    ANCKA_CUDA(cudaMemcpyAsync(q0cnt, sc.cnt, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, s));
+    ANCKA_CUDA(cudaMemcpyAsync(q0inv, sc.inv, sizeof(float) * k, cudaMemcpyDeviceToDevice, s));
+  }
   // fork: everything above (Y^(0), Q^(0), the scratch) is ready on s here
   SideJoin sj;
   cudaEvent_t q_ev = nullptr, disc_done[2] = {nullptr, nullptr};
@@ -2730,7 +2918,24 @@ static ancka_status run_ancka_rows(Workspace& ws, const Walk& w, const IterCfg& 
       PhaseTimer pt(tr, s, 3);
       {
         PhaseTimer pw(tr, s, 6);
-        ANCKA_TRY(apply_walk(c, Q, ld, Z, 1.f, nullptr, nullptr, 0.f));  // Z = P Q
+        if (t == 1 && q0_labels) {  // Z = P Q^(0) from the labels
+          const int64_t blocks = ceil_div(n, (int64_t)8);
+          const LongRows& lr = c.lr_walk;
+          const bool longs = lr.rows && lr.count_host > 0;
+          const float c0 = (float)(1.0 / sqrt((double)n));
+          k_walk_q0<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(
+              w.topo.ptr, w.topo.col, w.row_uniform ? nullptr : w.topo.val, w.rs_topo, w.knn.ptr, w.knn.col,
+              w.knn.val, y0, q0inv, q0cnt, w.names, k, ld, c0, n, longs ? lr.min_entries : 0, Z);
+          ANCKA_LAUNCHED();
+          if (longs) {
+            k_walk_q0_long<<<(unsigned)lr.count_host, 256, 0, s>>>(
+                lr.rows, w.topo.ptr, w.topo.col, w.row_uniform ? nullptr : w.topo.val, w.rs_topo, w.knn.ptr,
+                w.knn.col, w.knn.val, y0, q0inv, q0cnt, w.names, k, ld, c0, Z);
+            ANCKA_LAUNCHED();
+          }
+        } else {
+          ANCKA_TRY(apply_walk(c, Q, ld, Z, 1.f, nullptr, nullptr, 0.f));  // Z = P Q
+        }
       }
       if (Qprev && check)  // Q(t-1); CholeskyQR2 below uses Q as scratch
         ANCKA_CUDA(cudaMemcpyAsync(Qprev, Q, sizeof(float) * n * ld, cudaMemcpyDeviceToDevice, s));
