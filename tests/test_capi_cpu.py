@@ -46,6 +46,8 @@ int main(void) {
          sizeof(ancka_topology), sizeof(ancka_params), sizeof(ancka_outputs), sizeof(ancka_info));
   F(ancka_topology, he_nodes); F(ancka_topology, m); F(ancka_params, init_labels);
   F(ancka_params, knn_prec); F(ancka_info, phi_best); F(ancka_info, ms_knn); F(ancka_info, ms_total);
+  F(ancka_params, warm); F(ancka_params, knn_nlist); F(ancka_params, knn_nprobe); F(ancka_params, node_order);
+  F(ancka_info, knn_tiles); F(ancka_info, knn_full_tiles);
   return 0;
 }
 '''
@@ -67,6 +69,11 @@ int main(void) {
     assert int(vals["ancka_info.phi_best"]) == ancka.Info.phi_best.offset
     assert int(vals["ancka_info.ms_knn"]) == ancka.Info.ms_knn.offset
     assert int(vals["ancka_info.ms_total"]) == ancka.Info.ms_total.offset
+    # the fields appended at the ends of the two structs
+    for f in ("warm", "knn_nlist", "knn_nprobe", "node_order"):
+        assert int(vals[f"ancka_params.{f}"]) == getattr(ancka.Params, f).offset, f
+    for f in ("knn_tiles", "knn_full_tiles"):
+        assert int(vals[f"ancka_info.{f}"]) == getattr(ancka.Info, f).offset, f
 
 
 def test_oracle_and_cuda_path_are_independent():
