@@ -33,6 +33,8 @@ def test_status_strings_and_defaults(lib):
     p = ancka.default_params()
     assert (p.k, p.K, p.T, p.gamma, p.T_i, p.tau, p.disc_max_iter) == (5, 10, 10, 3, 25, 5, 20)
     assert abs(p.alpha - 0.2) < 1e-7 and abs(p.beta - 0.5) < 1e-7
+    # exact KNN lists, the automatic node order, InitBCM, the fixed schedule
+    assert (p.knn_nlist, p.knn_nprobe, p.node_order, p.init, p.early_stop) == (0, 0, 0, 0, 0)
 
 
 def test_struct_layout_matches_header():
